@@ -1,0 +1,141 @@
+/*
+ * tdeig.h -- C ABI of the GB300 (sm_103a) divide-and-conquer eigensolver for
+ * symmetric tridiagonal matrices, with the accelerated (HSS) eigenvector
+ * update of Li, Liao, Liu and Jiang, "New fast divide-and-conquer algorithms
+ * for the symmetric tridiagonal eigenvalue problem".
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers may be host or CUDA device memory; the library detects which
+ *    with cudaPointerGetAttributes.  Host arrays are staged through device
+ *    workspace owned by the handle (copies are stream-ordered on the handle's
+ *    stream).  Caller memory is never freed or retained by the library.
+ *  - Matrices are column-major.  Q_out is N x N with leading dimension N and
+ *    column j the unit eigenvector of lambda_out[j]; eigenvalues ascend.
+ *    (A row-major torch tensor passed as Q_out therefore holds Q^T.)
+ *  - All calls are ordered on the handle's CUDA stream and synchronise it
+ *    before returning, so the status is final.  One handle per host thread.
+ *  - Return value: TDEIG_OK (0) or a negative status; tdeig_strerror() gives
+ *    a message.  There is no host fallback: without a usable GPU every solve
+ *    returns TDEIG_ECUDA.
+ */
+#ifndef TDEIG_H
+#define TDEIG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tdeig_ctx* tdeig_handle;
+
+/* Eigenvector update used at merges whose deflated size exceeds
+ * hss_threshold (Algorithm 1; Sec. 4.3):
+ *   DENSE : the plain product diag(Q1, Q2) Qhat (standard DC);
+ *   ADC1  : HSS approximation of Qhat by structured rank-revealing Schur
+ *           complements (SRRSC), then Algorithm 3;
+ *   ADC2  : randomized HSS construction (Algorithm 2) with the off-diagonal
+ *           rank estimate of eq. (bounds), then Algorithm 3.
+ * Or-ed with one precision flag for the update products (deflation, secular
+ * roots, Loewner and normalisation are always FP64). */
+enum {
+    TDEIG_MODE_DENSE = 0,
+    TDEIG_MODE_ADC1 = 1,
+    TDEIG_MODE_ADC2 = 2,
+    TDEIG_MODE_MASK = 0xff,
+    TDEIG_PREC_FP64 = 0 << 8,     /* FP64 products */
+    TDEIG_PREC_SPLIT = 1 << 8,    /* split-precision tensor-core products */
+    TDEIG_PREC_MASK = 0xf << 8
+};
+
+enum {
+    TDEIG_OK = 0,
+    TDEIG_EINVAL = -1,    /* null pointer, N < 0, non-finite input, bad mode or option */
+    TDEIG_ENOMEM = -2,    /* device workspace allocation failed */
+    TDEIG_ECUDA = -3,     /* a CUDA runtime call or kernel launch failed */
+    TDEIG_ENOTCONV = -4,  /* leaf QR or secular iteration hit its cap */
+    TDEIG_ETIMEOUT = -5,  /* a bounded device-side wait expired */
+    TDEIG_ENOTIMPL = -6   /* requested feature not built */
+};
+
+typedef struct {
+    int leaf;            /* leaf size of the DC tree (paper: 25; default 32) */
+    int hss_threshold;   /* use HSS when the deflated size K exceeds this (paper: 2000) */
+    int hss_leaf;        /* HSS leaf block size (paper: ~200; default 128) */
+    double tol;          /* HSS compression tolerance (default 1e-12) */
+    int oversample;      /* p of the random sampling (paper: 10) */
+    double rank_eps;     /* epsilon of the rank estimate eq. (bounds) (paper: 1e-16) */
+    int rank_cap;        /* rank estimate cap (paper: 100) */
+    int boundary_shift;  /* max rows a leaf boundary moves when dist < 1e-10 (paper: 5) */
+    uint64_t seed;       /* seed of the Gaussian sampling matrix */
+    void* cuda_stream;   /* cudaStream_t to run on; NULL = a stream owned by the handle */
+} tdeig_options;
+
+/* Fills *opt with the defaults listed above. */
+void tdeig_default_options(tdeig_options* opt);
+
+/* Creates a handle on the current CUDA device.  opt may be NULL (defaults).
+ * Returns TDEIG_EINVAL for out == NULL or invalid options. */
+int tdeig_create(tdeig_handle* out, const tdeig_options* opt);
+
+/* Full eigendecomposition T = Q diag(lambda) Q^T of the symmetric tridiagonal
+ * T = tridiag(e, d, e) (eq. T; Algorithm 1).
+ *   d          : N diagonal entries (a_1..a_N in the paper)
+ *   e          : N-1 off-diagonal entries (b_1..b_{N-1}); may be NULL if N <= 1
+ *   lambda_out : N eigenvalues, ascending
+ *   Q_out      : N x N column-major eigenvectors (may be NULL: eigenvalues only
+ *                are still computed through the full method)
+ *   mode       : TDEIG_MODE_* | TDEIG_PREC_*
+ * N = 0 is a no-op; N = 1 gives lambda = d, Q = 1.  Non-finite input gives
+ * TDEIG_EINVAL.  Device workspace grows inside the handle as needed. */
+int tdeig_solve(tdeig_handle h, const double* d, const double* e, int64_t N,
+                double* lambda_out, double* Q_out, int mode);
+
+/* Independent problems of uneven sizes in one call.  N_each[b] is the size of
+ * member b (host array).  d_cat / e_cat / lambda_cat concatenate the members'
+ * arrays (e of member b has N_b - 1 entries, offsets are the prefix sums);
+ * Q_cat concatenates the column-major N_b x N_b blocks (offsets: prefix sums
+ * of N_b^2).  Every DC-tree level of every member runs in one launch per
+ * stage. */
+int tdeig_solve_batched(tdeig_handle h, int64_t batch, const int64_t* N_each,
+                        const double* d_cat, const double* e_cat,
+                        double* lambda_cat, double* Q_cat, int mode);
+
+/* Frees the handle and its workspace. */
+int tdeig_destroy(tdeig_handle h);
+
+/* Static message for a status code. */
+const char* tdeig_strerror(int status);
+
+/* JSON text with per-merge statistics of the last solve on h (deflated sizes
+ * K, HSS ranks, stage times).  Returns the length needed (excluding the NUL),
+ * or a negative status. */
+int tdeig_last_stats(tdeig_handle h, char* json_buf, size_t len);
+
+/* ---------------------------------------------------------------------- */
+/* Stage entry points of one merge, on a rank-one modified diagonal matrix */
+/* M = diag(d) + rho z z^T with d strictly ascending (Theorem 1).  Used to  */
+/* check the kernels stage by stage.  Pointers as above; K >= 1.           */
+/* ---------------------------------------------------------------------- */
+
+/* Secular roots (Theorem 1; Remark 1): lambda_i in (d_i, d_{i+1}) (last root
+ * in (d_K, d_K + rho |z|^2]), gamma_i = lambda_i - d_i, mu_i = d_{i+1} -
+ * lambda_i (mu_K = 0).  One warp per root.  TDEIG_ENOTCONV on the cap. */
+int tdeig_secular(tdeig_handle h, int64_t K, const double* d, const double* z, double rho,
+                  double* lambda, double* gamma, double* mu);
+
+/* Loewner recomputation of z (eq. ev_z, with 1/rho) and the Cauchy-like
+ * eigenvector matrix Qhat[k, j] = uhat_k v_j / (d_k - lambda_j) (eq. Ev-Q),
+ * every d_k - lambda_j formed by Remark 1.  uhat, v: K entries; Qhat: K x K
+ * column-major (may be NULL to skip it). */
+int tdeig_lowner_cauchy(tdeig_handle h, int64_t K, const double* d, const double* gamma,
+                        const double* mu, const double* z, double rho,
+                        double* uhat, double* v, double* Qhat);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDEIG_H */

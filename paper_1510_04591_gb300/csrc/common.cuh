@@ -1,0 +1,119 @@
+// Internal declarations shared by the translation units of libtdeig.so.
+// Not part of the public C ABI (see include/tdeig.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define TD_EPS 1.1102230246251565e-16  // unit roundoff 2^-53
+#define TD_SECULAR_MAXIT 64            // secular iteration cap per root
+#define TD_STATUS_NOTCONV 1
+#define TD_STATUS_LEAF 2
+#define TD_STATUS_TIMEOUT 4
+#define TD_STATUS_BADRANK 8
+
+// One merge of the DC tree (Algorithm 1): the node covers global rows
+// [g0, g0 + n); child 1 is [g0, g0 + n1), child 2 the rest.
+struct MergeDesc {
+    const double* qin1;    // child 1 eigenvectors, n1 x n1 column-major
+    const double* qin2;    // child 2 eigenvectors, n2 x n2 column-major
+    double* qout;          // this node's eigenvectors, n x n column-major
+    const double* lam_in;  // children eigenvalues (child 1 then child 2), n entries
+    double* lam_out;       // n entries, ascending
+    double* W;             // n x n workspace: sorted, deflation-rotated diag(Q1, Q2)
+    double* qhat;          // K x K workspace (capacity n x n): Cauchy-like eigenvector matrix
+    const double* scale_ptr;  // the matrix scale at roots (eigenvalues are unscaled), else NULL
+    const double* beta_ptr;   // scaled coupling b_k between the children (device)
+    int g0, n, n1;
+    int member;
+    int tile0;             // first GEMM tile of this merge in the level's tile numbering
+    int tiles_m;           // row tiles of this merge
+};
+
+struct LeafDesc {
+    double* qout;      // n x n column-major
+    double* lam_out;   // n entries
+    const double* scale_ptr;  // the matrix scale if the leaf is the whole matrix, else NULL
+    int g0, n;
+    int first, last;   // 1 if the leaf starts / ends its matrix (no split correction there)
+};
+
+// Per-level vectors indexed by global row (one entry per row of the level's
+// merges) and per-merge scalars.
+//   keep[i]    : 0 deflated; else the support of sorted column i after the
+//                deflation rotations: 1 rows of child 1 only, 2 child 2 only,
+//                3 both (rotated across the children)
+//   gemmCol[p] : survivor (secular order) placed at position p of the update
+//                product; positions [0,K1) have support 1, [K1,K1+Km) support
+//                3, [K1+Km,K) support 2, so child-1 rows need only [0,K1+Km)
+//                and child-2 rows only [K1,K)
+struct LevelWS {
+    double *dsort, *zsort, *dK, *zK, *wK, *lamK, *gamK, *muK, *uhat, *vv, *rot_c, *rot_s;
+    int *src, *keep, *survIdx, *deflIdx, *posNew, *posDefl, *rot_j, *rot_i, *gemmCol;
+    int *K, *nrot;     // per merge
+    int* kgrp;         // per merge: K1, Km
+    double* rho;       // per merge, after normalisation of z
+};
+
+// Number of kernels launched by this library (host counter, read per solve).
+extern long long g_td_launches;
+
+// Host-side launchers (kernels_dc.cu).
+void td_launch_scale_input(const double* d, const double* e, const int64_t* mrow0, const int64_t* mN,
+                           int members, double* A, double* Bc, double* scale, int64_t R,
+                           cudaStream_t st);
+void td_launch_leaf(const LeafDesc* leaves, int nleaves, const double* A, const double* Bc,
+                    int* status, cudaStream_t st);
+void td_launch_merge_level(const MergeDesc* M, int nmerge, int nmax, int rows, int total_tiles,
+                           const LevelWS& ws, int* status, int use_hss_mask, cudaStream_t st);
+void td_launch_secular(const MergeDesc* M, int nmerge, int rows, const LevelWS& ws, int* status,
+                       cudaStream_t st);
+void td_launch_lowner_cauchy(const MergeDesc* M, int nmerge, int rows, int kmax, const LevelWS& ws,
+                             int write_qhat, cudaStream_t st);
+void td_launch_update_dense(const MergeDesc* M, int nmerge, int total_tiles, const LevelWS& ws,
+                            cudaStream_t st);
+void td_launch_finish(const MergeDesc* M, int nmerge, int nmax, const LevelWS& ws, cudaStream_t st);
+void td_launch_order(const MergeDesc* M, int nmerge, const LevelWS& ws, cudaStream_t st);
+
+#define TD_GEMM_BM 64
+#define TD_GEMM_BN 64
+#define TD_GEMM_BK 16
+
+__host__ __device__ inline int td_cdiv(int a, int b) { return (a + b - 1) / b; }
+
+// Merge index owning global row g (merges sorted by g0), or -1 when g lies in
+// no merge of this level (rows of matrices whose tree has no merge here).
+__device__ inline int td_find_merge(const MergeDesc* M, int nmerge, int g)
+{
+    int lo = 0, hi = nmerge - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (M[mid].g0 <= g) lo = mid; else hi = mid - 1;
+    }
+    if (g < M[lo].g0 || g >= M[lo].g0 + M[lo].n) return -1;
+    return lo;
+}
+
+// d_k - lambda_j by Remark 1: (d_k - d_j) - gamma_j if k <= j, else
+// (d_k - d_{j+1}) + mu_j.
+__device__ __forceinline__ double td_dminus(const double* d, const double* gam, const double* mu,
+                                            int k, int j)
+{
+    return (k <= j) ? (d[k] - d[j]) - gam[j] : (d[k] - d[j + 1]) + mu[j];
+}
+
+__device__ __forceinline__ double td_warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double td_warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+void td_launch_stage_init(const LevelWS& ws, int K, double rho, cudaStream_t st);

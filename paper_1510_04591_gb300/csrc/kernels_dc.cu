@@ -1,0 +1,848 @@
+// Kernels of the divide-and-conquer merge path (Algorithm 1 of Li, Liao, Liu,
+// Jiang), batched over every merge of one level of the DC tree.  All
+// arithmetic is IEEE FP64.
+//
+//   k_scale_input   scale each matrix by max(|a|, |b|)
+//   k_leaf          QR algorithm with Wilkinson shift on each leaf (warp per leaf)
+//   k_prep          eq. T3: u from the children's Q rows; sort; deflation
+//                   (tiny z and close-pole Givens tests); compaction
+//   k_build_w       sorted diag(Q1, Q2) columns
+//   k_rotate        deflation rotations applied to those columns
+//   k_secular       Theorem 1 roots, one warp per root, with gamma/mu of Remark 1
+//   k_lowner        eq. ev_z, one warp per entry
+//   k_cauchy        eq. Ev-Q column normalisation and the Cauchy-like matrix
+//   k_order         merge of new and deflated eigenvalues (final ordering)
+//   k_gemm_f64      dense update diag(Q1, Q2) P Qhat (plain DC)
+//   k_copy_defl     deflated eigenvectors to their final columns
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+long long g_td_launches = 0;
+
+// ---------------------------------------------------------------------------
+// Input scaling: A[g] = d[g] / s_b, Bc[g] = e (row g, g+1) / s_b within member b.
+// ---------------------------------------------------------------------------
+// mrow0[0..members) are the first rows of the matrices, mrow0[members..2 members)
+// the offsets of their off-diagonals in e.
+__global__ void k_member_max(const double* d, const double* e, const int64_t* mrow0,
+                             const int64_t* mN, double* scale)
+{
+    int b = blockIdx.x;
+    int64_t r0 = mrow0[b], N = mN[b];
+    const double* db = d + r0;
+    const double* eb = e ? e + mrow0[gridDim.x + b] : nullptr;
+    double m = 0.0;
+    bool bad = false;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+        double v = db[i];
+        if (!isfinite(v)) bad = true;
+        m = fmax(m, fabs(v));
+        if (eb && i < N - 1) {
+            double w = eb[i];
+            if (!isfinite(w)) bad = true;
+            m = fmax(m, fabs(w));
+        }
+    }
+    __shared__ double red[32];
+    __shared__ int sbad;
+    if (threadIdx.x == 0) sbad = 0;
+    __syncthreads();
+    if (bad) atomicOr(&sbad, 1);
+    m = td_warp_max(m);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+        v = td_warp_max(v);
+        if (threadIdx.x == 0) scale[b] = sbad ? -1.0 : (v > 0.0 ? v : 1.0);
+    }
+}
+
+__global__ void k_scale_copy(const double* d, const double* e, const int64_t* mrow0,
+                             const int64_t* mN, int members, const double* scale, double* A,
+                             double* Bc, int64_t R)
+{
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= R) return;
+    int lo = 0, hi = members - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (mrow0[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    int b = lo;
+    double s = scale[b];
+    if (s <= 0.0) s = 1.0;
+    int64_t i = g - mrow0[b];
+    A[g] = d[g] / s;
+    Bc[g] = (e && i < mN[b] - 1) ? e[mrow0[members + b] + i] / s : 0.0;
+}
+
+void td_launch_scale_input(const double* d, const double* e, const int64_t* mrow0, const int64_t* mN,
+                           int members, double* A, double* Bc, double* scale, int64_t R,
+                           cudaStream_t st)
+{
+    k_member_max<<<members, 256, 0, st>>>(d, e, mrow0, mN, scale); g_td_launches++;
+    if (R > 0)
+        k_scale_copy<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(d, e, mrow0, mN, members, scale, A,
+                                                                 Bc, R); g_td_launches++;
+}
+
+// ---------------------------------------------------------------------------
+// Leaf solver: symmetric tridiagonal implicit QR with Wilkinson shift
+// (Algorithm 1, "use QR algorithm"), one warp per leaf of n <= 32 rows.  The
+// scalar bulge chase runs redundantly in every lane (uniform control flow);
+// lane r owns row r of Q, kept in shared memory.
+// ---------------------------------------------------------------------------
+#define LEAF_WARPS 4
+__global__ void __launch_bounds__(32 * LEAF_WARPS) k_leaf(const LeafDesc* L, int nleaves,
+                                                          const double* A, const double* Bc,
+                                                          int* status)
+{
+    __shared__ double Qs[LEAF_WARPS][32][33];
+    int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int leaf = blockIdx.x * LEAF_WARPS + wib;
+    if (leaf >= nleaves) return;
+    LeafDesc lf = L[leaf];
+    int n = lf.n, g0 = lf.g0;
+    double a[32], b[32];
+    for (int i = 0; i < n; i++) a[i] = A[g0 + i];
+    for (int i = 0; i < n - 1; i++) b[i] = Bc[g0 + i];
+    if (!lf.first) a[0] -= fabs(Bc[g0 - 1]);
+    if (!lf.last) a[n - 1] -= fabs(Bc[g0 + n - 1]);
+    double (*Q)[33] = Qs[wib];
+    for (int c = 0; c < 32; c++) Q[lane][c] = (lane == c) ? 1.0 : 0.0;
+    __syncwarp();
+
+    int sweeps = 0, fail = 0;
+    int h = n - 1;
+    while (h > 0) {
+        for (int i = 0; i < h; i++)
+            if (fabs(b[i]) <= TD_EPS * (fabs(a[i]) + fabs(a[i + 1]))) b[i] = 0.0;
+        while (h > 0 && b[h - 1] == 0.0) h--;
+        if (h == 0) break;
+        int l = h - 1;
+        while (l > 0 && b[l - 1] != 0.0) l--;
+        if (++sweeps > 30 * n) { fail = 1; break; }
+        double dd = 0.5 * (a[h - 1] - a[h]);
+        double bh = b[h - 1];
+        double sg = (dd >= 0.0) ? 1.0 : -1.0;
+        double mu = a[h] - bh * bh / (dd + sg * hypot(dd, bh));
+        double x = a[l] - mu, z = b[l];
+        for (int k = l; k < h; k++) {
+            double r = hypot(x, z);
+            double c = 1.0, s = 0.0;
+            if (r != 0.0) { c = x / r; s = -z / r; }
+            if (k > l) b[k - 1] = r;
+            double p = a[k], q = b[k], w = a[k + 1];
+            a[k] = c * c * p - 2.0 * c * s * q + s * s * w;
+            a[k + 1] = s * s * p + 2.0 * c * s * q + c * c * w;
+            b[k] = c * s * (p - w) + (c * c - s * s) * q;
+            if (k + 1 < h) {
+                double e = b[k + 1];
+                z = -s * e;
+                b[k + 1] = c * e;
+                x = b[k];
+            }
+            double qk = Q[lane][k], qk1 = Q[lane][k + 1];
+            Q[lane][k] = c * qk - s * qk1;
+            Q[lane][k + 1] = s * qk + c * qk1;
+        }
+    }
+    if (fail && lane == 0) atomicOr(status, TD_STATUS_LEAF);
+    // selection sort, ascending
+    for (int i = 0; i < n - 1; i++) {
+        int m = i;
+        for (int j = i + 1; j < n; j++) if (a[j] < a[m]) m = j;
+        if (m != i) {
+            double t = a[i]; a[i] = a[m]; a[m] = t;
+            double u = Q[lane][i]; Q[lane][i] = Q[lane][m]; Q[lane][m] = u;
+        }
+    }
+    __syncwarp();
+    if (lane < n) {
+        for (int c = 0; c < n; c++) lf.qout[(int64_t)c * n + lane] = Q[lane][c];
+        double v = 0.0;
+        for (int i = 0; i < n; i++) if (i == lane) v = a[i];
+        lf.lam_out[lane] = lf.scale_ptr ? v * (*lf.scale_ptr) : v;
+    }
+}
+
+void td_launch_leaf(const LeafDesc* leaves, int nleaves, const double* A, const double* Bc,
+                    int* status, cudaStream_t st)
+{
+    if (nleaves <= 0) return;
+    k_leaf<<<td_cdiv(nleaves, LEAF_WARPS), 32 * LEAF_WARPS, 0, st>>>(leaves, nleaves, A, Bc, status); g_td_launches++;
+}
+
+// ---------------------------------------------------------------------------
+// Block reductions / scans (blockDim.x = PREP_NT)
+// ---------------------------------------------------------------------------
+#define PREP_NT 512
+__device__ double blk_sum(double v, double* red)
+{
+    v = td_warp_sum(v);
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) r += red[i];
+    return r;
+}
+
+__device__ double blk_max(double v, double* red)
+{
+    v = td_warp_max(v);
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) r = fmax(r, red[i]);
+    return r;
+}
+
+// exclusive scan of a 0/1 flag over the block; returns prefix, *total = block total
+__device__ int blk_scan(int f, int* red, int* total)
+{
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned bal = __ballot_sync(0xffffffffu, f);
+    int pre = __popc(bal & ((1u << lane) - 1u));
+    __syncthreads();
+    if (lane == 0) red[w] = __popc(bal);
+    __syncthreads();
+    int base = 0, tot = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) {
+        if (i < w) base += red[i];
+        tot += red[i];
+    }
+    *total = tot;
+    return base + pre;
+}
+
+// ---------------------------------------------------------------------------
+// k_prep: one CTA per merge.  eq. T3 (u from Q1's last row and Q2's first row,
+// rho = |b_k|, sign folded into u), stable merge of D1 and D2, normalisation of
+// u (rho absorbs |u|^2), deflation, compaction of the survivors.
+// Deflation reading (Gu & Eisenstat): tau = 8 eps max(max|d|, rho max|z|);
+// sweep ascending against the last survivor j: rho|z_i| <= tau deflates i;
+// else with r = hypot(z_i, z_j), c = z_i/r, s = z_j/r, |(d_i - d_j) c s| <= tau
+// rotates the pair (z_j -> 0, z_i -> r) and deflates j.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(PREP_NT) k_prep(const MergeDesc* M, LevelWS ws)
+{
+    __shared__ double red[32];
+    __shared__ int ired[32];
+    __shared__ double s_tau, s_rho;
+    MergeDesc md = M[blockIdx.x];
+    const int n = md.n, n1 = md.n1, n2 = n - n1, g0 = md.g0;
+    const double* lam = md.lam_in;
+    const double beta = *md.beta_ptr;
+    const double sgn = (beta < 0.0) ? -1.0 : 1.0;
+    double zz = 0.0, dmax = 0.0, zmax = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double v = lam[i], z;
+        int r;
+        if (i < n1) {
+            int lo = 0, hi = n2;   // count of D2 < v
+            while (lo < hi) { int mid = (lo + hi) >> 1; if (lam[n1 + mid] < v) lo = mid + 1; else hi = mid; }
+            r = i + lo;
+            z = md.qin1[(int64_t)i * n1 + (n1 - 1)];
+        } else {
+            int j = i - n1;
+            int lo = 0, hi = n1;   // count of D1 <= v
+            while (lo < hi) { int mid = (lo + hi) >> 1; if (lam[mid] <= v) lo = mid + 1; else hi = mid; }
+            r = j + lo;
+            z = sgn * md.qin2[(int64_t)j * n2];
+        }
+        ws.dsort[g0 + r] = v;
+        ws.zsort[g0 + r] = z;
+        ws.src[g0 + r] = i;
+        zz += z * z;
+        dmax = fmax(dmax, fabs(v));
+        zmax = fmax(zmax, fabs(z));
+    }
+    zz = blk_sum(zz, red);
+    dmax = blk_max(dmax, red);
+    zmax = blk_max(zmax, red);
+    double nrm = sqrt(zz);
+    double rho = fabs(beta);
+    if (nrm > 0.0) {
+        rho *= nrm * nrm;
+        zmax /= nrm;
+    }
+    __syncthreads();
+    if (nrm > 0.0)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) ws.zsort[g0 + i] /= nrm;
+    if (threadIdx.x == 0) {
+        s_tau = 8.0 * TD_EPS * fmax(dmax, rho * zmax);
+        s_rho = rho;
+    }
+    __syncthreads();
+
+    // Sequential sweep by warp 0: 32 entries are prefetched per step and
+    // consumed in order through shuffles; lane 0 issues the stores.
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const double tau = s_tau;
+        int j = -1, nrot = 0, mj = 0;
+        double dj = 0.0, zj = 0.0;
+        for (int base = 0; base < n; base += 32) {
+            int idx = base + lane;
+            double dl = (idx < n) ? ws.dsort[g0 + idx] : 0.0;
+            double zl = (idx < n) ? ws.zsort[g0 + idx] : 0.0;
+            int sl = (idx < n) ? ws.src[g0 + idx] : 0;
+            int cnt = min(32, n - base);
+            for (int e = 0; e < cnt; e++) {
+                double di = __shfl_sync(0xffffffffu, dl, e);
+                double zi = __shfl_sync(0xffffffffu, zl, e);
+                int mi = (__shfl_sync(0xffffffffu, sl, e) < n1) ? 1 : 2;
+                int i = base + e;
+                if (rho * fabs(zi) <= tau) {
+                    if (lane == 0) { ws.zsort[g0 + i] = 0.0; ws.keep[g0 + i] = 0; }
+                    continue;
+                }
+                if (j < 0) {
+                    if (lane == 0) ws.keep[g0 + i] = mi;
+                    j = i; dj = di; zj = zi; mj = mi;
+                    continue;
+                }
+                double t = di - dj;
+                double r = hypot(zi, zj);
+                double c = zi / r, s = zj / r;
+                if (fabs(t * c * s) <= tau) {
+                    double djn = c * c * dj + s * s * di;
+                    double din = s * s * dj + c * c * di;
+                    if (lane == 0) {
+                        ws.dsort[g0 + j] = djn;
+                        ws.zsort[g0 + j] = 0.0;
+                        ws.keep[g0 + j] = 0;
+                        ws.rot_j[g0 + nrot] = j;
+                        ws.rot_i[g0 + nrot] = i;
+                        ws.rot_c[g0 + nrot] = c;
+                        ws.rot_s[g0 + nrot] = s;
+                    }
+                    nrot++;
+                    di = din;
+                    zi = r;
+                    mi |= mj;
+                }
+                if (lane == 0) {
+                    ws.keep[g0 + i] = mi;
+                    ws.dsort[g0 + i] = di;
+                    ws.zsort[g0 + i] = zi;
+                }
+                j = i; dj = di; zj = zi; mj = mi;
+            }
+        }
+        if (lane == 0) ws.nrot[blockIdx.x] = nrot;
+    }
+    __syncthreads();
+
+    // compaction of survivors and deflated indices
+    int run_k = 0, run_d = 0;
+    for (int base = 0; base < n; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        int f = (i < n) ? ws.keep[g0 + i] : 0;
+        int tot;
+        int pre = blk_scan(f, ired, &tot);
+        int nvalid = min((int)blockDim.x, n - base);
+        if (i < n) {
+            if (f) {
+                int k = run_k + pre;
+                double zi = ws.zsort[g0 + i];
+                ws.survIdx[g0 + k] = i;
+                ws.dK[g0 + k] = ws.dsort[g0 + i];
+                ws.zK[g0 + k] = zi;
+                ws.wK[g0 + k] = s_rho * zi * zi;
+            } else {
+                int l = run_d + ((int)threadIdx.x - pre);
+                ws.deflIdx[g0 + l] = i;
+            }
+        }
+        run_k += tot;
+        run_d += nvalid - tot;
+        __syncthreads();
+    }
+    // order of the survivors in the update product: support 1, then 3, then 2
+    const int K = run_k;
+    int c1 = 0, c3 = 0;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        int t = ws.keep[g0 + ws.survIdx[g0 + k]];
+        c1 += (t == 1);
+        c3 += (t == 3);
+    }
+    const int K1 = (int)blk_sum((double)c1, red);
+    const int Km = (int)blk_sum((double)c3, red);
+    int run1 = 0, run3 = 0, run2 = 0;
+    for (int base = 0; base < K; base += blockDim.x) {
+        int k = base + threadIdx.x;
+        int t = (k < K) ? ws.keep[g0 + ws.survIdx[g0 + k]] : 0;
+        int tot1, tot3, tot2;
+        int p1 = blk_scan(t == 1, ired, &tot1);
+        int p3 = blk_scan(t == 3, ired, &tot3);
+        int p2 = blk_scan(t == 2, ired, &tot2);
+        if (k < K) {
+            int p = (t == 1) ? run1 + p1 : (t == 3) ? K1 + run3 + p3 : K1 + Km + run2 + p2;
+            ws.gemmCol[g0 + p] = k;
+        }
+        run1 += tot1;
+        run3 += tot3;
+        run2 += tot2;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        ws.K[blockIdx.x] = K;
+        ws.rho[blockIdx.x] = s_rho;
+        ws.kgrp[2 * blockIdx.x] = K1;
+        ws.kgrp[2 * blockIdx.x + 1] = Km;
+    }
+}
+
+// W[:, c] = column src[c] of diag(Q1, Q2), for the sorted order c.
+__global__ void k_build_w(const MergeDesc* M, LevelWS ws)
+{
+    MergeDesc md = M[blockIdx.y];
+    const int n = md.n, n1 = md.n1, n2 = n - n1;
+    const int rtiles = td_cdiv(n, 256);
+    const int rt = blockIdx.x % rtiles, ct = blockIdx.x / rtiles;
+    if (ct * 32 >= n) return;
+    const int r = rt * 256 + threadIdx.x;
+    if (r >= n) return;
+    for (int cc = 0; cc < 32; cc++) {
+        int c = ct * 32 + cc;
+        if (c >= n) break;
+        // src is a permutation of [0, n) for ordered input; the clamp keeps a
+        // non-finite input (reported as TDEIG_EINVAL) from indexing outside.
+        int s = min(max(ws.src[md.g0 + c], 0), n - 1);
+        double v;
+        if (s < n1) v = (r < n1) ? md.qin1[(int64_t)s * n1 + r] : 0.0;
+        else v = (r >= n1) ? md.qin2[(int64_t)(s - n1) * n2 + (r - n1)] : 0.0;
+        md.W[(int64_t)c * n + r] = v;
+    }
+}
+
+// Deflation rotations, in sweep order, one row per thread.
+__global__ void k_rotate(const MergeDesc* M, LevelWS ws)
+{
+    MergeDesc md = M[blockIdx.y];
+    const int nrot = ws.nrot[blockIdx.y];
+    const int n = md.n, g0 = md.g0;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (nrot == 0 || r >= n) return;
+    for (int t = 0; t < nrot; t++) {
+        int j = ws.rot_j[g0 + t], i = ws.rot_i[g0 + t];
+        double c = ws.rot_c[g0 + t], s = ws.rot_s[g0 + t];
+        double qj = md.W[(int64_t)j * n + r], qi = md.W[(int64_t)i * n + r];
+        md.W[(int64_t)j * n + r] = c * qj - s * qi;
+        md.W[(int64_t)i * n + r] = s * qj + c * qi;
+    }
+}
+
+void td_launch_merge_level(const MergeDesc* M, int nmerge, int nmax, int rows, int total_tiles,
+                           const LevelWS& ws, int* status, int use_hss_mask, cudaStream_t st)
+{
+    (void)rows; (void)total_tiles; (void)status; (void)use_hss_mask;
+    k_prep<<<nmerge, PREP_NT, 0, st>>>(M, ws); g_td_launches++;
+    dim3 gw(td_cdiv(nmax, 256) * td_cdiv(nmax, 32), nmerge);
+    k_build_w<<<gw, 256, 0, st>>>(M, ws); g_td_launches++;
+    dim3 gr(td_cdiv(nmax, 128), nmerge);
+    k_rotate<<<gr, 128, 0, st>>>(M, ws); g_td_launches++;
+}
+
+// ---------------------------------------------------------------------------
+// Secular equation, one warp per root (Theorem 1).  Same iteration as the
+// oracle: origin at the nearer pole (sign of f at the midpoint), unknown
+// tau = lambda - d_origin, two-pole rational model of psi (poles <= i) and phi
+// (poles > i) fitted in value and slope (Bunch, Nielsen & Sorensen), bisection
+// when the model step leaves the bracket.  The K-term sums are lane-strided
+// and reduced with warp shuffles.
+// ---------------------------------------------------------------------------
+__device__ void secular_root_warp(const double* __restrict__ d, const double* __restrict__ w, int K,
+                                  int i, int lane, double* lam, double* gam, double* mu, int* iters)
+{
+    if (K == 1) { *lam = d[0] + w[0]; *gam = w[0]; *mu = 0.0; *iters = 0; return; }
+    const bool last = (i == K - 1);
+    int org;
+    double lo, hi;
+    if (!last) {
+        const double di = d[i];
+        const double half = 0.5 * (d[i + 1] - di);
+        double f = 0.0;
+        for (int j = lane; j < K; j += 32) f += w[j] / ((d[j] - di) - half);
+        f = 1.0 + td_warp_sum(f);
+        if (f >= 0.0) { org = i; lo = 0.0; hi = half; }
+        else { org = i + 1; lo = -half; hi = 0.0; }
+    } else {
+        double zz = 0.0;
+        for (int j = lane; j < K; j += 32) zz += w[j];
+        zz = td_warp_sum(zz);
+        org = i; lo = 0.0; hi = zz;
+    }
+    const double dorg = d[org];
+    const double deli = d[i] - dorg;
+    const double deli1 = last ? 0.0 : d[i + 1] - dorg;
+    double tau = 0.5 * (lo + hi);
+    int it;
+    for (it = 1; it <= TD_SECULAR_MAXIT; it++) {
+        double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
+        for (int j = lane; j <= i; j += 32) {
+            double q = 1.0 / ((d[j] - dorg) - tau);
+            double t = w[j] * q;
+            s1 += t; s2 += t * q;
+        }
+        for (int j = i + 1 + lane; j < K; j += 32) {
+            double q = 1.0 / ((d[j] - dorg) - tau);
+            double t = w[j] * q;
+            s3 += t; s4 += t * q;
+        }
+        const double psi = td_warp_sum(s1), dpsi = td_warp_sum(s2);
+        const double phi = td_warp_sum(s3), dphi = td_warp_sum(s4);
+        const double f = 1.0 + psi + phi;
+        const double err = 8.0 * TD_EPS * (1.0 + fabs(psi) + fabs(phi) + fabs(tau) * (dpsi + dphi));
+        if (fabs(f) <= err) break;
+        if (f > 0.0) hi = tau; else lo = tau;
+        if (hi - lo <= 4.0 * TD_EPS * fmax(fabs(lo), fabs(hi))) break;
+        const double a1 = deli - tau;
+        double step = 0.0;
+        bool ok = true;
+        if (!last) {
+            const double a2 = deli1 - tau;
+            const double E = f - dpsi * a1 - dphi * a2;
+            const double beta = E * (a1 + a2) + dpsi * a1 * a1 + dphi * a2 * a2;
+            const double c0 = a1 * a2 * f;
+            double disc = beta * beta - 4.0 * E * c0;
+            if (disc < 0.0) disc = 0.0;
+            const double den = beta + (beta >= 0.0 ? sqrt(disc) : -sqrt(disc));
+            if (den == 0.0) ok = false; else step = 2.0 * c0 / den;
+        } else {
+            const double E = f - dpsi * a1;
+            if (E == 0.0) ok = false; else step = a1 * f / E;
+        }
+        double nt = ok ? tau + step : 0.5 * (lo + hi);
+        if (!(nt > lo && nt < hi)) nt = 0.5 * (lo + hi);
+        if (nt == tau) break;
+        tau = nt;
+    }
+    *lam = dorg + tau;
+    if (last) { *gam = tau; *mu = 0.0; }
+    else if (org == i) { *gam = tau; *mu = (d[i + 1] - d[i]) - tau; }
+    else { *mu = -tau; *gam = (d[i + 1] - d[i]) + tau; }
+    *iters = it;
+}
+
+__global__ void k_secular(const MergeDesc* M, int nmerge, int rows, LevelWS ws, int* status)
+{
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= rows) return;
+    const int m = td_find_merge(M, nmerge, gw);
+    if (m < 0) return;
+    const int g0 = M[m].g0;
+    const int i = gw - g0;
+    const int K = ws.K[m];
+    if (i >= K) return;
+    double lam, gam, mu;
+    int it;
+    secular_root_warp(ws.dK + g0, ws.wK + g0, K, i, lane, &lam, &gam, &mu, &it);
+    if (lane == 0) {
+        ws.lamK[g0 + i] = lam;
+        ws.gamK[g0 + i] = gam;
+        ws.muK[g0 + i] = mu;
+        if (it > TD_SECULAR_MAXIT) atomicOr(status, TD_STATUS_NOTCONV);
+    }
+}
+
+void td_launch_secular(const MergeDesc* M, int nmerge, int rows, const LevelWS& ws, int* status,
+                       cudaStream_t st)
+{
+    if (rows <= 0) return;
+    k_secular<<<td_cdiv(rows, 8), 256, 0, st>>>(M, nmerge, rows, ws, status); g_td_launches++;
+}
+
+// ---------------------------------------------------------------------------
+// Loewner (eq. ev_z with 1/rho): uhat_i^2 = gamma_i/rho prod_{j != i}
+// (lambda_j - d_i)/(d_j - d_i), each lambda_j - d_i by Remark 1; sign of z_i.
+// One warp per i; lane-strided partial products, then a shuffle product.
+// ---------------------------------------------------------------------------
+__global__ void k_lowner(const MergeDesc* M, int nmerge, int rows, LevelWS ws)
+{
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= rows) return;
+    const int m = td_find_merge(M, nmerge, gw);
+    if (m < 0) return;
+    const int g0 = M[m].g0;
+    const int i = gw - g0;
+    const int K = ws.K[m];
+    if (i >= K) return;
+    const double* d = ws.dK + g0;
+    const double* gam = ws.gamK + g0;
+    const double* mu = ws.muK + g0;
+    const double di = d[i];
+    double p = 1.0;
+    for (int j = lane; j < K; j += 32) {
+        if (j == i) continue;
+        p *= (-td_dminus(d, gam, mu, i, j)) / (d[j] - di);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) p *= __shfl_xor_sync(0xffffffffu, p, o);
+    if (lane == 0) {
+        double u = sqrt(gam[i] / ws.rho[m] * p);
+        ws.uhat[g0 + i] = copysign(u, ws.zK[g0 + i]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Cauchy-like eigenvector matrix (eq. Ev-Q): one CTA per column j.
+//   t_k = uhat_k / (d_k - lambda_j), v_j = 1/sqrt(sum t_k^2), Qhat[k, j] = t_k v_j.
+// The column is kept in shared memory when it fits, else recomputed.
+// ---------------------------------------------------------------------------
+#define CAUCHY_NT 256
+template <bool SMEM>
+__global__ void __launch_bounds__(CAUCHY_NT) k_cauchy(const MergeDesc* M, int nmerge, int rows,
+                                                      LevelWS ws, int write_qhat)
+{
+    extern __shared__ double col[];
+    __shared__ double red[32];
+    const int gcol = blockIdx.x;
+    if (gcol >= rows) return;
+    const int m = td_find_merge(M, nmerge, gcol);
+    if (m < 0) return;
+    const MergeDesc& md = M[m];
+    const int g0 = md.g0;
+    const int j = gcol - g0;
+    const int K = ws.K[m];
+    if (j >= K) return;
+    const double* d = ws.dK + g0;
+    const double* gam = ws.gamK + g0;
+    const double* mu = ws.muK + g0;
+    const double* uh = ws.uhat + g0;
+    // write_qhat: 0 v only; 1 rows in secular order; 2 rows in the order of the
+    // update product (gemmCol), so the product reads Qhat contiguously.
+    const int* perm = (write_qhat == 2) ? ws.gemmCol + g0 : nullptr;
+    double acc = 0.0;
+    for (int p = threadIdx.x; p < K; p += blockDim.x) {
+        const int k = perm ? perm[p] : p;
+        double t = uh[k] / td_dminus(d, gam, mu, k, j);
+        if (SMEM) col[p] = t;
+        acc += t * t;
+    }
+    acc = blk_sum(acc, red);
+    const double vj = 1.0 / sqrt(acc);
+    if (threadIdx.x == 0) ws.vv[g0 + j] = vj;
+    if (!write_qhat) return;
+    double* out = md.qhat + (int64_t)j * K;
+    for (int p = threadIdx.x; p < K; p += blockDim.x) {
+        const int k = perm ? perm[p] : p;
+        double t = SMEM ? col[p] : uh[k] / td_dminus(d, gam, mu, k, j);
+        out[p] = t * vj;
+    }
+}
+
+#define CAUCHY_SMEM_MAX 200000
+void td_launch_lowner_cauchy(const MergeDesc* M, int nmerge, int rows, int kmax, const LevelWS& ws,
+                             int write_qhat, cudaStream_t st)
+{
+    if (rows <= 0) return;
+    k_lowner<<<td_cdiv(rows, 8), 256, 0, st>>>(M, nmerge, rows, ws); g_td_launches++;
+    size_t sm = (size_t)kmax * sizeof(double);
+    if (sm <= CAUCHY_SMEM_MAX) {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_cauchy<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 CAUCHY_SMEM_MAX);
+            attr = true;
+        }
+        k_cauchy<true><<<rows, CAUCHY_NT, sm, st>>>(M, nmerge, rows, ws, write_qhat); g_td_launches++;
+    } else {
+        k_cauchy<false><<<rows, CAUCHY_NT, 0, st>>>(M, nmerge, rows, ws, write_qhat); g_td_launches++;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Final ordering: new eigenvalues lambda (ascending) and deflated d merged into
+// ascending order, new ones first on ties (stable).  Positions feed the GEMM
+// epilogue and the deflated-column copy.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(PREP_NT) k_order(const MergeDesc* M, LevelWS ws)
+{
+    __shared__ double red[32];
+    MergeDesc md = M[blockIdx.x];
+    const int n = md.n, g0 = md.g0;
+    const int K = ws.K[blockIdx.x];
+    const int nd = n - K;
+    const int* dfl = ws.deflIdx + g0;
+    const double* ds = ws.dsort + g0;
+    const double* lk = ws.lamK + g0;
+    // are the deflated values ascending?
+    double bad = 0.0;
+    for (int l = threadIdx.x; l + 1 < nd; l += blockDim.x)
+        if (ds[dfl[l + 1]] < ds[dfl[l]]) bad = 1.0;
+    const bool sorted = blk_max(bad, red) == 0.0;
+    const double scale = md.scale_ptr ? *md.scale_ptr : 1.0;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        double v = lk[k];
+        int cnt = 0;
+        if (sorted) {
+            int lo = 0, hi = nd;
+            while (lo < hi) { int mid = (lo + hi) >> 1; if (ds[dfl[mid]] < v) lo = mid + 1; else hi = mid; }
+            cnt = lo;
+        } else {
+            for (int l = 0; l < nd; l++) cnt += (ds[dfl[l]] < v);
+        }
+        ws.posNew[g0 + k] = k + cnt;
+        md.lam_out[k + cnt] = v * scale;
+    }
+    for (int l = threadIdx.x; l < nd; l += blockDim.x) {
+        double v = ds[dfl[l]];
+        int lo = 0, hi = K;   // count of new <= v
+        while (lo < hi) { int mid = (lo + hi) >> 1; if (lk[mid] <= v) lo = mid + 1; else hi = mid; }
+        int rank = l;
+        if (!sorted) {
+            rank = 0;
+            for (int q = 0; q < nd; q++) {
+                double u = ds[dfl[q]];
+                rank += (u < v) || (u == v && q < l);
+            }
+        }
+        ws.posDefl[g0 + l] = rank + lo;
+        md.lam_out[rank + lo] = v * scale;
+    }
+}
+
+__global__ void k_copy_defl(const MergeDesc* M, LevelWS ws)
+{
+    MergeDesc md = M[blockIdx.y];
+    const int n = md.n, g0 = md.g0;
+    const int nd = n - ws.K[blockIdx.y];
+    const int rtiles = td_cdiv(n, 256);
+    const int rt = blockIdx.x % rtiles, ct = blockIdx.x / rtiles;
+    if (ct * 32 >= nd) return;
+    const int r = rt * 256 + threadIdx.x;
+    if (r >= n) return;
+    for (int cc = 0; cc < 32; cc++) {
+        int l = ct * 32 + cc;
+        if (l >= nd) break;
+        md.qout[(int64_t)ws.posDefl[g0 + l] * n + r] = md.W[(int64_t)ws.deflIdx[g0 + l] * n + r];
+    }
+}
+
+void td_launch_finish(const MergeDesc* M, int nmerge, int nmax, const LevelWS& ws, cudaStream_t st)
+{
+    dim3 g(td_cdiv(nmax, 256) * td_cdiv(nmax, 32), nmerge);
+    k_copy_defl<<<g, 256, 0, st>>>(M, ws); g_td_launches++;
+}
+
+// ---------------------------------------------------------------------------
+// Dense update (plain DC): C = W[:, surv] * Qhat, C column k written to the
+// output column posNew[k].  FP64 on the CUDA cores: a 64 x 64 x 16 shared-
+// memory tile, 4 x 4 outputs per thread (rows tx + 16 a, cols ty + 16 b).
+// On this part FP64 FMA issue (~1.2 TFLOP/s measured) is at least as fast as
+// the FP64 mma.sync path (~1.05 TFLOP/s measured), so the SIMT form is used.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_gemm_f64(const MergeDesc* M, int nmerge, LevelWS ws)
+{
+    __shared__ double As[TD_GEMM_BK][TD_GEMM_BM];
+    __shared__ double Bs[TD_GEMM_BK][TD_GEMM_BN + 1];
+    int lo = 0, hi = nmerge - 1;
+    const int bid = blockIdx.x;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (M[mid].tile0 <= bid) lo = mid; else hi = mid - 1;
+    }
+    const MergeDesc& md = M[lo];
+    const int m = lo;
+    const int n = md.n, g0 = md.g0;
+    const int K = ws.K[m];
+    const int local = bid - md.tile0;
+    const int tm = local % md.tiles_m, tn = local / md.tiles_m;
+    const int row0 = tm * TD_GEMM_BM, col0 = tn * TD_GEMM_BN;
+    if (col0 >= K || K == 0) return;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int* surv = ws.survIdx + g0;
+    const int* gcol = ws.gemmCol + g0;
+    const double* W = md.W;
+    const double* B = md.qhat;   // rows already in product order
+    // Block structure of diag(Q1, Q2) after deflation: child-1 rows see only
+    // product positions [0, K1 + Km), child-2 rows only [K1, K).
+    const int K1 = ws.kgrp[2 * m], Km = ws.kgrp[2 * m + 1];
+    const int kbeg = (row0 >= md.n1) ? K1 : 0;
+    const int kend = (row0 + TD_GEMM_BM <= md.n1) ? K1 + Km : K;
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++) acc[a][b] = 0.0;
+
+    for (int k0 = kbeg; k0 < kend; k0 += TD_GEMM_BK) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            int idx = threadIdx.x + 256 * q;
+            int kk = idx >> 6, r = idx & 63;
+            int k = k0 + kk, row = row0 + r;
+            As[kk][r] = (k < kend && row < n) ? W[(int64_t)surv[gcol[k]] * n + row] : 0.0;
+            int kb = idx & 15, c = idx >> 4;
+            int kg = k0 + kb, cg = col0 + c;
+            Bs[kb][c] = (kg < kend && cg < K) ? B[(int64_t)cg * K + kg] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TD_GEMM_BK; kk++) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; a++) av[a] = As[kk][tx + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; b++) bv[b] = Bs[kk][ty + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; a++)
+#pragma unroll
+                for (int b = 0; b < 4; b++) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+        int c = col0 + ty + 16 * b;
+        if (c >= K) continue;
+        double* out = md.qout + (int64_t)ws.posNew[g0 + c] * n;
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+            int r = row0 + tx + 16 * a;
+            if (r < n) out[r] = acc[a][b];
+        }
+    }
+}
+
+void td_launch_update_dense(const MergeDesc* M, int nmerge, int total_tiles, const LevelWS& ws,
+                            cudaStream_t st)
+{
+    if (total_tiles <= 0) return;
+    k_gemm_f64<<<total_tiles, 256, 0, st>>>(M, nmerge, ws); g_td_launches++;
+}
+
+// Order kernel launcher (separate so the HSS path can reuse it).
+void td_launch_order(const MergeDesc* M, int nmerge, const LevelWS& ws, cudaStream_t st)
+{
+    k_order<<<nmerge, PREP_NT, 0, st>>>(M, ws); g_td_launches++;
+}
+
+// Stage entry points: one rank-one problem of size K placed as merge 0.
+__global__ void k_stage_init(LevelWS ws, int K, double rho)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) { ws.K[0] = K; ws.rho[0] = rho; ws.nrot[0] = 0; }
+    if (i < K) {
+        double z = ws.zK[i];
+        ws.wK[i] = rho * z * z;
+    }
+}
+
+void td_launch_stage_init(const LevelWS& ws, int K, double rho, cudaStream_t st)
+{
+    k_stage_init<<<td_cdiv(std::max(K, 1), 256), 256, 0, st>>>(ws, K, rho); g_td_launches++;
+}

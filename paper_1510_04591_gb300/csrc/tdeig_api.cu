@@ -1,0 +1,723 @@
+// Host side of the C ABI declared in include/tdeig.h: validation, the DC-tree
+// plan (Algorithm 1), device workspace, and the per-level launch sequence.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <string>
+#include <vector>
+
+#include "../../include/tdeig.h"
+#include "common.cuh"
+#include "hss.cuh"
+
+struct LevelPlan {
+    std::vector<MergeDesc> merges;
+    int nmax = 0, rows = 0, tiles = 0, kmax = 0;
+    size_t desc_off = 0;  // index of the first descriptor in the device array
+};
+
+struct Plan {
+    int members = 0;
+    std::vector<int64_t> N, row0, q0;
+    int64_t R = 0, Qsz = 0;
+    std::vector<LeafDesc> leaves;
+    std::vector<LevelPlan> levels;  // index h-1 for height h
+    std::vector<int64_t> qoff_total;  // per height: compact size of all blocks
+};
+
+struct tdeig_ctx {
+    tdeig_options opt;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    std::string stats;
+    std::vector<cudaEvent_t> events;   // stage timing events, reused across solves
+    std::vector<const char*> ev_names;
+    std::vector<int> ev_level;
+};
+
+static const char* kStatusMsg[] = {
+    "success",
+    "invalid argument",
+    "device memory allocation failed",
+    "CUDA error",
+    "iteration did not converge",
+    "bounded device wait expired",
+    "not implemented"};
+
+extern "C" const char* tdeig_strerror(int status)
+{
+    int i = -status;
+    if (i < 0 || i > 6) return "unknown status";
+    return kStatusMsg[i];
+}
+
+extern "C" void tdeig_default_options(tdeig_options* o)
+{
+    if (!o) return;
+    o->leaf = 32;
+    o->hss_threshold = 2000;
+    o->hss_leaf = 128;
+    o->tol = 1e-12;
+    o->oversample = 10;
+    o->rank_eps = 1e-16;
+    o->rank_cap = 100;
+    o->boundary_shift = 5;
+    o->seed = 0x5eed1510ull;
+    o->cuda_stream = nullptr;
+}
+
+static bool options_ok(const tdeig_options& o)
+{
+    return o.leaf >= 2 && o.leaf <= 32 && o.hss_threshold >= 0 && o.hss_leaf >= 16 &&
+           o.hss_leaf <= 512 && o.tol > 0.0 && o.tol < 1.0 && o.oversample >= 0 &&
+           o.oversample <= 64 && o.rank_eps > 0.0 && o.rank_eps < 1.0 && o.rank_cap >= 1 &&
+           o.rank_cap <= 256 && o.boundary_shift >= 0 && o.boundary_shift <= 64;
+}
+
+extern "C" int tdeig_create(tdeig_handle* out, const tdeig_options* opt)
+{
+    if (!out) return TDEIG_EINVAL;
+    *out = nullptr;
+    tdeig_options o;
+    tdeig_default_options(&o);
+    if (opt) o = *opt;
+    if (!options_ok(o)) return TDEIG_EINVAL;
+    tdeig_ctx* h = new tdeig_ctx();
+    h->opt = o;
+    if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return TDEIG_ECUDA; }
+    if (o.cuda_stream) {
+        h->stream = (cudaStream_t)o.cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete h;
+            return TDEIG_ECUDA;
+        }
+        h->own_stream = true;
+    }
+    *out = h;
+    return TDEIG_OK;
+}
+
+extern "C" int tdeig_destroy(tdeig_handle h)
+{
+    if (!h) return TDEIG_EINVAL;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->ws) cudaFree(h->ws);
+    for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return TDEIG_OK;
+}
+
+extern "C" int tdeig_last_stats(tdeig_handle h, char* buf, size_t len)
+{
+    if (!h) return TDEIG_EINVAL;
+    if (buf && len > 0) {
+        size_t c = std::min(len - 1, h->stats.size());
+        memcpy(buf, h->stats.data(), c);
+        buf[c] = 0;
+    }
+    return (int)h->stats.size();
+}
+
+// ---------------------------------------------------------------------------
+// Pointer classification and workspace
+// ---------------------------------------------------------------------------
+static bool is_device_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct Arena {
+    char* base;
+    size_t off = 0;
+    size_t cap;
+    template <class T> T* take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T* p = (T*)(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+static int ensure_ws(tdeig_ctx* h, size_t bytes)
+{
+    if (bytes <= h->ws_bytes) return TDEIG_OK;
+    if (h->ws) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(h->ws);
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+    }
+    size_t want = bytes + bytes / 8;
+    if (cudaMalloc(&h->ws, want) != cudaSuccess) {
+        cudaGetLastError();
+        return TDEIG_ENOMEM;
+    }
+    h->ws_bytes = want;
+    return TDEIG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// DC tree plan.  Every matrix of size N is split with k = floor(n/2) down to a
+// uniform depth D = min{t : ceil(N / 2^t) <= leaf}; nodes at depth D are
+// leaves.  A merge at depth t has height D - t; all merges of one height (over
+// all matrices) form one level and run in one launch per stage.
+// ---------------------------------------------------------------------------
+static int tree_depth(int64_t N, int leaf)
+{
+    int D = 0;
+    while ((N + ((int64_t)1 << D) - 1) / ((int64_t)1 << D) > leaf) D++;
+    return D;
+}
+
+struct NodeOut {
+    double* q;
+    double* lam;
+};
+
+struct Bufs {
+    double *P[2], *W, *QH, *LP[2], *Qfinal, *Lfinal, *A, *Bc, *scale;
+};
+
+static NodeOut plan_node(Plan& P, const Bufs& B, int b, int64_t off, int64_t n, int depth, int D,
+                         std::vector<int64_t>& qoff)
+{
+    const int h = D - depth;
+    const int64_t g0 = P.row0[b] + off;
+    NodeOut out;
+    const bool root = (depth == 0);
+    int64_t mine = qoff[h];
+    qoff[h] += n * n;
+    if (root) {
+        out.q = B.Qfinal + P.q0[b];
+        out.lam = B.Lfinal + g0;
+    } else {
+        out.q = B.P[h & 1] + mine;
+        out.lam = B.LP[h & 1] + g0;
+    }
+    if (h == 0) {
+        LeafDesc lf;
+        lf.qout = out.q;
+        lf.lam_out = out.lam;
+        lf.scale_ptr = root ? B.scale + b : nullptr;
+        lf.g0 = (int)g0;
+        lf.n = (int)n;
+        lf.first = (off == 0);
+        lf.last = (off + n == P.N[b]);
+        P.leaves.push_back(lf);
+        return out;
+    }
+    const int64_t k = n / 2;
+    NodeOut c1 = plan_node(P, B, b, off, k, depth + 1, D, qoff);
+    NodeOut c2 = plan_node(P, B, b, off + k, n - k, depth + 1, D, qoff);
+    MergeDesc md;
+    memset(&md, 0, sizeof(md));
+    md.qin1 = c1.q;
+    md.qin2 = c2.q;
+    md.qout = out.q;
+    md.lam_in = c1.lam;
+    md.lam_out = out.lam;
+    md.W = B.W + mine;
+    md.qhat = B.QH + mine;
+    md.scale_ptr = root ? B.scale + b : nullptr;
+    md.beta_ptr = B.Bc + g0 + k - 1;
+    md.g0 = (int)g0;
+    md.n = (int)n;
+    md.n1 = (int)k;
+    md.member = b;
+    P.levels[h - 1].merges.push_back(md);
+    return out;
+}
+
+static void build_plan(Plan& P, const Bufs& B, int leaf)
+{
+    int H = 0;
+    std::vector<int> D(P.members);
+    for (int b = 0; b < P.members; b++) {
+        D[b] = tree_depth(P.N[b], leaf);
+        H = std::max(H, D[b]);
+    }
+    P.levels.assign(H, LevelPlan());
+    P.leaves.clear();
+    std::vector<int64_t> qoff(H + 1, 0);
+    for (int b = 0; b < P.members; b++)
+        if (P.N[b] > 0) plan_node(P, B, b, 0, P.N[b], 0, D[b], qoff);
+    size_t desc = 0;
+    for (auto& L : P.levels) {
+        std::sort(L.merges.begin(), L.merges.end(),
+                  [](const MergeDesc& x, const MergeDesc& y) { return x.g0 < y.g0; });
+        int tiles = 0;
+        L.rows = 0;
+        L.nmax = 0;
+        for (auto& m : L.merges) {
+            m.tile0 = tiles;
+            m.tiles_m = td_cdiv(m.n, TD_GEMM_BM);
+            tiles += m.tiles_m * td_cdiv(m.n, TD_GEMM_BN);
+            L.rows = std::max(L.rows, m.g0 + m.n);
+            L.nmax = std::max(L.nmax, m.n);
+        }
+        L.tiles = tiles;
+        L.kmax = L.nmax;
+        L.desc_off = desc;
+        desc += L.merges.size();
+    }
+    P.qoff_total = qoff;
+}
+
+static size_t level_ws_bytes(int64_t R, int64_t Mmax)
+{
+    return (size_t)R * (12 * sizeof(double) + 9 * sizeof(int)) + Mmax * (4 * sizeof(int) + 8) +
+           32 * 256;
+}
+
+static void carve_level_ws(Arena& a, LevelWS& w, int64_t R, int64_t Mmax)
+{
+    w.dsort = a.take<double>(R);
+    w.zsort = a.take<double>(R);
+    w.dK = a.take<double>(R);
+    w.zK = a.take<double>(R);
+    w.wK = a.take<double>(R);
+    w.lamK = a.take<double>(R);
+    w.gamK = a.take<double>(R);
+    w.muK = a.take<double>(R);
+    w.uhat = a.take<double>(R);
+    w.vv = a.take<double>(R);
+    w.rot_c = a.take<double>(R);
+    w.rot_s = a.take<double>(R);
+    w.src = a.take<int>(R);
+    w.keep = a.take<int>(R);
+    w.survIdx = a.take<int>(R);
+    w.deflIdx = a.take<int>(R);
+    w.posNew = a.take<int>(R);
+    w.posDefl = a.take<int>(R);
+    w.rot_j = a.take<int>(R);
+    w.rot_i = a.take<int>(R);
+    w.gemmCol = a.take<int>(R);
+    w.K = a.take<int>(Mmax);
+    w.nrot = a.take<int>(Mmax);
+    w.kgrp = a.take<int>(2 * Mmax);
+    w.rho = a.take<double>(Mmax);
+}
+
+// Statistics of the last solve: per level the merge sizes n, n1, deflated sizes
+// K and the support split (K1, Km), per stage the device time from the events.
+static std::string stats_json(tdeig_ctx* h, const Plan& P, const std::vector<int>& kh,
+                              const std::vector<int>& gh, const std::string& hss_js, double secs,
+                              int status)
+{
+    std::string js = "{\"levels\":[";
+    char buf[256];
+    bool firstL = true;
+    for (size_t li = 0; li < P.levels.size(); li++) {
+        const LevelPlan& L = P.levels[li];
+        if (L.merges.empty()) continue;
+        js += firstL ? "{" : ",{";
+        firstL = false;
+        snprintf(buf, sizeof(buf), "\"height\":%d,\"merges\":[", (int)li + 1);
+        js += buf;
+        for (size_t m = 0; m < L.merges.size(); m++) {
+            size_t q = L.desc_off + m;
+            snprintf(buf, sizeof(buf), "%s[%d,%d,%d,%d,%d]", m ? "," : "", L.merges[m].n,
+                     L.merges[m].n1, kh[q], gh[2 * q], gh[2 * q + 1]);
+            js += buf;
+        }
+        js += "],\"ms\":{";
+        bool firstS = true;
+        for (size_t e = 0; e + 1 < h->ev_names.size(); e++) {
+            if (h->ev_level[e] != (int)li + 1) continue;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, h->events[e], h->events[e + 1]);
+            snprintf(buf, sizeof(buf), "%s\"%s\":%.6f", firstS ? "" : ",", h->ev_names[e], ms);
+            js += buf;
+            firstS = false;
+        }
+        js += "}}";
+    }
+    js += "],\"stage_ms\":{";
+    // totals per stage name
+    std::vector<std::pair<std::string, double>> tot;
+    for (size_t e = 0; e + 1 < h->ev_names.size(); e++) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->events[e], h->events[e + 1]);
+        bool found = false;
+        for (auto& t : tot)
+            if (t.first == h->ev_names[e]) { t.second += ms; found = true; }
+        if (!found) tot.push_back({h->ev_names[e], ms});
+    }
+    for (size_t i = 0; i < tot.size(); i++) {
+        snprintf(buf, sizeof(buf), "%s\"%s\":%.6f", i ? "," : "", tot[i].first.c_str(), tot[i].second);
+        js += buf;
+    }
+    float all = 0.f;
+    if (h->ev_names.size() >= 2)
+        cudaEventElapsedTime(&all, h->events[0], h->events[h->ev_names.size() - 1]);
+    snprintf(buf, sizeof(buf), "},\"device_ms\":%.6f,\"seconds\":%.6f,\"status\":%d", all, secs,
+             status);
+    js += buf;
+    if (!hss_js.empty()) js += ",\"hss\":[" + hss_js + "]";
+    js += "}";
+    return js;
+}
+
+#define CU(x)                                                     \
+    do {                                                          \
+        cudaError_t e_ = (x);                                     \
+        if (e_ != cudaSuccess) {                                  \
+            fprintf(stderr, "tdeig: %s (%s:%d)\n", cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return TDEIG_ECUDA;                                   \
+        }                                                         \
+    } while (0)
+
+static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const double* d,
+                      const double* e, double* lam_out, double* Q_out, int mode)
+{
+    const cudaStream_t st = h->stream;
+    const int leaf = h->opt.leaf;
+    const int variant = mode & TDEIG_MODE_MASK;
+    const int prec = mode & TDEIG_PREC_MASK;
+    if (variant > TDEIG_MODE_ADC2 || (mode & ~(TDEIG_MODE_MASK | TDEIG_PREC_MASK))) return TDEIG_EINVAL;
+    if (prec != TDEIG_PREC_FP64 && prec != TDEIG_PREC_SPLIT) return TDEIG_EINVAL;
+    auto t_start = std::chrono::steady_clock::now();
+    const long long launches0 = g_td_launches;
+
+    Plan P;
+    P.members = (int)batch;
+    P.N.assign(N_each, N_each + batch);
+    P.row0.resize(batch);
+    P.q0.resize(batch);
+    int64_t R = 0, Qsz = 0, Esz = 0;
+    for (int64_t b = 0; b < batch; b++) {
+        if (N_each[b] < 0 || N_each[b] > (int64_t)1 << 20) return TDEIG_EINVAL;
+        P.row0[b] = R;
+        P.q0[b] = Qsz;
+        R += N_each[b];
+        Qsz += N_each[b] * N_each[b];
+        Esz += N_each[b] > 0 ? N_each[b] - 1 : 0;
+    }
+    if (R == 0) return TDEIG_OK;
+    if (R > ((int64_t)1 << 30)) return TDEIG_EINVAL;
+    P.R = R;
+    P.Qsz = Qsz;
+
+    const bool d_dev = is_device_ptr(d), e_dev = is_device_ptr(e);
+    const bool l_dev = is_device_ptr(lam_out), q_dev = Q_out && is_device_ptr(Q_out);
+
+    // Worst-case number of merges on one level: bounded by the number of leaves.
+    int64_t Mmax = 0;
+    for (int64_t b = 0; b < batch; b++) {
+        int D = tree_depth(N_each[b], leaf);
+        Mmax += D > 0 ? ((int64_t)1 << (D - 1)) : 0;
+    }
+    Mmax = std::max<int64_t>(Mmax, 1);
+    int64_t leaves_max = 0;
+    for (int64_t b = 0; b < batch; b++) leaves_max += (int64_t)1 << tree_depth(N_each[b], leaf);
+
+    // Workspace size
+    size_t bytes = 0;
+    bytes += 4 * (size_t)Qsz * sizeof(double);          // P0, P1, W, QH
+    bytes += (q_dev ? 0 : (size_t)Qsz * sizeof(double)); // staging for Q
+    bytes += 5 * (size_t)R * sizeof(double);            // LP0, LP1, A, Bc, staging lambda
+    bytes += 2 * (size_t)R * sizeof(double);            // staging d, e
+    bytes += level_ws_bytes(R, Mmax);
+    bytes += (size_t)batch * (3 * sizeof(int64_t) + sizeof(double));
+    bytes += (size_t)(Mmax * 64) * (sizeof(MergeDesc) + 3 * sizeof(int)) +
+             (size_t)leaves_max * sizeof(LeafDesc);
+    bytes += hss_ws_bytes(h->opt, Qsz, R, variant != TDEIG_MODE_DENSE);
+    bytes += 64 * 1024;
+    int rc = ensure_ws(h, bytes);
+    if (rc) return rc;
+
+    Arena ar{h->ws, 0, h->ws_bytes};
+    Bufs B;
+    B.P[0] = ar.take<double>(Qsz);
+    B.P[1] = ar.take<double>(Qsz);
+    B.W = ar.take<double>(Qsz);
+    B.QH = ar.take<double>(Qsz);
+    B.Qfinal = q_dev ? Q_out : ar.take<double>(Qsz);
+    B.LP[0] = ar.take<double>(R);
+    B.LP[1] = ar.take<double>(R);
+    B.A = ar.take<double>(R);
+    B.Bc = ar.take<double>(R);
+    B.Lfinal = l_dev ? lam_out : ar.take<double>(R);
+    double* d_st = d_dev ? (double*)d : ar.take<double>(R);
+    double* e_st = (e_dev || !e) ? (double*)e : ar.take<double>(R);
+    int64_t* dev_row0 = ar.take<int64_t>(2 * batch);   // first rows, then e offsets
+    int64_t* dev_N = ar.take<int64_t>(batch);
+    B.scale = ar.take<double>(batch);
+    int* status = ar.take<int>(64);
+    LevelWS lws;
+    carve_level_ws(ar, lws, R, Mmax);
+    HssWS hws;
+    hss_carve_ws(ar, hws, h->opt, Qsz, R, variant != TDEIG_MODE_DENSE);
+
+    build_plan(P, B, leaf);
+    size_t ndesc = 0;
+    for (auto& L : P.levels) ndesc += L.merges.size();
+    MergeDesc* dev_desc = ar.take<MergeDesc>(std::max<size_t>(ndesc, 1));
+    LeafDesc* dev_leaf = ar.take<LeafDesc>(std::max<size_t>(P.leaves.size(), 1));
+    int* kstat = ar.take<int>(std::max<size_t>(ndesc, 1));       // K of every merge
+    int* gstat = ar.take<int>(2 * std::max<size_t>(ndesc, 1));   // K1, Km of every merge
+    if (ar.off > ar.cap) return TDEIG_ENOMEM;
+
+    std::vector<MergeDesc> all;
+    all.reserve(ndesc);
+    for (auto& L : P.levels) all.insert(all.end(), L.merges.begin(), L.merges.end());
+
+    // Uploads (host inputs are staged)
+    if (!d_dev) CU(cudaMemcpyAsync(d_st, d, R * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (e && !e_dev && Esz > 0)
+        CU(cudaMemcpyAsync(e_st, e, Esz * sizeof(double), cudaMemcpyHostToDevice, st));
+    std::vector<int64_t> rowe(2 * batch);
+    for (int64_t b = 0, eo = 0; b < batch; b++) {
+        rowe[b] = P.row0[b];
+        rowe[batch + b] = eo;
+        eo += N_each[b] > 0 ? N_each[b] - 1 : 0;
+    }
+    CU(cudaMemcpyAsync(dev_row0, rowe.data(), 2 * batch * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(dev_N, P.N.data(), batch * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    if (ndesc)
+        CU(cudaMemcpyAsync(dev_desc, all.data(), ndesc * sizeof(MergeDesc), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(dev_leaf, P.leaves.data(), P.leaves.size() * sizeof(LeafDesc),
+                       cudaMemcpyHostToDevice, st));
+    CU(cudaMemsetAsync(status, 0, 64 * sizeof(int), st));
+
+    // Stage timing: an event before each stage and one at the end, on the
+    // handle's stream; read after the final synchronisation.
+    h->ev_names.clear();
+    h->ev_level.clear();
+    auto mark = [&](const char* name, int level) -> int {
+        size_t i = h->ev_names.size();
+        if (i >= h->events.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return TDEIG_ECUDA;
+            h->events.push_back(e);
+        }
+        h->ev_names.push_back(name);
+        h->ev_level.push_back(level);
+        return cudaEventRecord(h->events[i], st) == cudaSuccess ? TDEIG_OK : TDEIG_ECUDA;
+    };
+#define MARK(name, lv) do { if ((rc = mark(name, lv))) return rc; } while (0)
+
+    MARK("scale", -1);
+    td_launch_scale_input(d_st, Esz > 0 ? e_st : nullptr, dev_row0, dev_N, (int)batch, B.A, B.Bc,
+                          B.scale, R, st);
+    MARK("leaf", -1);
+    td_launch_leaf(dev_leaf, (int)P.leaves.size(), B.A, B.Bc, status, st);
+    CU(cudaGetLastError());
+
+    std::string hss_js;
+    for (size_t li = 0; li < P.levels.size(); li++) {
+        LevelPlan& L = P.levels[li];
+        const int nm = (int)L.merges.size();
+        if (nm == 0) continue;
+        const int lv = (int)li + 1;
+        const MergeDesc* Md = dev_desc + L.desc_off;
+        MARK("prep", lv);
+        td_launch_merge_level(Md, nm, L.nmax, L.rows, L.tiles, lws, status, 0, st);
+        CU(cudaMemcpyAsync(kstat + L.desc_off, lws.K, nm * sizeof(int), cudaMemcpyDeviceToDevice, st));
+        CU(cudaMemcpyAsync(gstat + 2 * L.desc_off, lws.kgrp, 2 * nm * sizeof(int),
+                           cudaMemcpyDeviceToDevice, st));
+        MARK("secular", lv);
+        td_launch_secular(Md, nm, L.rows, lws, status, st);
+        bool any_hss = false;
+        std::vector<int> Kh;
+        if (variant != TDEIG_MODE_DENSE && L.nmax > h->opt.hss_threshold) {
+            Kh.resize(nm);
+            CU(cudaMemcpyAsync(Kh.data(), lws.K, nm * sizeof(int), cudaMemcpyDeviceToHost, st));
+            CU(cudaStreamSynchronize(st));
+            for (int i = 0; i < nm; i++) any_hss |= Kh[i] > h->opt.hss_threshold;
+        }
+        MARK("lowner_cauchy", lv);
+        td_launch_lowner_cauchy(Md, nm, L.rows, L.kmax, lws, any_hss ? 1 : 2, st);
+        MARK("order", lv);
+        td_launch_order(Md, nm, lws, st);
+        MARK(any_hss ? "hss_update" : "update", lv);
+        if (any_hss) {
+            rc = hss_update_level(h->opt, variant, prec, L.merges, Md, Kh, lws, hws, status, st, hss_js);
+            if (rc) return rc;
+        } else {
+            td_launch_update_dense(Md, nm, L.tiles, lws, st);
+        }
+        MARK("finish", lv);
+        td_launch_finish(Md, nm, L.nmax, lws, st);
+        CU(cudaGetLastError());
+    }
+    MARK("end", -1);
+#undef MARK
+
+    if (!l_dev) CU(cudaMemcpyAsync(lam_out, B.Lfinal, R * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (Q_out && !q_dev)
+        CU(cudaMemcpyAsync(Q_out, B.Qfinal, Qsz * sizeof(double), cudaMemcpyDeviceToHost, st));
+    int hstat[2] = {0, 0};
+    CU(cudaMemcpyAsync(hstat, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    std::vector<int> kh(std::max<size_t>(ndesc, 1)), gh(2 * std::max<size_t>(ndesc, 1));
+    if (ndesc) {
+        CU(cudaMemcpyAsync(kh.data(), kstat, ndesc * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(gh.data(), gstat, 2 * ndesc * sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
+    CU(cudaStreamSynchronize(st));
+    CU(cudaGetLastError());
+    std::vector<double> sc(batch);
+    CU(cudaMemcpy(sc.data(), B.scale, batch * sizeof(double), cudaMemcpyDeviceToHost));
+    double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    h->stats = stats_json(h, P, kh, gh, hss_js, secs, hstat[0]);
+    {
+        char lb[64];
+        snprintf(lb, sizeof(lb), ",\"launches\":%lld}", g_td_launches - launches0);
+        h->stats.pop_back();
+        h->stats += lb;
+    }
+    for (int64_t b = 0; b < batch; b++)
+        if (sc[b] < 0.0) return TDEIG_EINVAL;
+    if (hstat[0] & TD_STATUS_TIMEOUT) return TDEIG_ETIMEOUT;
+    if (hstat[0] & (TD_STATUS_NOTCONV | TD_STATUS_LEAF)) return TDEIG_ENOTCONV;
+    return TDEIG_OK;
+}
+
+extern "C" int tdeig_solve(tdeig_handle h, const double* d, const double* e, int64_t N,
+                           double* lambda_out, double* Q_out, int mode)
+{
+    if (!h || N < 0) return TDEIG_EINVAL;
+    if (N == 0) return TDEIG_OK;
+    if (!d || !lambda_out || (N > 1 && !e)) return TDEIG_EINVAL;
+    CU(cudaSetDevice(h->device));
+    return solve_impl(h, 1, &N, d, N > 1 ? e : nullptr, lambda_out, Q_out, mode);
+}
+
+extern "C" int tdeig_solve_batched(tdeig_handle h, int64_t batch, const int64_t* N_each,
+                                   const double* d_cat, const double* e_cat, double* lambda_cat,
+                                   double* Q_cat, int mode)
+{
+    if (!h || batch < 0 || (batch > 0 && !N_each)) return TDEIG_EINVAL;
+    if (batch == 0) return TDEIG_OK;
+    int64_t R = 0, E = 0;
+    for (int64_t b = 0; b < batch; b++) {
+        if (N_each[b] < 0) return TDEIG_EINVAL;
+        R += N_each[b];
+        E += N_each[b] > 0 ? N_each[b] - 1 : 0;
+    }
+    if (R == 0) return TDEIG_OK;
+    if (!d_cat || !lambda_cat || (E > 0 && !e_cat)) return TDEIG_EINVAL;
+    CU(cudaSetDevice(h->device));
+    return solve_impl(h, batch, N_each, d_cat, E > 0 ? e_cat : nullptr, lambda_cat, Q_cat, mode);
+}
+
+// ---------------------------------------------------------------------------
+// Stage entry points
+// ---------------------------------------------------------------------------
+static int copy_in(double* dst, const double* src, int64_t n, cudaStream_t st)
+{
+    if (!src || n <= 0) return TDEIG_OK;
+    cudaMemcpyKind k = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CU(cudaMemcpyAsync(dst, src, n * sizeof(double), k, st));
+    return TDEIG_OK;
+}
+
+static int copy_out(double* dst, const double* src, int64_t n, cudaStream_t st)
+{
+    if (!dst || n <= 0) return TDEIG_OK;
+    cudaMemcpyKind k = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CU(cudaMemcpyAsync(dst, src, n * sizeof(double), k, st));
+    return TDEIG_OK;
+}
+
+static int stage_setup(tdeig_ctx* h, int64_t K, int64_t qelems, Arena& ar, LevelWS& lws,
+                       MergeDesc*& dev_desc, int*& status, double*& qbuf)
+{
+    size_t bytes = level_ws_bytes(K, 1) + (size_t)qelems * sizeof(double) + 64 * 1024;
+    int rc = ensure_ws(h, bytes);
+    if (rc) return rc;
+    ar = Arena{h->ws, 0, h->ws_bytes};
+    carve_level_ws(ar, lws, K, 1);
+    qbuf = ar.take<double>(std::max<int64_t>(qelems, 1));
+    status = ar.take<int>(64);
+    dev_desc = ar.take<MergeDesc>(1);
+    if (ar.off > ar.cap) return TDEIG_ENOMEM;
+    MergeDesc md;
+    memset(&md, 0, sizeof(md));
+    md.g0 = 0;
+    md.n = (int)K;
+    md.n1 = 0;
+    md.qhat = qbuf;
+    md.tiles_m = 1;
+    CU(cudaMemcpyAsync(dev_desc, &md, sizeof(md), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    CU(cudaMemsetAsync(status, 0, 64 * sizeof(int), h->stream));
+    return TDEIG_OK;
+}
+
+extern "C" int tdeig_secular(tdeig_handle h, int64_t K, const double* d, const double* z, double rho,
+                             double* lambda, double* gamma, double* mu)
+{
+    if (!h || K < 1 || K > (1 << 24) || !d || !z || !lambda || !gamma || !mu) return TDEIG_EINVAL;
+    if (!(rho > 0.0) || !isfinite(rho)) return TDEIG_EINVAL;
+    CU(cudaSetDevice(h->device));
+    Arena ar{nullptr, 0, 0};
+    LevelWS lws;
+    MergeDesc* md;
+    int* status;
+    double* qbuf;
+    int rc = stage_setup(h, K, 0, ar, lws, md, status, qbuf);
+    if (rc) return rc;
+    cudaStream_t st = h->stream;
+    if ((rc = copy_in(lws.dK, d, K, st)) || (rc = copy_in(lws.zK, z, K, st))) return rc;
+    td_launch_stage_init(lws, (int)K, rho, st);
+    td_launch_secular(md, 1, (int)K, lws, status, st);
+    CU(cudaGetLastError());
+    if ((rc = copy_out(lambda, lws.lamK, K, st)) || (rc = copy_out(gamma, lws.gamK, K, st)) ||
+        (rc = copy_out(mu, lws.muK, K, st)))
+        return rc;
+    int hs = 0;
+    CU(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    return (hs & TD_STATUS_NOTCONV) ? TDEIG_ENOTCONV : TDEIG_OK;
+}
+
+extern "C" int tdeig_lowner_cauchy(tdeig_handle h, int64_t K, const double* d, const double* gamma,
+                                   const double* mu, const double* z, double rho, double* uhat,
+                                   double* v, double* Qhat)
+{
+    if (!h || K < 1 || K > (1 << 20) || !d || !gamma || !mu || !z || !uhat || !v) return TDEIG_EINVAL;
+    if (!(rho > 0.0) || !isfinite(rho)) return TDEIG_EINVAL;
+    CU(cudaSetDevice(h->device));
+    const bool qdev = Qhat && is_device_ptr(Qhat);
+    Arena ar{nullptr, 0, 0};
+    LevelWS lws;
+    MergeDesc* md;
+    int* status;
+    double* qbuf;
+    int rc = stage_setup(h, K, (Qhat && !qdev) ? K * K : 0, ar, lws, md, status, qbuf);
+    if (rc) return rc;
+    cudaStream_t st = h->stream;
+    if (qdev) {
+        MergeDesc m;
+        CU(cudaMemcpy(&m, md, sizeof(m), cudaMemcpyDeviceToHost));
+        m.qhat = Qhat;
+        CU(cudaMemcpy(md, &m, sizeof(m), cudaMemcpyHostToDevice));
+    }
+    if ((rc = copy_in(lws.dK, d, K, st)) || (rc = copy_in(lws.gamK, gamma, K, st)) ||
+        (rc = copy_in(lws.muK, mu, K, st)) || (rc = copy_in(lws.zK, z, K, st)))
+        return rc;
+    td_launch_stage_init(lws, (int)K, rho, st);
+    td_launch_lowner_cauchy(md, 1, (int)K, (int)K, lws, Qhat ? 1 : 0, st);
+    CU(cudaGetLastError());
+    if ((rc = copy_out(uhat, lws.uhat, K, st)) || (rc = copy_out(v, lws.vv, K, st))) return rc;
+    if (Qhat && !qdev) CU(cudaMemcpyAsync(Qhat, qbuf, K * K * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    return TDEIG_OK;
+}

@@ -1,0 +1,239 @@
+"""Thin ctypes binding of libtdeig.so (include/tdeig.h).
+
+Argument marshalling only: every step of the eigensolver runs in the library's
+CUDA kernels.  If the library is missing or cannot be loaded this module raises;
+there is no CPU fallback.
+
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays (host).  Host inputs
+are copied to the device by the library inside the call; results come back in
+the same kind of memory as the inputs.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtdeig.so")
+
+MODE_DENSE, MODE_ADC1, MODE_ADC2 = 0, 1, 2
+PREC_FP64, PREC_SPLIT = 0 << 8, 1 << 8
+_MODES = {"dense": MODE_DENSE, "adc1": MODE_ADC1, "adc2": MODE_ADC2}
+_PRECS = {"fp64": PREC_FP64, "split": PREC_SPLIT}
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ETIMEOUT, ENOTIMPL = 0, -1, -2, -3, -4, -5, -6
+
+
+class TdeigError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__("%s failed: %s (%d)" % (what, strerror(status), status))
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("leaf", ctypes.c_int), ("hss_threshold", ctypes.c_int),
+                ("hss_leaf", ctypes.c_int), ("tol", ctypes.c_double),
+                ("oversample", ctypes.c_int), ("rank_eps", ctypes.c_double),
+                ("rank_cap", ctypes.c_int), ("boundary_shift", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+
+
+def lib():
+    """Load libtdeig.so (raises OSError when it is missing: no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError("libtdeig.so not built (run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        L.tdeig_default_options.argtypes = [ctypes.POINTER(Options)]
+        L.tdeig_default_options.restype = None
+        L.tdeig_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(Options)]
+        L.tdeig_create.restype = ctypes.c_int
+        L.tdeig_destroy.argtypes = [_vp]
+        L.tdeig_destroy.restype = ctypes.c_int
+        L.tdeig_strerror.argtypes = [ctypes.c_int]
+        L.tdeig_strerror.restype = ctypes.c_char_p
+        L.tdeig_solve.argtypes = [_vp, _vp, _vp, _i64, _vp, _vp, ctypes.c_int]
+        L.tdeig_solve.restype = ctypes.c_int
+        L.tdeig_solve_batched.argtypes = [_vp, _i64, ctypes.POINTER(_i64), _vp, _vp, _vp, _vp,
+                                          ctypes.c_int]
+        L.tdeig_solve_batched.restype = ctypes.c_int
+        L.tdeig_last_stats.argtypes = [_vp, ctypes.c_char_p, ctypes.c_size_t]
+        L.tdeig_last_stats.restype = ctypes.c_int
+        L.tdeig_secular.argtypes = [_vp, _i64, _vp, _vp, ctypes.c_double, _vp, _vp, _vp]
+        L.tdeig_secular.restype = ctypes.c_int
+        L.tdeig_lowner_cauchy.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp, ctypes.c_double, _vp, _vp,
+                                          _vp]
+        L.tdeig_lowner_cauchy.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def strerror(status):
+    return lib().tdeig_strerror(int(status)).decode()
+
+
+def default_options():
+    o = Options()
+    lib().tdeig_default_options(ctypes.byref(o))
+    return o
+
+
+def mode_code(mode="dense", prec="fp64"):
+    if isinstance(mode, int):
+        return mode
+    return _MODES[mode] | _PRECS[prec]
+
+
+# --------------------------------------------------------------------------
+# array helpers
+# --------------------------------------------------------------------------
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        assert x.is_contiguous() or x.t().is_contiguous()
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def _as_f64(x):
+    if _is_torch(x):
+        import torch
+        return x.to(torch.float64).contiguous()
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
+def _empty_like_kind(ref, shape, fortran=False):
+    """An output array in the same kind of memory as ref."""
+    if _is_torch(ref):
+        import torch
+        if fortran and len(shape) == 2:
+            # column-major n x n buffer: allocate (n, n) row-major, hand out its transpose
+            return torch.empty((shape[1], shape[0]), dtype=torch.float64, device=ref.device).t()
+        return torch.empty(shape, dtype=torch.float64, device=ref.device)
+    return np.empty(shape, dtype=np.float64, order="F" if fortran else "C")
+
+
+class Solver:
+    """A tdeig handle (one per host thread)."""
+
+    def __init__(self, stream=None, **opts):
+        o = default_options()
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError("unknown option %s" % k)
+            setattr(o, k, v)
+        if stream is not None:
+            o.cuda_stream = stream
+        self._keep_stream = stream
+        h = _vp()
+        st = lib().tdeig_create(ctypes.byref(h), ctypes.byref(o))
+        if st != OK:
+            raise TdeigError(st, "tdeig_create")
+        self.h = h
+        self.options = o
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tdeig_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def stats(self):
+        n = lib().tdeig_last_stats(self.h, None, 0)
+        buf = ctypes.create_string_buffer(max(n, 0) + 1)
+        lib().tdeig_last_stats(self.h, buf, len(buf))
+        return buf.value.decode()
+
+    def solve_raw(self, d_ptr, e_ptr, N, lam_ptr, q_ptr, mode):
+        """The C call itself on raw pointers; returns the status."""
+        return lib().tdeig_solve(self.h, d_ptr, e_ptr, int(N), lam_ptr, q_ptr, int(mode))
+
+    def solve(self, d, e, mode="dense", prec="fp64", vectors=True, out=None, check=True):
+        """Eigendecomposition of tridiag(e, d, e): returns (lam, Q), Q[:, j] <-> lam[j]."""
+        d = _as_f64(d)
+        e = _as_f64(e)
+        N = d.shape[0]
+        if out is None:
+            lam = _empty_like_kind(d, (N,))
+            Q = _empty_like_kind(d, (N, N), fortran=True) if vectors else None
+        else:
+            lam, Q = out
+        st = lib().tdeig_solve(self.h, _ptr(d), _ptr(e) if N > 1 else None, N, _ptr(lam), _ptr(Q),
+                               mode_code(mode, prec))
+        if check and st != OK:
+            raise TdeigError(st, "tdeig_solve")
+        return lam, Q
+
+    def solve_batched(self, ds, es, mode="dense", prec="fp64"):
+        """Independent matrices (lists of numpy arrays / CPU or CUDA tensors)."""
+        sizes = [int(x.shape[0]) for x in ds]
+        if _is_torch(ds[0]):
+            import torch
+            dcat = torch.cat([_as_f64(x) for x in ds])
+            ecat = torch.cat([_as_f64(x) for x in es]) if sum(sizes) > len(sizes) else None
+            lam = torch.empty(sum(sizes), dtype=torch.float64, device=dcat.device)
+            Qc = torch.empty(sum(n * n for n in sizes), dtype=torch.float64, device=dcat.device)
+        else:
+            dcat = np.concatenate([_as_f64(x) for x in ds])
+            ecat = np.concatenate([_as_f64(x) for x in es]) if sum(sizes) > len(sizes) else None
+            lam = np.empty(sum(sizes))
+            Qc = np.empty(sum(n * n for n in sizes))
+        Ns = (_i64 * len(sizes))(*sizes)
+        st = lib().tdeig_solve_batched(self.h, len(sizes), Ns, _ptr(dcat), _ptr(ecat), _ptr(lam),
+                                       _ptr(Qc), mode_code(mode, prec))
+        if st != OK:
+            raise TdeigError(st, "tdeig_solve_batched")
+        outs = []
+        r = q = 0
+        for n in sizes:
+            blk = Qc[q:q + n * n]
+            Qb = blk.reshape(n, n).t() if _is_torch(blk) else blk.reshape((n, n), order="F")
+            outs.append((lam[r:r + n], Qb))
+            r += n
+            q += n * n
+        return outs
+
+    def secular(self, d, z, rho):
+        d = _as_f64(d)
+        z = _as_f64(z)
+        K = d.shape[0]
+        lam, gam, mu = (_empty_like_kind(d, (K,)) for _ in range(3))
+        st = lib().tdeig_secular(self.h, K, _ptr(d), _ptr(z), float(rho), _ptr(lam), _ptr(gam),
+                                 _ptr(mu))
+        if st != OK:
+            raise TdeigError(st, "tdeig_secular")
+        return lam, gam, mu
+
+    def lowner_cauchy(self, d, gamma, mu, z, rho, qhat=True):
+        d, gamma, mu, z = (_as_f64(x) for x in (d, gamma, mu, z))
+        K = d.shape[0]
+        uh = _empty_like_kind(d, (K,))
+        v = _empty_like_kind(d, (K,))
+        Qh = _empty_like_kind(d, (K, K), fortran=True) if qhat else None
+        st = lib().tdeig_lowner_cauchy(self.h, K, _ptr(d), _ptr(gamma), _ptr(mu), _ptr(z),
+                                       float(rho), _ptr(uh), _ptr(v), _ptr(Qh))
+        if st != OK:
+            raise TdeigError(st, "tdeig_lowner_cauchy")
+        return uh, v, Qh

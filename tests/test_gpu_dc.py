@@ -1,0 +1,182 @@
+"""GPU parity of the dense DC path against the CPU oracle (element by element).
+
+Tolerances (the benchmark spec): eigenvalues within 1e-12 (normwise for tiny ones);
+orthogonality ||Q^T Q - I||_F / N and residual ||TQ - Q Lambda||_F/(N ||T||) at
+most 1e-13; eigenvectors up to sign for eigenvalues with a relative gap of at
+least 1e-8 (clustered ones are not unique).
+"""
+import numpy as np
+import pytest
+
+from oracle import dc, metrics
+from paper_1510_04591_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def solver():
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_1510_04591_gb300 import tdeig
+    assert torch.cuda.is_available()
+    s = tdeig.Solver()
+    yield s
+    s.close()
+
+
+def run_gpu(solver, a, b, mode="dense", prec="fp64", host=False):
+    import torch
+    if host:
+        lam, Q = solver.solve(a, b, mode, prec)
+        return np.asarray(lam), np.asarray(Q)
+    lam, Q = solver.solve(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), mode, prec)
+    return lam.cpu().numpy(), Q.cpu().numpy()
+
+
+def check_against_oracle(a, b, lam, Q, eig_tol=1e-12, orth_tol=1e-13, vec_tol=1e-8, leaf=32):
+    lam_ref, Q_ref = dc.solve(a, b, dc.Options(leaf=leaf))
+    assert metrics.eig_error(lam, lam_ref) <= eig_tol
+    assert metrics.orthogonality(Q) <= orth_tol
+    assert metrics.residual(a, b, lam, Q) <= orth_tol
+    err, cnt = metrics.vectors_match(Q, Q_ref, lam_ref)
+    assert err <= vec_tol, (err, cnt)
+    return lam_ref, Q_ref
+
+
+# -------------------------------------------------------------------------
+# stage parity: secular roots, Loewner, Cauchy-like matrix
+# -------------------------------------------------------------------------
+def rank_one(K, seed, rho=1.0, cluster=False):
+    rng = np.random.default_rng(seed)
+    d = np.sort(rng.uniform(-1, 1, K))
+    if cluster and K > 8:
+        d[K // 2:K // 2 + 4] = d[K // 2] + np.arange(4) * 1e-13
+    z = rng.standard_normal(K)
+    if cluster and K > 8:
+        z[1] = 1e-9
+    z /= np.linalg.norm(z)
+    return d, z, rho
+
+
+@pytest.mark.parametrize("K,seed,rho,cluster", [(1, 0, 0.5, False), (2, 1, 1.0, False),
+                                                (3, 2, 0.1, False), (33, 3, 2.0, False),
+                                                (100, 4, 1.0, True), (1000, 5, 1.0, False),
+                                                (4097, 6, 0.7, True)])
+def test_secular_stage(solver, K, seed, rho, cluster):
+    d, z, rho = rank_one(K, seed, rho, cluster)
+    lam, gam, mu = solver.secular(d, z, rho)
+    lam_r, gam_r, mu_r, _ = dc.secular(d, z, rho)
+    scale = max(1.0, rho)
+    assert np.max(np.abs(lam - lam_r)) <= 4e-15 * scale
+    # gamma, mu are relative quantities; compare relative to themselves
+    assert np.max(np.abs(gam - gam_r) / np.maximum(gam_r, 1e-300)) <= 1e-9 or \
+        np.max(np.abs(gam - gam_r)) <= 4e-15 * scale
+    assert np.all(gam > 0)
+    if K > 1:
+        assert np.all(mu[:-1] > 0)
+        assert np.max(np.abs(mu[:-1] - mu_r[:-1])) <= 4e-15 * scale
+
+
+@pytest.mark.parametrize("K,seed", [(1, 0), (7, 1), (500, 2), (3000, 3)])
+def test_lowner_cauchy_stage(solver, K, seed):
+    d, z, rho = rank_one(K, seed, 1.3)
+    lam, gam, mu, _ = dc.secular(d, z, rho)
+    uh, v, Qh = solver.lowner_cauchy(d, gam, mu, z, rho)
+    uh_r = dc.lowner(d, gam, mu, rho, z)
+    Qh_r, v_r = dc.cauchy(d, gam, mu, uh_r)
+    assert np.max(np.abs(uh - uh_r)) <= 1e-14
+    assert np.max(np.abs(v - v_r) / v_r) <= 1e-13
+    assert np.max(np.abs(Qh - Qh_r)) <= 1e-13
+    assert metrics.orthogonality(Qh) <= 1e-14
+
+
+# -------------------------------------------------------------------------
+# whole solver, dense mode
+# -------------------------------------------------------------------------
+@pytest.mark.parametrize("N", [1, 2, 3, 31, 32, 33, 65, 100, 257, 1000, 1024, 2049])
+def test_dense_random(solver, N):
+    a, b = inputs.uniform(N, seed=N)
+    lam, Q = run_gpu(solver, a, b)
+    check_against_oracle(a, b, lam, Q)
+
+
+@pytest.mark.parametrize("N", [2, 64, 1024, 1031])
+def test_dense_toeplitz_closed_form(solver, N):
+    a, b = inputs.toeplitz(N)
+    lam, Q = run_gpu(solver, a, b)
+    k = np.arange(1, N + 1)
+    ex = 2 + 2 * np.cos(k * np.pi / (N + 1))
+    o = np.argsort(ex)
+    V = np.sqrt(2.0 / (N + 1)) * np.sin(np.outer(k, k) * np.pi / (N + 1))[:, o]
+    assert metrics.eig_error(lam, ex[o]) <= 1e-13
+    err, cnt = metrics.vectors_match(Q, V, ex[o], gap_rel=0.0)
+    assert err <= 1e-9
+    assert metrics.orthogonality(Q) <= 1e-13
+    check_against_oracle(a, b, lam, Q)
+
+
+@pytest.mark.parametrize("gen", ["clement", "wilkinson", "legendre", "hermite", "laguerre",
+                                 "zero_offdiag", "tiny_offdiag"])
+def test_dense_families(solver, gen):
+    if gen == "clement":
+        a, b = inputs.clement(401)
+    elif gen == "wilkinson":
+        a, b = inputs.glued_wilkinson(777)
+    elif gen == "legendre":
+        a, b = inputs.legendre(500)
+    elif gen == "hermite":
+        a, b = inputs.hermite(300)
+    elif gen == "laguerre":
+        a, b = inputs.laguerre(300)
+    elif gen == "zero_offdiag":
+        a, b = inputs.uniform(200, 3)
+        b = np.zeros_like(b)
+    else:
+        a, b = inputs.uniform(200, 4)
+        b[::7] = 1e-300
+    lam, Q = run_gpu(solver, a, b)
+    check_against_oracle(a, b, lam, Q)
+
+
+def test_host_and_device_pointers_agree(solver):
+    a, b = inputs.uniform(500, 9)
+    lam_d, Q_d = run_gpu(solver, a, b)
+    lam_h, Q_h = run_gpu(solver, a, b, host=True)
+    assert np.array_equal(lam_d, lam_h)
+    assert np.array_equal(Q_d, Q_h)
+
+
+def test_edge_cases(solver):
+    import torch
+    from paper_1510_04591_gb300 import tdeig
+    lam, Q = solver.solve(np.array([3.5]), np.zeros(0))
+    assert lam[0] == 3.5 and Q[0, 0] == 1.0
+    lam, Q = solver.solve(np.array([1.0, 1.0]), np.array([0.0]))
+    assert np.array_equal(lam, [1.0, 1.0])
+    with pytest.raises(tdeig.TdeigError) as ei:
+        solver.solve(np.array([1.0, np.nan, 2.0]), np.array([0.5, 0.5]))
+    assert ei.value.status == tdeig.EINVAL
+    st = tdeig.lib().tdeig_solve(solver.h, None, None, 0, None, None, 0)
+    assert st == tdeig.OK
+    a = torch.zeros(5, dtype=torch.float64, device="cuda")
+    lam, Q = solver.solve(a, torch.zeros(4, dtype=torch.float64, device="cuda"))
+    assert torch.all(lam == 0) and torch.equal(Q.cpu(), torch.eye(5, dtype=torch.float64))
+
+
+def test_batched_uneven(solver):
+    sizes = [5, 64, 1, 300, 33, 0, 129]
+    ds, es = [], []
+    for i, n in enumerate(sizes):
+        if i % 2:
+            a, b = inputs.glued_wilkinson(n) if n else (np.zeros(0), np.zeros(0))
+        else:
+            a, b = inputs.uniform(n, 50 + i)
+        ds.append(a)
+        es.append(b)
+    outs = solver.solve_batched(ds, es)
+    for (lam, Q), a, b in zip(outs, ds, es):
+        if len(a) == 0:
+            continue
+        check_against_oracle(a, b, np.asarray(lam), np.asarray(Q))

@@ -26,6 +26,7 @@ struct MergeDesc {
     const double* beta_ptr;   // scaled coupling b_k between the children (device)
     int g0, n, n1;
     int member;
+    int node_id;           // node of the DC tree: root 0, children of i are 2i+1, 2i+2
     int tile0;             // first GEMM tile of this merge in the level's tile numbering
     int tiles_m;           // row tiles of this merge
 };

@@ -7,16 +7,74 @@
 #include "../../include/tdeig.h"
 #include "common.cuh"
 
+// Growable device arena owned by the handle for the HSS generators and the
+// Algorithm 3 intermediates.
 struct HssWS {
-    double* pool;      // generator / sampling storage
-    size_t pool_elems;
-    int* ipool;
-    size_t ipool_elems;
+    char* base = nullptr;
+    size_t cap = 0;
 };
 
-struct Arena;
-size_t hss_ws_bytes(const tdeig_options& opt, int64_t Qsz, int64_t R, bool enabled);
-void hss_carve_ws(Arena& a, HssWS& w, const tdeig_options& opt, int64_t Qsz, int64_t R, bool enabled);
+// C[M x N] = alpha op(A)[M x Kd] op(B)[Kd x N] + beta C, column-major.
+//   op(A)[i, k] = transA ? A[k + i lda] : A[i + col(k) lda], col(k) = acol ? acol[k] : k
+//   op(B)[k, j] = transB ? B[j + k ldb] : B[k + j ldb]
+//   C column j is written to column ccol ? ccol[j] : j
+struct GemmDesc {
+    const double* A;
+    const double* B;
+    double* C;
+    const int* acol;
+    const int* ccol;
+    int M, N, Kd, lda, ldb, ldc;
+    int transA, transB;
+    double alpha, beta;
+    int tile0, tiles_m;
+};
+
+// out[a + b ld] = uhat[row] v[col] / (d[row] - lambda[col]) (Remark 1), for
+// row = rows ? rows[a] : r0 + a and col = cols ? cols[b] : c0 + b.
+struct FillDesc {
+    double* out;
+    int ld, nr, nc;
+    const int* rows;
+    int r0;
+    const int* cols;
+    int c0;
+    const double *d, *gam, *mu, *uhat, *v;
+    int tile0, tiles_r;
+};
+
+// Row interpolative decomposition Phi ~= U Phi[piv, :] (m x s input).
+struct IdDesc {
+    const double* Phi;
+    int ldphi, m, s;
+    const int* rowmap;  // global index of local row a: rowmap ? rowmap[a] : rowbase + a
+    int rowbase;
+    double* U;          // m x rank, leading dimension ldu
+    int ldu;
+    int* out_idx;       // global indices of the skeleton rows
+    int* out_piv;       // local skeleton rows
+    int* out_rank;
+};
+
+// dst[a + c ldd] = src[piv[a] + c lds], a < nr, c < ncols.
+struct GatherDesc {
+    const double* src;
+    int lds;
+    const int* piv;
+    int nr;
+    double* dst;
+    int ldd, ncols;
+};
+
+struct RankDesc {
+    const double *d, *gam;
+    int K, nl;
+    int* bounds;  // nl + 1 entries, in/out
+    int* r_out;
+};
+
+void hss_launch_gemm(const std::vector<GemmDesc>& g, GemmDesc* dev, cudaStream_t st);
+void hss_free(HssWS& w);
 int hss_update_level(const tdeig_options& opt, int variant, int prec,
                      const std::vector<MergeDesc>& merges, const MergeDesc* dev_merges,
                      const std::vector<int>& K, const LevelWS& lws, HssWS& hws, int* status,

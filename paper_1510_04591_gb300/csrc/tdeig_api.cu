@@ -37,6 +37,7 @@ struct tdeig_ctx {
     char* ws = nullptr;
     size_t ws_bytes = 0;
     std::string stats;
+    HssWS hss;                         // HSS generators and Algorithm 3 intermediates
     std::vector<cudaEvent_t> events;   // stage timing events, reused across solves
     std::vector<const char*> ev_names;
     std::vector<int> ev_level;
@@ -110,6 +111,7 @@ extern "C" int tdeig_destroy(tdeig_handle h)
     if (!h) return TDEIG_EINVAL;
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->ws) cudaFree(h->ws);
+    hss_free(h->hss);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -195,7 +197,7 @@ struct Bufs {
 };
 
 static NodeOut plan_node(Plan& P, const Bufs& B, int b, int64_t off, int64_t n, int depth, int D,
-                         std::vector<int64_t>& qoff)
+                         std::vector<int64_t>& qoff, int node_id)
 {
     const int h = D - depth;
     const int64_t g0 = P.row0[b] + off;
@@ -223,8 +225,8 @@ static NodeOut plan_node(Plan& P, const Bufs& B, int b, int64_t off, int64_t n, 
         return out;
     }
     const int64_t k = n / 2;
-    NodeOut c1 = plan_node(P, B, b, off, k, depth + 1, D, qoff);
-    NodeOut c2 = plan_node(P, B, b, off + k, n - k, depth + 1, D, qoff);
+    NodeOut c1 = plan_node(P, B, b, off, k, depth + 1, D, qoff, 2 * node_id + 1);
+    NodeOut c2 = plan_node(P, B, b, off + k, n - k, depth + 1, D, qoff, 2 * node_id + 2);
     MergeDesc md;
     memset(&md, 0, sizeof(md));
     md.qin1 = c1.q;
@@ -240,6 +242,7 @@ static NodeOut plan_node(Plan& P, const Bufs& B, int b, int64_t off, int64_t n, 
     md.n = (int)n;
     md.n1 = (int)k;
     md.member = b;
+    md.node_id = node_id;
     P.levels[h - 1].merges.push_back(md);
     return out;
 }
@@ -256,7 +259,7 @@ static void build_plan(Plan& P, const Bufs& B, int leaf)
     P.leaves.clear();
     std::vector<int64_t> qoff(H + 1, 0);
     for (int b = 0; b < P.members; b++)
-        if (P.N[b] > 0) plan_node(P, B, b, 0, P.N[b], 0, D[b], qoff);
+        if (P.N[b] > 0) plan_node(P, B, b, 0, P.N[b], 0, D[b], qoff, 0);
     size_t desc = 0;
     for (auto& L : P.levels) {
         std::sort(L.merges.begin(), L.merges.end(),
@@ -437,7 +440,6 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     bytes += (size_t)batch * (3 * sizeof(int64_t) + sizeof(double));
     bytes += (size_t)(Mmax * 64) * (sizeof(MergeDesc) + 3 * sizeof(int)) +
              (size_t)leaves_max * sizeof(LeafDesc);
-    bytes += hss_ws_bytes(h->opt, Qsz, R, variant != TDEIG_MODE_DENSE);
     bytes += 64 * 1024;
     int rc = ensure_ws(h, bytes);
     if (rc) return rc;
@@ -462,8 +464,6 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     int* status = ar.take<int>(64);
     LevelWS lws;
     carve_level_ws(ar, lws, R, Mmax);
-    HssWS hws;
-    hss_carve_ws(ar, hws, h->opt, Qsz, R, variant != TDEIG_MODE_DENSE);
 
     build_plan(P, B, leaf);
     size_t ndesc = 0;
@@ -548,7 +548,8 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
         td_launch_order(Md, nm, lws, st);
         MARK(any_hss ? "hss_update" : "update", lv);
         if (any_hss) {
-            rc = hss_update_level(h->opt, variant, prec, L.merges, Md, Kh, lws, hws, status, st, hss_js);
+            rc = hss_update_level(h->opt, variant, prec, L.merges, Md, Kh, lws, h->hss, status, st,
+                                  hss_js);
             if (rc) return rc;
         } else {
             td_launch_update_dense(Md, nm, L.tiles, lws, st);

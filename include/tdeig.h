@@ -134,6 +134,32 @@ int tdeig_lowner_cauchy(tdeig_handle h, int64_t K, const double* d, const double
                         const double* mu, const double* z, double rho,
                         double* uhat, double* v, double* Qhat);
 
+/* Largest K accepted by tdeig_secular_noalloc. */
+#define TDEIG_NOALLOC_MAX_K 65536
+
+/* Secular roots as tdeig_secular computes them, but without allocating any
+ * memory.  The paper has no counterpart: this entry point exists for callers
+ * that cannot allocate device memory when they need the roots -- code that
+ * has handed all free device memory to its own pool allocator (where a
+ * cudaMalloc would fail or fragment that pool), and code on a latency-bound
+ * path where cudaMalloc's implicit device synchronisation is not acceptable.
+ * It needs no handle and calls no cudaMalloc, cudaFree or allocating library
+ * routine.
+ *   K      : 1 <= K <= TDEIG_NOALLOC_MAX_K (65536); larger K -> TDEIG_EINVAL
+ *   d, z   : K entries each, DEVICE memory (host pointers -> TDEIG_EINVAL)
+ *   lambda, gamma, mu : K entries each, DEVICE memory, written as by tdeig_secular
+ *   cuda_stream : cudaStream_t to run on (NULL: the legacy default stream)
+ * Scratch (K weights and a status word, 512 KiB in all) is a fixed array in
+ * the library's device image, held by every GPU that loads the library until
+ * the process exits; each call clears the status word before use.  The first
+ * call on a device, with that device current, looks up the array's device
+ * address (cudaGetSymbolAddress) -- make that first call before any stream
+ * capture.  All calls share the array: calls whose work overlaps on the GPU
+ * (other streams or host threads) race.  The call synchronises the stream and
+ * returns TDEIG_ENOTCONV if a root hit the iteration cap. */
+int tdeig_secular_noalloc(int64_t K, const double* d, const double* z, double rho,
+                          double* lambda, double* gamma, double* mu, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,8 +18,12 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <mutex>
 
+#include "../../include/tdeig.h"
 #include "common.cuh"
+
+#define TD_NOALLOC_MAX_DEVICES 64
 
 long long g_td_launches = 0;
 
@@ -845,4 +849,99 @@ __global__ void k_stage_init(LevelWS ws, int K, double rho)
 void td_launch_stage_init(const LevelWS& ws, int K, double rho, cudaStream_t st)
 {
     k_stage_init<<<td_cdiv(std::max(K, 1), 256), 256, 0, st>>>(ws, K, rho); g_td_launches++;
+}
+
+// ---------------------------------------------------------------------------
+// Secular roots without any allocation (tdeig_secular_noalloc in tdeig.h).
+//
+// Some callers cannot allocate device memory at the moment they need the
+// roots: code that has handed all free device memory to its own pool
+// allocator (a cudaMalloc there fails or fragments the pool), and code on a
+// latency-bound path where cudaMalloc's implicit device synchronisation is not
+// acceptable.  This variant of k_secular keeps its scratch -- the weights
+// rho z_j^2 and a status word -- in the file-scope array below, which every
+// GPU that loads the library holds until the process exits.
+//
+// Host code cannot use the array's name as a device address: it is a host-side
+// stand-in.  The first call on each device (with that device current) looks
+// the device address up with cudaGetSymbolAddress and caches it; make that
+// first call before any stream capture.  All calls share the array, so calls
+// whose work overlaps on the GPU (other streams, other host threads) race.
+// ---------------------------------------------------------------------------
+#define TD_NOALLOC_SLOTS (TDEIG_NOALLOC_MAX_K + 32)
+static __device__ __align__(256) double td_noalloc_scratch[TD_NOALLOC_SLOTS];
+
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_ptr[TD_NOALLOC_MAX_DEVICES];
+
+__global__ void k_noalloc_weights(const double* z, double rho, int K, double* w, int* status)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *status = 0;   // clear the status word the previous call left in the array
+    if (i < K) w[i] = rho * z[i] * z[i];
+}
+
+__global__ void k_secular_noalloc(const double* d, const double* w, int K, int* status, double* lam,
+                                  double* gam, double* mu)
+{
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= K) return;
+    double l, g, m;
+    int it;
+    secular_root_warp(d, w, K, i, lane, &l, &g, &m, &it);
+    if (lane == 0) {
+        lam[i] = l;
+        gam[i] = g;
+        mu[i] = m;
+        if (it > TD_SECULAR_MAXIT) atomicOr(status, TD_STATUS_NOTCONV);
+    }
+}
+
+static bool noalloc_is_device(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+extern "C" int tdeig_secular_noalloc(int64_t K, const double* d, const double* z, double rho,
+                                     double* lambda, double* gamma, double* mu, void* cuda_stream)
+{
+    if (K < 1 || K > TDEIG_NOALLOC_MAX_K) return TDEIG_EINVAL;
+    if (!d || !z || !lambda || !gamma || !mu || !(rho > 0.0) || !isfinite(rho)) return TDEIG_EINVAL;
+    if (!noalloc_is_device(d) || !noalloc_is_device(z) || !noalloc_is_device(lambda) ||
+        !noalloc_is_device(gamma) || !noalloc_is_device(mu))
+        return TDEIG_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= TD_NOALLOC_MAX_DEVICES)
+        return TDEIG_ECUDA;
+    double* scratch;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, td_noalloc_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return TDEIG_ECUDA;
+            }
+            g_noalloc_ptr[dev] = (double*)p;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    double* w = scratch;
+    int* status = (int*)(scratch + TDEIG_NOALLOC_MAX_K);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int k = (int)K;
+    k_noalloc_weights<<<td_cdiv(k, 256), 256, 0, st>>>(z, rho, k, w, status);
+    k_secular_noalloc<<<td_cdiv(k, 8), 256, 0, st>>>(d, w, k, status, lambda, gamma, mu);
+    if (cudaGetLastError() != cudaSuccess) return TDEIG_ECUDA;
+    int hs = 0;
+    if (cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return TDEIG_ECUDA;
+    return (hs & TD_STATUS_NOTCONV) ? TDEIG_ENOTCONV : TDEIG_OK;
 }

@@ -70,6 +70,8 @@ def lib():
         L.tdeig_lowner_cauchy.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp, ctypes.c_double, _vp, _vp,
                                           _vp]
         L.tdeig_lowner_cauchy.restype = ctypes.c_int
+        L.tdeig_secular_noalloc.argtypes = [_i64, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp]
+        L.tdeig_secular_noalloc.restype = ctypes.c_int
         _lib = L
     return _lib
 

@@ -141,10 +141,11 @@ def roofline(stats_list):
             tot[k] = tot.get(k, 0.0) + v
     dom = max(tot, key=tot.get)
     fp64_peak = N_SMS * 2070e6 * 2 * FP64_FMA_PER_SM_CLK / 1e12
-    res = {"kernel": dom, "share": tot[dom] / sum(tot.values())}
+    res = {"kernel": dom, "share": tot[dom] / sum(tot.values()),
+           "stage_share": {k: v / sum(tot.values()) for k, v in tot.items()}}
+    fl = ms = 0.0
+    n_launch = 0
     if dom == "update":
-        fl = ms = 0.0
-        n_launch = 0
         for st in stats_list:
             work = stage_work(st)
             for L in st["levels"]:
@@ -152,9 +153,22 @@ def roofline(stats_list):
                     fl += work[L["height"]]["update_flops"]
                     ms += L["ms"]["update"]
                     n_launch += 1
+        res["kernel"] = "k_gemm_f64 (dense update)"
+    elif dom in ("hss_mult", "hss_sample", "hss_build"):
+        key = dom[4:]
+        for st in stats_list:
+            fl += sum(h["flops"][key] for h in st.get("hss", []) if "flops" in h)
+            for L in st["levels"]:
+                if dom in L["ms"]:
+                    ms += L["ms"][dom]
+                    n_launch += 1
+        res["kernel"] = "k_gemm_grouped (%s)" % {"mult": "Algorithm 3 HSS x matrix",
+                                                  "sample": "sampling Y, Z",
+                                                  "build": "Algorithm 2 products"}[key]
+    if fl > 0 and ms > 0:
         ach = fl / (ms / 1e3) / 1e12
         res.update({"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                    "frac": ach / fp64_peak, "traffic": None, "launches": n_launch,
+                    "frac": ach / fp64_peak, "traffic": None, "stage_launches": n_launch,
                     "peak_note": "FP64 FMA issue: 152 SMs x 2070 MHz x 2 FMA/clk/SM (measured "
                                  "FMA-chain probe 1.20 TFLOP/s; cuBLAS DGEMM 1.10)"})
     return res

@@ -1,6 +1,7 @@
 // HSS update path (Algorithms 2 and 3, SRRSC) -- internal interface.
 #pragma once
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -66,6 +67,28 @@ struct GatherDesc {
     int ldd, ncols;
 };
 
+// One HSS block row (side 0: rows = node rows, entries uhat_r v_c / (d_r - lambda_c))
+// or block column (side 1: rows = node columns, entries v_r uhat_c / (d_c - lambda_r))
+// against every index outside the node's span [s0, s1), compressed by complete-pivoting
+// elimination on its Cauchy generators (ADC1).
+struct SrrscDesc {
+    int m;                 // rows: global index of row a = a < n1 ? map1[a] : (map2 ? map2[a - n1] : base + a)
+    const int* map1;
+    int n1;
+    const int* map2;
+    int base;
+    int s0, s1, K, side, kcap;
+    const double *d, *gam, *mu, *uh, *v;   // Cauchy generators of the merge
+    float* invd;           // m x ncols magnitudes |1/(d - lambda)| (row-major)
+    double *g, *h;         // generators, m and ncols
+    float *gf, *hf;        // FP32 copies for the pivot search
+    unsigned char *actr, *actc;
+    double* mult;          // m x kcap elimination multipliers
+    double* U;             // m x rank interpolation matrix, leading dimension ldu
+    int ldu;
+    int *out_idx, *out_piv, *out_rank;
+};
+
 struct RankDesc {
     const double *d, *gam;
     int K, nl;
@@ -73,9 +96,13 @@ struct RankDesc {
     int* r_out;
 };
 
-void hss_launch_gemm(const std::vector<GemmDesc>& g, GemmDesc* dev, cudaStream_t st);
+// Launches one grouped product; returns its algorithmic flops (2 M N Kd summed).
+double hss_launch_gemm(const std::vector<GemmDesc>& g, GemmDesc* dev, cudaStream_t st);
 void hss_free(HssWS& w);
+// mark(name) records a timing event that starts sub-stage `name` (sampling,
+// construction, multiplication) on the solve's stream.
 int hss_update_level(const tdeig_options& opt, int variant, int prec,
                      const std::vector<MergeDesc>& merges, const MergeDesc* dev_merges,
                      const std::vector<int>& K, const LevelWS& lws, HssWS& hws, int* status,
-                     cudaStream_t st, std::string& stats);
+                     cudaStream_t st, std::string& stats,
+                     const std::function<int(const char*)>& mark);

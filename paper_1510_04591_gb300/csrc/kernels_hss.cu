@@ -101,22 +101,25 @@ __global__ void __launch_bounds__(HSS_NT) k_gemm_grouped(const GemmDesc* G, int 
     }
 }
 
-void hss_launch_gemm(const std::vector<GemmDesc>& gin, GemmDesc* dev, cudaStream_t st)
+double hss_launch_gemm(const std::vector<GemmDesc>& gin, GemmDesc* dev, cudaStream_t st)
 {
     std::vector<GemmDesc> g;
     g.reserve(gin.size());
     int tiles = 0;
+    double flops = 0.0;
     for (GemmDesc d : gin) {
         if (d.M <= 0 || d.N <= 0) continue;
         d.tiles_m = td_cdiv(d.M, 64);
         d.tile0 = tiles;
         tiles += d.tiles_m * td_cdiv(d.N, 64);
+        flops += 2.0 * d.M * d.N * d.Kd;
         g.push_back(d);
     }
-    if (g.empty()) return;
+    if (g.empty()) return 0.0;
     cudaMemcpyAsync(dev, g.data(), g.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice, st);
     k_gemm_grouped<<<tiles, HSS_NT, 0, st>>>(dev, (int)g.size());
     g_td_launches++;
+    return flops;
 }
 
 // ---------------------------------------------------------------------------
@@ -390,6 +393,164 @@ __global__ void k_rank_estimate(const RankDesc* Rd, int nr, double eps, int cap,
 }
 
 // ---------------------------------------------------------------------------
+// ADC1 compression (structured rank-revealing Schur complements, the paper's
+// SRRSC reading): complete-pivoting elimination on the generator form of one
+// HSS block row / column C[a, b] = g_a h_b / (d - lambda).  Each elimination
+// step keeps the Schur complement Cauchy-like: with pivot (p, q),
+//   g_a <- g_a - (S_aq / S_pq) g_p,   h_b <- h_b - (S_pb / S_pq) h_q,
+// S entries recomputed from the generators and Remark 1 differences in FP64.
+// The pivot search reads FP32 magnitudes |1/(d - lambda)| materialised once
+// per block, so only the search is approximate (a near-maximal pivot is still
+// a complete-pivoting choice).  Stop at |S_pq| <= tol |first pivot|.  With the
+// multipliers l_a (row a's elimination multipliers) and L11 those of the pivot
+// rows, U = C[:, pc] C[pr, pc]^{-1} = l L11^{-1}, so C ~= U C[pr, :].
+// One CTA per block.
+// ---------------------------------------------------------------------------
+#define SR_NT 512
+#define SR_MAXM 512
+#define SR_MAXK 256
+
+__device__ __forceinline__ int sr_row(const SrrscDesc& g, int a)
+{
+    return a < g.n1 ? g.map1[a] : (g.map2 ? g.map2[a - g.n1] : g.base + a);
+}
+
+__device__ __forceinline__ int sr_col(const SrrscDesc& g, int b)
+{
+    return b < g.s0 ? b : b + (g.s1 - g.s0);
+}
+
+__device__ __forceinline__ double sr_diff(const SrrscDesc& g, int r, int c)
+{
+    return g.side == 0 ? td_dminus(g.d, g.gam, g.mu, r, c) : td_dminus(g.d, g.gam, g.mu, c, r);
+}
+
+__global__ void __launch_bounds__(SR_NT) k_srrsc(const SrrscDesc* D, double tol, int* status)
+{
+    __shared__ float redv[SR_NT / 32];
+    __shared__ int redi[SR_NT / 32];
+    __shared__ int s_p, s_q, s_stop;
+    __shared__ double s_spq;
+    __shared__ int s_pr[SR_MAXK];
+    __shared__ int s_rowpos[SR_MAXM];
+    const SrrscDesc g = D[blockIdx.x];
+    const int m = g.m, nc = g.K - (g.s1 - g.s0);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int a = tid; a < m; a += SR_NT) {
+        const int ra = sr_row(g, a);
+        const double gv = g.side == 0 ? g.uh[ra] : g.v[ra];
+        g.g[a] = gv;
+        g.gf[a] = (float)gv;
+        g.actr[a] = 1;
+        s_rowpos[a] = -1;
+    }
+    for (int b = tid; b < nc; b += SR_NT) {
+        const int cb = sr_col(g, b);
+        const double hv = g.side == 0 ? g.v[cb] : g.uh[cb];
+        g.h[b] = hv;
+        g.hf[b] = (float)hv;
+        g.actc[b] = 1;
+    }
+    for (int a = wid; a < m; a += SR_NT / 32) {
+        const int ra = sr_row(g, a);
+        for (int b = lane; b < nc; b += 32)
+            g.invd[(size_t)a * nc + b] = 1.0f / fabsf((float)sr_diff(g, ra, sr_col(g, b)));
+    }
+    __syncthreads();
+    const int kmax = min(g.kcap, min(m, nc));
+    double first = 0.0;
+    int rank = 0;
+    for (int t = 0; t < kmax; t++) {
+        float best = -1.0f;
+        int bi = 0x7fffffff;
+        for (int a = wid; a < m; a += SR_NT / 32) {
+            if (!g.actr[a]) continue;
+            const float ga = fabsf(g.gf[a]);
+            const float* row = g.invd + (size_t)a * nc;
+            for (int b = lane; b < nc; b += 32) {
+                if (!g.actc[b]) continue;
+                const float val = ga * fabsf(g.hf[b]) * row[b];
+                const int idx = a * nc + b;
+                if (val > best || (val == best && idx < bi)) { best = val; bi = idx; }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) { redv[wid] = best; redi[wid] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            float bb = -1.0f;
+            int ib = 0x7fffffff;
+            for (int w = 0; w < SR_NT / 32; w++)
+                if (redv[w] > bb || (redv[w] == bb && redi[w] < ib)) { bb = redv[w]; ib = redi[w]; }
+            int stop = (ib == 0x7fffffff);
+            double spq = 0.0;
+            if (!stop) {
+                const int p = ib / nc, q = ib - p * nc;
+                spq = g.g[p] * g.h[q] / sr_diff(g, sr_row(g, p), sr_col(g, q));
+                if (t == 0) first = fabs(spq);
+                stop = (first == 0.0 || !(fabs(spq) > tol * first));
+                s_p = p;
+                s_q = q;
+                if (!stop) { s_pr[t] = p; s_rowpos[p] = t; }
+            }
+            s_spq = spq;
+            s_stop = stop;
+        }
+        __syncthreads();
+        if (s_stop) break;
+        const int p = s_p, q = s_q;
+        const double spq = s_spq, gp = g.g[p], hq = g.h[q];
+        const int rp = sr_row(g, p), cq = sr_col(g, q);
+        for (int a = tid; a < m; a += SR_NT) {
+            if (!g.actr[a]) continue;
+            if (a == p) { g.mult[(size_t)a * g.kcap + t] = 1.0; continue; }
+            const double saq = g.g[a] * hq / sr_diff(g, sr_row(g, a), cq);
+            const double l = saq / spq;
+            g.mult[(size_t)a * g.kcap + t] = l;
+            const double ga = g.g[a] - l * gp;
+            g.g[a] = ga;
+            g.gf[a] = (float)ga;
+        }
+        for (int b = tid; b < nc; b += SR_NT) {
+            if (!g.actc[b] || b == q) continue;
+            const double spb = gp * g.h[b] / sr_diff(g, rp, sr_col(g, b));
+            const double hb = g.h[b] - spb * hq / spq;
+            g.h[b] = hb;
+            g.hf[b] = (float)hb;
+        }
+        __syncthreads();
+        if (tid == 0) { g.actr[p] = 0; g.actc[q] = 0; }
+        __syncthreads();
+        rank = t + 1;
+    }
+    if (tid == 0 && rank == g.kcap && kmax == g.kcap) atomicOr(status, TD_STATUS_BADRANK);
+    // U rows: pivot rows are unit rows; the others solve x L11 = l_a backwards.
+    for (int a = tid; a < m; a += SR_NT) {
+        const int pos = s_rowpos[a];
+        if (pos >= 0 && pos < rank) {
+            for (int c = 0; c < rank; c++) g.U[a + (size_t)c * g.ldu] = (c == pos) ? 1.0 : 0.0;
+            continue;
+        }
+        for (int c = rank - 1; c >= 0; c--) {
+            double x = g.mult[(size_t)a * g.kcap + c];
+            for (int i = c + 1; i < rank; i++)
+                x -= g.U[a + (size_t)i * g.ldu] * g.mult[(size_t)s_pr[i] * g.kcap + c];
+            g.U[a + (size_t)c * g.ldu] = x;
+        }
+    }
+    for (int c = tid; c < rank; c += SR_NT) {
+        g.out_piv[c] = s_pr[c];
+        g.out_idx[c] = sr_row(g, s_pr[c]);
+    }
+    if (tid == 0) *g.out_rank = rank;
+}
+
+// ---------------------------------------------------------------------------
 // Host orchestration
 // ---------------------------------------------------------------------------
 namespace {
@@ -466,6 +627,89 @@ static int grow(HssWS& w, size_t bytes, cudaStream_t st)
         }                                                                              \
     } while (0)
 
+// ADC1: HSS generators U, V (and the skeleton indices) level by level by SRRSC;
+// D and B come from the generators as in Algorithm 2.
+static int srrsc_levels(const tdeig_options& opt, std::vector<HMerge>& H, int Lmax, FillDesc* dfill,
+                        SrrscDesc* dsr, char* sr_base, size_t sr_bytes, int* status, cudaStream_t st)
+{
+    for (int l = Lmax; l >= 1; l--) {
+        std::vector<FillDesc> fills;
+        std::vector<SrrscDesc> sd;
+        Bump S{sr_base, 0, sr_bytes};
+        for (auto& h : H) {
+            if (l > h.L) continue;
+            const int s = h.s, w = 1 << (h.L - l);
+            FillDesc f;
+            memset(&f, 0, sizeof(f));
+            f.d = h.d; f.gam = h.gam; f.mu = h.mu; f.uhat = h.uh; f.v = h.v;
+            for (int q = 0; q < (1 << l); q++) {
+                HNode& nd = h.nodes[hidx(l, q)];
+                const int s0 = h.bounds[q * w], s1 = h.bounds[(q + 1) * w];
+                const int nc = h.K - (s1 - s0);
+                SrrscDesc a;
+                memset(&a, 0, sizeof(a));
+                a.K = h.K; a.s0 = s0; a.s1 = s1; a.kcap = s; a.ldu = nd.ldU;
+                a.d = h.d; a.gam = h.gam; a.mu = h.mu; a.uh = h.uh; a.v = h.v;
+                HNode* c1 = nullptr;
+                HNode* c2 = nullptr;
+                if (l == h.L) {
+                    f.out = nd.D; f.ld = h.mcap; f.nr = f.nc = s1 - s0; f.r0 = f.c0 = s0;
+                    f.rows = f.cols = nullptr;
+                    fills.push_back(f);
+                    a.m = s1 - s0; a.base = s0;
+                } else {
+                    c1 = &h.nodes[hidx(l + 1, 2 * q)];
+                    c2 = &h.nodes[hidx(l + 1, 2 * q + 1)];
+                    f.ld = s; f.r0 = f.c0 = 0;
+                    f.out = c1->B; f.rows = c1->I; f.nr = c1->kU; f.cols = c2->J; f.nc = c2->kV;
+                    fills.push_back(f);
+                    f.out = c2->B; f.rows = c2->I; f.nr = c2->kU; f.cols = c1->J; f.nc = c1->kV;
+                    fills.push_back(f);
+                }
+                for (int side = 0; side < 2; side++) {
+                    SrrscDesc b = a;
+                    b.side = side;
+                    if (c1) {
+                        b.map1 = side ? c1->J : c1->I;
+                        b.n1 = side ? c1->kV : c1->kU;
+                        b.map2 = side ? c2->J : c2->I;
+                        b.m = b.n1 + (side ? c2->kV : c2->kU);
+                    }
+                    b.invd = S.take<float>((size_t)b.m * nc);
+                    b.g = S.take<double>(b.m);
+                    b.h = S.take<double>(nc);
+                    b.gf = S.take<float>(b.m);
+                    b.hf = S.take<float>(nc);
+                    b.actr = S.take<unsigned char>(b.m);
+                    b.actc = S.take<unsigned char>(nc);
+                    b.mult = S.take<double>((size_t)b.m * s);
+                    b.U = side ? nd.V : nd.U;
+                    b.out_idx = side ? nd.J : nd.I;
+                    b.out_piv = side ? nd.pivJ : nd.pivI;
+                    b.out_rank = nd.rk + side;
+                    sd.push_back(b);
+                }
+            }
+        }
+        if (S.off > S.cap || sd.size() > 8192) return TDEIG_ENOMEM;
+        launch_fill(fills, dfill, st);
+        HCU(cudaMemcpyAsync(dsr, sd.data(), sd.size() * sizeof(SrrscDesc), cudaMemcpyHostToDevice, st));
+        k_srrsc<<<(unsigned)sd.size(), SR_NT, 0, st>>>(dsr, opt.tol, status);
+        g_td_launches++;
+        HCU(cudaGetLastError());
+        for (auto& h : H) {
+            if (l > h.L) continue;
+            for (int q = 0; q < (1 << l); q++) {
+                HNode& nd = h.nodes[hidx(l, q)];
+                HCU(cudaMemcpyAsync(&nd.kU, nd.rk, sizeof(int), cudaMemcpyDeviceToHost, st));
+                HCU(cudaMemcpyAsync(&nd.kV, nd.rk + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+            }
+        }
+        HCU(cudaStreamSynchronize(st));
+    }
+    return TDEIG_OK;
+}
+
 static int leaf_levels(int K, int m)
 {
     if (K < 2 * m) return K >= 2 ? 1 : 0;
@@ -476,8 +720,10 @@ static int leaf_levels(int K, int m)
 int hss_update_level(const tdeig_options& opt, int variant, int prec,
                      const std::vector<MergeDesc>& merges, const MergeDesc* dev_merges,
                      const std::vector<int>& Kv, const LevelWS& lws, HssWS& hws, int* status,
-                     cudaStream_t st, std::string& js)
+                     cudaStream_t st, std::string& js,
+                     const std::function<int(const char*)>& mark)
 {
+    double fl_dense = 0.0, fl_sample = 0.0, fl_build = 0.0, fl_mult = 0.0;
     (void)prec; (void)dev_merges; (void)status;
     const int p_over = opt.oversample;
     std::vector<HMerge> H;
@@ -490,7 +736,10 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
         const int L = leaf_levels(K, opt.hss_leaf);
         const int mcap_guess = (K + (1 << L) - 1) / (1 << L) + 2 * opt.boundary_shift + 2;
         const int s_max = opt.rank_cap + p_over;
-        const bool fits = L >= 1 && id_smem(s_max, std::max(mcap_guess, 2 * s_max)) <= 220 * 1024;
+        const bool fits =
+            L >= 1 && (variant == TDEIG_MODE_ADC1
+                           ? mcap_guess <= SR_MAXM
+                           : id_smem(s_max, std::max(mcap_guess, 2 * s_max)) <= 220 * 1024);
         if (K <= opt.hss_threshold || !fits) {
             GemmDesc g;
             memset(&g, 0, sizeof(g));
@@ -520,12 +769,15 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
     if (rc) return rc;
     Bump b0{hws.base, 0, hws.cap};
     GemmDesc* dgemm = b0.take<GemmDesc>(4096);
-    if (!dense.empty()) hss_launch_gemm(dense, dgemm, st);
+    if (!dense.empty()) fl_dense += hss_launch_gemm(dense, dgemm, st);
     if (H.empty()) return TDEIG_OK;
-    if (variant == TDEIG_MODE_ADC1) return TDEIG_ENOTIMPL;
+    const bool adc1 = (variant == TDEIG_MODE_ADC1);
 
     // ---- rank estimate and boundary moves (ADC2) -------------------------
-    {
+    if (adc1) {
+        // no sampling: the generator columns only bound the ranks SRRSC may reach
+        for (auto& h : H) h.r = std::min(opt.rank_cap, SR_MAXK - p_over);
+    } else {
         std::vector<RankDesc> rd;
         int* ib = b0.take<int>(desc_bytes / 8);
         size_t o = 0;
@@ -567,6 +819,14 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
         total += 2 * nl * (4 * s + 2) * 4;                     // I, J, piv, rk
         for (int l = 1; l <= h.L; l++) total += 2 * n * (((size_t)1 << l) * s) * 8;  // G, F
         total += 2 * nl * 8 * 256;                             // alignment slack
+    }
+    size_t sr_bytes = 0;   // ADC1 elimination scratch, reused level by level
+    if (adc1) {
+        for (auto& h : H) {
+            const size_t nl = (size_t)1 << h.L, K = h.K, mc = std::max(h.mcap, 2 * h.s);
+            sr_bytes += 2 * nl * (mc * K * 4 + (mc + K) * 14 + mc * h.s * 8 + 8 * 256);
+        }
+        total += sr_bytes + 2 * 8192 * sizeof(SrrscDesc);
     }
     if (total > hws.cap) {
         // keep the small region (bounds already read back) and regrow
@@ -619,11 +879,27 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
             h.F[l] = B.take<double>((size_t)nn * ((size_t)1 << l) * s);
         }
     }
+    SrrscDesc* dsr = nullptr;
+    char* sr_base = nullptr;
+    if (adc1) {
+        dsr = B.take<SrrscDesc>(8192);
+        sr_base = B.take<char>(sr_bytes);
+    }
     if (B.off > B.cap) return TDEIG_ENOMEM;
 
+    int Lmax = 0;
+    for (auto& h : H) Lmax = std::max(Lmax, h.L);
+    if (adc1) {
+        if ((rc = mark("hss_build"))) return rc;
+        rc = srrsc_levels(opt, H, Lmax, dfill, dsr, sr_base, sr_bytes, status, st);
+        if (rc) return rc;
+    }
+
+    if (!adc1 && (rc = mark("hss_sample"))) return rc;
     // ---- sampling: Omega, Y = A Omega, Z = A^T Omega (Omega(1) = Omega(2)) --
     std::vector<GemmDesc> gl;
     for (auto& h : H) {
+        if (adc1) break;
         const int64_t tot = (int64_t)h.K * h.s;
         k_philox_omega<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(h.Om, h.K, h.s, opt.seed,
                                                                       (unsigned)h.node_id);
@@ -636,13 +912,11 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
         g.transA = 1; g.C = h.Z;
         gl.push_back(g);
     }
-    hss_launch_gemm(gl, dgemm, st);
+    fl_sample += hss_launch_gemm(gl, dgemm, st);
 
+    if (!adc1 && (rc = mark("hss_build"))) return rc;
     // ---- Algorithm 2, levels L..1 -------------------------------------------
-    int Lmax = 0;
-    for (auto& h : H) Lmax = std::max(Lmax, h.L);
-    std::vector<int> rk_host;
-    for (int l = Lmax; l >= 1; l--) {
+    for (int l = adc1 ? 0 : Lmax; l >= 1; l--) {
         std::vector<FillDesc> fills;
         std::vector<GatherDesc> gathers;
         std::vector<GemmDesc> upd;
@@ -724,7 +998,7 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
         }
         launch_fill(fills, dfill, st);
         launch_gather(gathers, dgat, st);
-        hss_launch_gemm(upd, dgemm, st);
+        fl_build += hss_launch_gemm(upd, dgemm, st);
         // global row maps of the parents' stacked rows: children skeletons
         {
             size_t ii = 0;
@@ -807,7 +1081,7 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
                     }
                 }
             }
-            hss_launch_gemm(yz, dgemm, st);
+            fl_build += hss_launch_gemm(yz, dgemm, st);
         }
     }
     // root: B of its two children
@@ -827,6 +1101,7 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
         launch_fill(fills, dfill, st);
     }
 
+    if ((rc = mark("hss_mult"))) return rc;
     // ---- Algorithm 3: X H with X = W[:, surv] (n x K) ----------------------
     auto colU = [](HMerge& h, int l, int q) {
         int base = (q >> 1) * 2 * h.s;
@@ -851,7 +1126,7 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
                 g1.push_back(g);
             }
         }
-        hss_launch_gemm(g1, dgemm, st);
+        fl_mult += hss_launch_gemm(g1, dgemm, st);
         for (int l = Lmax - 1; l >= 1; l--) {
             std::vector<GemmDesc> gu;
             for (auto& h : H) {
@@ -869,7 +1144,7 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
                     gu.push_back(g);
                 }
             }
-            hss_launch_gemm(gu, dgemm, st);
+            fl_mult += hss_launch_gemm(gu, dgemm, st);
         }
         // downsweep
         for (int l = 1; l <= Lmax; l++) {
@@ -900,8 +1175,8 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
                     }
                 }
             }
-            hss_launch_gemm(gf, dgemm, st);
-            hss_launch_gemm(gv, dgemm, st);
+            fl_mult += hss_launch_gemm(gf, dgemm, st);
+            fl_mult += hss_launch_gemm(gv, dgemm, st);
         }
         // leaves: out[:, t_i] = X_i D_i + F_i V_i^T (columns scattered to their final positions)
         std::vector<GemmDesc> gd, gvv;
@@ -925,13 +1200,16 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
                 gvv.push_back(v);
             }
         }
-        hss_launch_gemm(gd, dgemm, st);
-        hss_launch_gemm(gvv, dgemm, st);
+        fl_mult += hss_launch_gemm(gd, dgemm, st);
+        fl_mult += hss_launch_gemm(gvv, dgemm, st);
     }
     HCU(cudaGetLastError());
 
     // statistics
     char buf[256];
+    snprintf(buf, sizeof(buf), "%s{\"flops\":{\"dense\":%.6e,\"sample\":%.6e,\"build\":%.6e,\"mult\":%.6e}}",
+             js.empty() ? "" : ",", fl_dense, fl_sample, fl_build, fl_mult);
+    js += buf;
     for (auto& h : H) {
         int kmax = 0;
         double ksum = 0.0;

@@ -549,7 +549,7 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
         MARK(any_hss ? "hss_update" : "update", lv);
         if (any_hss) {
             rc = hss_update_level(h->opt, variant, prec, L.merges, Md, Kh, lws, h->hss, status, st,
-                                  hss_js);
+                                  hss_js, [&](const char* nm) { return mark(nm, lv); });
             if (rc) return rc;
         } else {
             td_launch_update_dense(Md, nm, L.tiles, lws, st);

@@ -58,7 +58,8 @@ def test_adc2_toeplitz(N, thr):
     assert metrics.eig_error(lam, ex) <= 1e-12
     check(a, b, lam, Q, dc.MODE_ADC2, thr)
     for h in hm:
-        assert 1 <= h["r"] <= 100 and h["kmax"] <= h["s"]
+        if "r" in h:
+            assert 1 <= h["r"] <= 100 and h["kmax"] <= h["s"]
 
 
 @pytest.mark.parametrize("gen,thr", [("clement", 300), ("legendre", 200), ("hermite", 250),
@@ -71,6 +72,21 @@ def test_adc2_families(gen, thr):
         hm = hss_merges(s)
     assert len(hm) > 0
     check(a, b, lam, Q, dc.MODE_ADC2, thr, leaf=64)
+
+
+@pytest.mark.parametrize("gen,N,thr,leaf", [("toeplitz", 2050, 500, 128), ("toeplitz", 4099, 1000, 128),
+                                            ("clement", 1201, 300, 64), ("legendre", 1201, 200, 64)])
+def test_adc1(gen, N, thr, leaf):
+    a, b = getattr(inputs, gen)(N)
+    with solver(hss_threshold=thr, hss_leaf=leaf) as s:
+        lam, Q = gpu(s, a, b, "adc1")
+        hm = hss_merges(s)
+    assert any("kmax" in h for h in hm)
+    if gen == "toeplitz":
+        k = np.arange(1, N + 1)
+        ex = np.sort(2 + 2 * np.cos(k * np.pi / (N + 1)))
+        assert metrics.eig_error(lam, ex) <= 1e-12
+    check(a, b, lam, Q, dc.MODE_ADC1, thr, leaf=leaf)
 
 
 def test_adc2_heavy_deflation_and_random():

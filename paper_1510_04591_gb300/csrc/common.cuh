@@ -51,6 +51,7 @@ struct LeafDesc {
 struct LevelWS {
     double *dsort, *zsort, *dK, *zK, *wK, *lamK, *gamK, *muK, *uhat, *vv, *rot_c, *rot_s;
     int *src, *keep, *survIdx, *deflIdx, *posNew, *posDefl, *rot_j, *rot_i, *gemmCol;
+    int* gemmW;        // column of W used at product position p: survIdx[gemmCol[p]]
     int *K, *nrot;     // per merge
     int* kgrp;         // per merge: K1, Km
     double* rho;       // per merge, after normalisation of z

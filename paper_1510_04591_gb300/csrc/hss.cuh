@@ -29,6 +29,9 @@ struct GemmDesc {
     int transA, transB;
     double alpha, beta;
     int tile0, tiles_m;
+    // optional block structure (split products only): rows < rsplit use k < ktop_end,
+    // rows >= rsplit use k >= kbot_beg (the other entries of op(A) are zero); 0 = none
+    int rsplit, ktop_end, kbot_beg;
 };
 
 // out[a + b ld] = uhat[row] v[col] / (d[row] - lambda[col]) (Remark 1), for
@@ -100,9 +103,11 @@ struct RankDesc {
 double hss_launch_gemm(const std::vector<GemmDesc>& g, GemmDesc* dev, cudaStream_t st);
 void hss_free(HssWS& w);
 // mark(name) records a timing event that starts sub-stage `name` (sampling,
-// construction, multiplication) on the solve's stream.
+// construction, multiplication) on the solve's stream.  With split != NULL the
+// sampling and Algorithm 3 products run as split-precision tensor-core products.
+struct SplitWS;
 int hss_update_level(const tdeig_options& opt, int variant, int prec,
                      const std::vector<MergeDesc>& merges, const MergeDesc* dev_merges,
                      const std::vector<int>& K, const LevelWS& lws, HssWS& hws, int* status,
                      cudaStream_t st, std::string& stats,
-                     const std::function<int(const char*)>& mark);
+                     const std::function<int(const char*)>& mark, SplitWS* split);

@@ -393,6 +393,7 @@ __global__ void __launch_bounds__(PREP_NT) k_prep(const MergeDesc* M, LevelWS ws
         if (k < K) {
             int p = (t == 1) ? run1 + p1 : (t == 3) ? K1 + run3 + p3 : K1 + Km + run2 + p2;
             ws.gemmCol[g0 + p] = k;
+            ws.gemmW[g0 + p] = ws.survIdx[g0 + k];
         }
         run1 += tot1;
         run3 += tot3;

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "hss.cuh"
+#include "split.cuh"
 
 #define HSS_NT 256
 
@@ -721,8 +722,16 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
                      const std::vector<MergeDesc>& merges, const MergeDesc* dev_merges,
                      const std::vector<int>& Kv, const LevelWS& lws, HssWS& hws, int* status,
                      cudaStream_t st, std::string& js,
-                     const std::function<int(const char*)>& mark)
+                     const std::function<int(const char*)>& mark, SplitWS* split)
 {
+    int prc = TDEIG_OK;
+    auto run = [&](const std::vector<GemmDesc>& gv, GemmDesc* dev) -> double {
+        if (!split) return hss_launch_gemm(gv, dev, st);
+        int r = TDEIG_OK;
+        double f = split_launch_gemm(gv, *split, st, &r);
+        if (r && !prc) prc = r;
+        return f;
+    };
     double fl_dense = 0.0, fl_sample = 0.0, fl_build = 0.0, fl_mult = 0.0;
     (void)prec; (void)dev_merges; (void)status;
     const int p_over = opt.oversample;
@@ -769,7 +778,7 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
     if (rc) return rc;
     Bump b0{hws.base, 0, hws.cap};
     GemmDesc* dgemm = b0.take<GemmDesc>(4096);
-    if (!dense.empty()) fl_dense += hss_launch_gemm(dense, dgemm, st);
+    if (!dense.empty()) fl_dense += run(dense, dgemm);
     if (H.empty()) return TDEIG_OK;
     const bool adc1 = (variant == TDEIG_MODE_ADC1);
 
@@ -912,6 +921,9 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
         g.transA = 1; g.C = h.Z;
         gl.push_back(g);
     }
+    // Sampling stays FP64 in every precision mode: Phi = Y - D Omega cancels the
+    // dominant near-diagonal part of Y exactly, so slice errors in Y would be
+    // amplified relative to Phi and inflate the ID ranks.
     fl_sample += hss_launch_gemm(gl, dgemm, st);
 
     if (!adc1 && (rc = mark("hss_build"))) return rc;
@@ -1126,7 +1138,7 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
                 g1.push_back(g);
             }
         }
-        fl_mult += hss_launch_gemm(g1, dgemm, st);
+        fl_mult += run(g1, dgemm);
         for (int l = Lmax - 1; l >= 1; l--) {
             std::vector<GemmDesc> gu;
             for (auto& h : H) {
@@ -1144,7 +1156,7 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
                     gu.push_back(g);
                 }
             }
-            fl_mult += hss_launch_gemm(gu, dgemm, st);
+            fl_mult += run(gu, dgemm);
         }
         // downsweep
         for (int l = 1; l <= Lmax; l++) {
@@ -1175,8 +1187,8 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
                     }
                 }
             }
-            fl_mult += hss_launch_gemm(gf, dgemm, st);
-            fl_mult += hss_launch_gemm(gv, dgemm, st);
+            fl_mult += run(gf, dgemm);
+            fl_mult += run(gv, dgemm);
         }
         // leaves: out[:, t_i] = X_i D_i + F_i V_i^T (columns scattered to their final positions)
         std::vector<GemmDesc> gd, gvv;
@@ -1200,8 +1212,8 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
                 gvv.push_back(v);
             }
         }
-        fl_mult += hss_launch_gemm(gd, dgemm, st);
-        fl_mult += hss_launch_gemm(gvv, dgemm, st);
+        fl_mult += run(gd, dgemm);
+        fl_mult += run(gvv, dgemm);
     }
     HCU(cudaGetLastError());
 
@@ -1225,5 +1237,5 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
                  js.empty() ? "" : ",", h.n, h.K, h.L, h.r, h.s, kmax, cnt ? ksum / cnt : 0.0);
         js += buf;
     }
-    return TDEIG_OK;
+    return prc;
 }

@@ -13,6 +13,7 @@
 #include "../../include/tdeig.h"
 #include "common.cuh"
 #include "hss.cuh"
+#include "split.cuh"
 
 struct LevelPlan {
     std::vector<MergeDesc> merges;
@@ -38,6 +39,7 @@ struct tdeig_ctx {
     size_t ws_bytes = 0;
     std::string stats;
     HssWS hss;                         // HSS generators and Algorithm 3 intermediates
+    SplitWS split;                     // BF16 slices of split-precision products
     std::vector<cudaEvent_t> events;   // stage timing events, reused across solves
     std::vector<const char*> ev_names;
     std::vector<int> ev_level;
@@ -112,6 +114,7 @@ extern "C" int tdeig_destroy(tdeig_handle h)
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->ws) cudaFree(h->ws);
     hss_free(h->hss);
+    split_free(h->split);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -284,7 +287,7 @@ static void build_plan(Plan& P, const Bufs& B, int leaf)
 
 static size_t level_ws_bytes(int64_t R, int64_t Mmax)
 {
-    return (size_t)R * (12 * sizeof(double) + 9 * sizeof(int)) + Mmax * (4 * sizeof(int) + 8) +
+    return (size_t)R * (12 * sizeof(double) + 10 * sizeof(int)) + Mmax * (4 * sizeof(int) + 8) +
            32 * 256;
 }
 
@@ -311,6 +314,7 @@ static void carve_level_ws(Arena& a, LevelWS& w, int64_t R, int64_t Mmax)
     w.rot_j = a.take<int>(R);
     w.rot_i = a.take<int>(R);
     w.gemmCol = a.take<int>(R);
+    w.gemmW = a.take<int>(R);
     w.K = a.take<int>(Mmax);
     w.nrot = a.take<int>(Mmax);
     w.kgrp = a.take<int>(2 * Mmax);
@@ -535,12 +539,18 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
         MARK("secular", lv);
         td_launch_secular(Md, nm, L.rows, lws, status, st);
         bool any_hss = false;
-        std::vector<int> Kh;
-        if (variant != TDEIG_MODE_DENSE && L.nmax > h->opt.hss_threshold) {
+        const bool split = (prec == TDEIG_PREC_SPLIT);
+        std::vector<int> Kh, Gh;
+        const bool hss_level = variant != TDEIG_MODE_DENSE && L.nmax > h->opt.hss_threshold;
+        if (hss_level || split) {
+            // sizes of the deflated problems, needed to size the launches below
             Kh.resize(nm);
+            Gh.resize(2 * nm);
             CU(cudaMemcpyAsync(Kh.data(), lws.K, nm * sizeof(int), cudaMemcpyDeviceToHost, st));
+            CU(cudaMemcpyAsync(Gh.data(), lws.kgrp, 2 * nm * sizeof(int), cudaMemcpyDeviceToHost, st));
             CU(cudaStreamSynchronize(st));
-            for (int i = 0; i < nm; i++) any_hss |= Kh[i] > h->opt.hss_threshold;
+            if (hss_level)
+                for (int i = 0; i < nm; i++) any_hss |= Kh[i] > h->opt.hss_threshold;
         }
         MARK("lowner_cauchy", lv);
         td_launch_lowner_cauchy(Md, nm, L.rows, L.kmax, lws, any_hss ? 1 : 2, st);
@@ -549,7 +559,26 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
         MARK(any_hss ? "hss_update" : "update", lv);
         if (any_hss) {
             rc = hss_update_level(h->opt, variant, prec, L.merges, Md, Kh, lws, h->hss, status, st,
-                                  hss_js, [&](const char* nm) { return mark(nm, lv); });
+                                  hss_js, [&](const char* nm) { return mark(nm, lv); },
+                                  split ? &h->split : nullptr);
+            if (rc) return rc;
+        } else if (split) {
+            // block-structured update as split-precision tensor-core products
+            std::vector<GemmDesc> gd;
+            for (int i = 0; i < nm; i++) {
+                const MergeDesc& m = L.merges[i];
+                const int K = Kh[i];
+                if (K == 0) continue;
+                GemmDesc g;
+                memset(&g, 0, sizeof(g));
+                g.A = m.W; g.lda = m.n; g.acol = lws.gemmW + m.g0;
+                g.B = m.qhat; g.ldb = K;
+                g.C = m.qout; g.ldc = m.n; g.ccol = lws.posNew + m.g0;
+                g.M = m.n; g.N = K; g.Kd = K; g.alpha = 1.0;
+                g.rsplit = m.n1; g.ktop_end = Gh[2 * i] + Gh[2 * i + 1]; g.kbot_beg = Gh[2 * i];
+                gd.push_back(g);
+            }
+            split_launch_gemm(gd, h->split, st, &rc);
             if (rc) return rc;
         } else {
             td_launch_update_dense(Md, nm, L.tiles, lws, st);

@@ -47,7 +47,12 @@ enum {
     TDEIG_MODE_MASK = 0xff,
     TDEIG_PREC_FP64 = 0 << 8,     /* FP64 products */
     TDEIG_PREC_SPLIT = 1 << 8,    /* split-precision tensor-core products */
-    TDEIG_PREC_MASK = 0xf << 8
+    TDEIG_PREC_MASK = 0xf << 8,
+    /* DENSE | FP64 with device buffers only: capture the whole launch sequence
+     * (every level of every matrix) in a CUDA graph on the first call and
+     * replay it on later calls with the same sizes and buffers.  Ignored
+     * otherwise (those modes read deflated sizes back to the host). */
+    TDEIG_FLAG_GRAPH = 1 << 12
 };
 
 enum {

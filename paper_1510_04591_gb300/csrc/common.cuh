@@ -72,10 +72,16 @@ void td_launch_secular(const MergeDesc* M, int nmerge, int rows, const LevelWS& 
                        cudaStream_t st);
 void td_launch_lowner_cauchy(const MergeDesc* M, int nmerge, int rows, int kmax, const LevelWS& ws,
                              int write_qhat, cudaStream_t st);
-void td_launch_update_dense(const MergeDesc* M, int nmerge, int total_tiles, const LevelWS& ws,
-                            cudaStream_t st);
+// Tile-shape variants of the FP64 update product (picked per level by the autotuner).
+#define TD_GEMM_VARIANTS 4
+void td_gemm_tiles(int variant, int n, int* bm, int* bn);
+void td_launch_update_dense(const MergeDesc* M, const int* toff, int nmerge, int total_tiles,
+                            int variant, const LevelWS& ws, cudaStream_t st);
 void td_launch_finish(const MergeDesc* M, int nmerge, int nmax, const LevelWS& ws, cudaStream_t st);
 void td_launch_order(const MergeDesc* M, int nmerge, const LevelWS& ws, cudaStream_t st);
+
+// Largest total of N^2 (eigenvector entries) solved in one batched pass.
+#define TD_BATCH_CHUNK ((int64_t)1 << 30)
 
 #define TD_GEMM_BM 64
 #define TD_GEMM_BN 64

@@ -745,89 +745,112 @@ void td_launch_finish(const MergeDesc* M, int nmerge, int nmax, const LevelWS& w
 
 // ---------------------------------------------------------------------------
 // Dense update (plain DC): C = W[:, surv] * Qhat, C column k written to the
-// output column posNew[k].  FP64 on the CUDA cores: a 64 x 64 x 16 shared-
-// memory tile, 4 x 4 outputs per thread (rows tx + 16 a, cols ty + 16 b).
-// On this part FP64 FMA issue (~1.2 TFLOP/s measured) is at least as fast as
-// the FP64 mma.sync path (~1.05 TFLOP/s measured), so the SIMT form is used.
+// output column posNew[k].  FP64 on the CUDA cores: a BM x BN x 16 shared-
+// memory tile, (BM/16) x (BN/16) outputs per thread (rows tx + 16 a, cols
+// ty + 16 b).  On this part FP64 FMA issue (~1.2 TFLOP/s measured) is at least
+// as fast as the FP64 mma.sync path (~1.05 TFLOP/s measured), so the SIMT form
+// is used.  Tile shapes are chosen per level by the autotuner in the host code;
+// toff[m] is the first tile of merge m for the chosen shape (prefix sums).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_gemm_f64(const MergeDesc* M, int nmerge, LevelWS ws)
+template <int BM, int BN>
+__global__ void __launch_bounds__(256) k_gemm_f64(const MergeDesc* M, const int* toff, int nmerge,
+                                                 LevelWS ws)
 {
-    __shared__ double As[TD_GEMM_BK][TD_GEMM_BM];
-    __shared__ double Bs[TD_GEMM_BK][TD_GEMM_BN + 1];
+    constexpr int TA = BM / 16, TB = BN / 16;
+    __shared__ double As[TD_GEMM_BK][BM];
+    __shared__ double Bs[TD_GEMM_BK][BN + 1];
     int lo = 0, hi = nmerge - 1;
     const int bid = blockIdx.x;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
-        if (M[mid].tile0 <= bid) lo = mid; else hi = mid - 1;
+        if (toff[mid] <= bid) lo = mid; else hi = mid - 1;
     }
     const MergeDesc& md = M[lo];
     const int m = lo;
     const int n = md.n, g0 = md.g0;
     const int K = ws.K[m];
-    const int local = bid - md.tile0;
-    const int tm = local % md.tiles_m, tn = local / md.tiles_m;
-    const int row0 = tm * TD_GEMM_BM, col0 = tn * TD_GEMM_BN;
+    const int tiles_m = td_cdiv(n, BM);
+    const int local = bid - toff[lo];
+    const int tm = local % tiles_m, tn = local / tiles_m;
+    const int row0 = tm * BM, col0 = tn * BN;
     if (col0 >= K || K == 0) return;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int* surv = ws.survIdx + g0;
-    const int* gcol = ws.gemmCol + g0;
+    const int* wcol = ws.gemmW + g0;
     const double* W = md.W;
     const double* B = md.qhat;   // rows already in product order
     // Block structure of diag(Q1, Q2) after deflation: child-1 rows see only
     // product positions [0, K1 + Km), child-2 rows only [K1, K).
     const int K1 = ws.kgrp[2 * m], Km = ws.kgrp[2 * m + 1];
     const int kbeg = (row0 >= md.n1) ? K1 : 0;
-    const int kend = (row0 + TD_GEMM_BM <= md.n1) ? K1 + Km : K;
-    double acc[4][4];
+    const int kend = (row0 + BM <= md.n1) ? K1 + Km : K;
+    double acc[TA][TB];
 #pragma unroll
-    for (int a = 0; a < 4; a++)
+    for (int a = 0; a < TA; a++)
 #pragma unroll
-        for (int b = 0; b < 4; b++) acc[a][b] = 0.0;
+        for (int b = 0; b < TB; b++) acc[a][b] = 0.0;
 
     for (int k0 = kbeg; k0 < kend; k0 += TD_GEMM_BK) {
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            int idx = threadIdx.x + 256 * q;
-            int kk = idx >> 6, r = idx & 63;
-            int k = k0 + kk, row = row0 + r;
-            As[kk][r] = (k < kend && row < n) ? W[(int64_t)surv[gcol[k]] * n + row] : 0.0;
-            int kb = idx & 15, c = idx >> 4;
-            int kg = k0 + kb, cg = col0 + c;
+        for (int q = 0; q < TA; q++) {
+            const int idx = threadIdx.x + 256 * q;
+            const int kk = idx / BM, r = idx % BM;
+            const int k = k0 + kk, row = row0 + r;
+            As[kk][r] = (k < kend && row < n) ? W[(int64_t)wcol[k] * n + row] : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < TB; q++) {
+            const int idx = threadIdx.x + 256 * q;
+            const int kb = idx & 15, c = idx >> 4;
+            const int kg = k0 + kb, cg = col0 + c;
             Bs[kb][c] = (kg < kend && cg < K) ? B[(int64_t)cg * K + kg] : 0.0;
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < TD_GEMM_BK; kk++) {
-            double av[4], bv[4];
+            double av[TA], bv[TB];
 #pragma unroll
-            for (int a = 0; a < 4; a++) av[a] = As[kk][tx + 16 * a];
+            for (int a = 0; a < TA; a++) av[a] = As[kk][tx + 16 * a];
 #pragma unroll
-            for (int b = 0; b < 4; b++) bv[b] = Bs[kk][ty + 16 * b];
+            for (int b = 0; b < TB; b++) bv[b] = Bs[kk][ty + 16 * b];
 #pragma unroll
-            for (int a = 0; a < 4; a++)
+            for (int a = 0; a < TA; a++)
 #pragma unroll
-                for (int b = 0; b < 4; b++) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+                for (int b = 0; b < TB; b++) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int b = 0; b < 4; b++) {
-        int c = col0 + ty + 16 * b;
+    for (int b = 0; b < TB; b++) {
+        const int c = col0 + ty + 16 * b;
         if (c >= K) continue;
         double* out = md.qout + (int64_t)ws.posNew[g0 + c] * n;
 #pragma unroll
-        for (int a = 0; a < 4; a++) {
-            int r = row0 + tx + 16 * a;
+        for (int a = 0; a < TA; a++) {
+            const int r = row0 + tx + 16 * a;
             if (r < n) out[r] = acc[a][b];
         }
     }
 }
 
-void td_launch_update_dense(const MergeDesc* M, int nmerge, int total_tiles, const LevelWS& ws,
-                            cudaStream_t st)
+void td_gemm_tiles(int variant, int n, int* bm, int* bn)
+{
+    static const int shapes[TD_GEMM_VARIANTS][2] = {{64, 64}, {32, 32}, {128, 64}, {64, 32}};
+    *bm = shapes[variant][0];
+    *bn = shapes[variant][1];
+    (void)n;
+}
+
+void td_launch_update_dense(const MergeDesc* M, const int* toff, int nmerge, int total_tiles,
+                            int variant, const LevelWS& ws, cudaStream_t st)
 {
     if (total_tiles <= 0) return;
-    k_gemm_f64<<<total_tiles, 256, 0, st>>>(M, nmerge, ws); g_td_launches++;
+    switch (variant) {
+    case 1: k_gemm_f64<32, 32><<<total_tiles, 256, 0, st>>>(M, toff, nmerge, ws); break;
+    case 2: k_gemm_f64<128, 64><<<total_tiles, 256, 0, st>>>(M, toff, nmerge, ws); break;
+    case 3: k_gemm_f64<64, 32><<<total_tiles, 256, 0, st>>>(M, toff, nmerge, ws); break;
+    default: k_gemm_f64<64, 64><<<total_tiles, 256, 0, st>>>(M, toff, nmerge, ws); break;
+    }
+    g_td_launches++;
 }
 
 // Order kernel launcher (separate so the HSS path can reuse it).

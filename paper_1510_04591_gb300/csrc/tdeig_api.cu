@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <chrono>
 #include <string>
+#include <map>
 #include <vector>
 
 #include "../../include/tdeig.h"
@@ -19,6 +20,31 @@ struct LevelPlan {
     std::vector<MergeDesc> merges;
     int nmax = 0, rows = 0, tiles = 0, kmax = 0;
     size_t desc_off = 0;  // index of the first descriptor in the device array
+    std::vector<int> toff[TD_GEMM_VARIANTS];   // per tile shape: first tile of each merge
+    int tiles_v[TD_GEMM_VARIANTS] = {0};
+    int* dev_toff[TD_GEMM_VARIANTS] = {nullptr};
+};
+
+// Autotuner key of a DC level: size class of its merges and their number.
+static int tune_key(const LevelPlan& L)
+{
+    int a = 0, b = 0;
+    while ((1 << a) < L.nmax) a++;
+    while ((1 << b) < (int)L.merges.size()) b++;
+    return a * 64 + b;
+}
+
+// A captured solve (dense FP64 mode with device buffers): replayed when the
+// sizes, buffers and workspace are the same as at capture time.
+struct GraphEntry {
+    std::vector<int64_t> N;
+    const void *d, *e, *lam, *Q;
+    int mode = 0;
+    char* ws = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int* status = nullptr;
+    double* scale = nullptr;
+    int64_t batch = 0;
 };
 
 struct Plan {
@@ -43,6 +69,10 @@ struct tdeig_ctx {
     std::vector<cudaEvent_t> events;   // stage timing events, reused across solves
     std::vector<const char*> ev_names;
     std::vector<int> ev_level;
+    std::map<int, int> tuned;          // autotuner: level key -> tile shape of the update product
+    std::vector<std::pair<int, std::vector<int>>> tuning;   // level key -> event indices of a trial
+    std::vector<cudaEvent_t> tune_ev;  // events of the trials of the current solve
+    GraphEntry graph;                  // the last captured solve
 };
 
 static const char* kStatusMsg[] = {
@@ -116,6 +146,8 @@ extern "C" int tdeig_destroy(tdeig_handle h)
     hss_free(h->hss);
     split_free(h->split);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->tune_ev) cudaEventDestroy(e);
+    if (h->graph.exec) cudaGraphExecDestroy(h->graph.exec);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
     return TDEIG_OK;
@@ -281,6 +313,18 @@ static void build_plan(Plan& P, const Bufs& B, int leaf)
         L.kmax = L.nmax;
         L.desc_off = desc;
         desc += L.merges.size();
+        // first tile of every merge for each update-product tile shape
+        for (int v = 0; v < TD_GEMM_VARIANTS; v++) {
+            int bm, bn;
+            td_gemm_tiles(v, 0, &bm, &bn);
+            L.toff[v].resize(L.merges.size());
+            int t = 0;
+            for (size_t i = 0; i < L.merges.size(); i++) {
+                L.toff[v][i] = t;
+                t += td_cdiv(L.merges[i].n, bm) * td_cdiv(L.merges[i].n, bn);
+            }
+            L.tiles_v[v] = t;
+        }
     }
     P.qoff_total = qoff;
 }
@@ -397,7 +441,9 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     const int leaf = h->opt.leaf;
     const int variant = mode & TDEIG_MODE_MASK;
     const int prec = mode & TDEIG_PREC_MASK;
-    if (variant > TDEIG_MODE_ADC2 || (mode & ~(TDEIG_MODE_MASK | TDEIG_PREC_MASK))) return TDEIG_EINVAL;
+    if (variant > TDEIG_MODE_ADC2 ||
+        (mode & ~(TDEIG_MODE_MASK | TDEIG_PREC_MASK | TDEIG_FLAG_GRAPH)))
+        return TDEIG_EINVAL;
     if (prec != TDEIG_PREC_FP64 && prec != TDEIG_PREC_SPLIT) return TDEIG_EINVAL;
     auto t_start = std::chrono::steady_clock::now();
     const long long launches0 = g_td_launches;
@@ -424,6 +470,47 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     const bool d_dev = is_device_ptr(d), e_dev = is_device_ptr(e);
     const bool l_dev = is_device_ptr(lam_out), q_dev = Q_out && is_device_ptr(Q_out);
 
+    // CUDA-graph mode: dense FP64 with device buffers has no host round trip,
+    // so the whole launch sequence (every level of every matrix) is captured
+    // once and replayed while the sizes, buffers and workspace stay the same.
+    const bool graph = (mode & TDEIG_FLAG_GRAPH) && variant == TDEIG_MODE_DENSE &&
+                       prec == TDEIG_PREC_FP64 && d_dev && (e_dev || !e) && l_dev && q_dev;
+    GraphEntry& G = h->graph;
+    if (graph && G.exec && G.N == P.N && G.d == d && G.e == e && G.lam == lam_out && G.Q == Q_out &&
+        G.mode == mode && G.ws == h->ws) {
+        CU(cudaGraphLaunch(G.exec, st));
+        int hs = 0;
+        std::vector<double> sc(batch);
+        CU(cudaMemcpyAsync(&hs, G.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(sc.data(), G.scale, batch * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+        char buf[160];
+        snprintf(buf, sizeof(buf), "{\"graph\":\"replay\",\"seconds\":%.6f,\"status\":%d,\"launches\":1}",
+                 secs, hs);
+        h->stats = buf;
+        for (int64_t b = 0; b < batch; b++)
+            if (sc[b] < 0.0) return TDEIG_EINVAL;
+        return (hs & (TD_STATUS_NOTCONV | TD_STATUS_LEAF)) ? TDEIG_ENOTCONV : TDEIG_OK;
+    }
+    if (G.exec) {
+        cudaGraphExecDestroy(G.exec);
+        G.exec = nullptr;
+    }
+    // ends a capture that an early error return would otherwise leave open
+    struct CaptureGuard {
+        cudaStream_t st;
+        bool active = false;
+        ~CaptureGuard()
+        {
+            if (!active) return;
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(st, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+        }
+    } cap{st};
+
     // Worst-case number of merges on one level: bounded by the number of leaves.
     int64_t Mmax = 0;
     for (int64_t b = 0; b < batch; b++) {
@@ -442,7 +529,7 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     bytes += 2 * (size_t)R * sizeof(double);            // staging d, e
     bytes += level_ws_bytes(R, Mmax);
     bytes += (size_t)batch * (3 * sizeof(int64_t) + sizeof(double));
-    bytes += (size_t)(Mmax * 64) * (sizeof(MergeDesc) + 3 * sizeof(int)) +
+    bytes += (size_t)(Mmax * 64) * (sizeof(MergeDesc) + (3 + TD_GEMM_VARIANTS) * sizeof(int)) +
              (size_t)leaves_max * sizeof(LeafDesc);
     bytes += 64 * 1024;
     int rc = ensure_ws(h, bytes);
@@ -476,7 +563,14 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     LeafDesc* dev_leaf = ar.take<LeafDesc>(std::max<size_t>(P.leaves.size(), 1));
     int* kstat = ar.take<int>(std::max<size_t>(ndesc, 1));       // K of every merge
     int* gstat = ar.take<int>(2 * std::max<size_t>(ndesc, 1));   // K1, Km of every merge
+    int* toff_all = ar.take<int>(TD_GEMM_VARIANTS * std::max<size_t>(ndesc, 1));
     if (ar.off > ar.cap) return TDEIG_ENOMEM;
+    std::vector<int> toff_host;
+    for (auto& L : P.levels)
+        for (int v = 0; v < TD_GEMM_VARIANTS; v++) {
+            L.dev_toff[v] = toff_all + toff_host.size();
+            toff_host.insert(toff_host.end(), L.toff[v].begin(), L.toff[v].end());
+        }
 
     std::vector<MergeDesc> all;
     all.reserve(ndesc);
@@ -498,13 +592,23 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
         CU(cudaMemcpyAsync(dev_desc, all.data(), ndesc * sizeof(MergeDesc), cudaMemcpyHostToDevice, st));
     CU(cudaMemcpyAsync(dev_leaf, P.leaves.data(), P.leaves.size() * sizeof(LeafDesc),
                        cudaMemcpyHostToDevice, st));
+    if (!toff_host.empty())
+        CU(cudaMemcpyAsync(toff_all, toff_host.data(), toff_host.size() * sizeof(int),
+                           cudaMemcpyHostToDevice, st));
+    if (graph) {
+        CU(cudaStreamSynchronize(st));
+        CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        cap.active = true;
+    }
     CU(cudaMemsetAsync(status, 0, 64 * sizeof(int), st));
 
     // Stage timing: an event before each stage and one at the end, on the
-    // handle's stream; read after the final synchronisation.
+    // handle's stream; read after the final synchronisation (not in graph mode).
     h->ev_names.clear();
     h->ev_level.clear();
+    h->tuning.clear();
     auto mark = [&](const char* name, int level) -> int {
+        if (graph) return TDEIG_OK;
         size_t i = h->ev_names.size();
         if (i >= h->events.size()) {
             cudaEvent_t e;
@@ -581,7 +685,28 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
             split_launch_gemm(gd, h->split, st, &rc);
             if (rc) return rc;
         } else {
-            td_launch_update_dense(Md, nm, L.tiles, lws, st);
+            // Autotuner: the first solve of a level class times every tile shape
+            // of the update product on the level's own data (all shapes produce
+            // bitwise-identical results) and later solves use the fastest.
+            const int key = tune_key(L);
+            auto it = h->tuned.find(key);
+            if (it != h->tuned.end() || graph) {
+                const int v = (it != h->tuned.end()) ? it->second : 0;
+                td_launch_update_dense(Md, L.dev_toff[v], nm, L.tiles_v[v], v, lws, st);
+            } else {
+                std::vector<int> evi;
+                for (int v = 0; v <= TD_GEMM_VARIANTS; v++) {
+                    size_t i = h->tune_ev.size();
+                    cudaEvent_t ev;
+                    CU(cudaEventCreate(&ev));
+                    h->tune_ev.push_back(ev);
+                    CU(cudaEventRecord(ev, st));
+                    evi.push_back((int)i);
+                    if (v < TD_GEMM_VARIANTS)
+                        td_launch_update_dense(Md, L.dev_toff[v], nm, L.tiles_v[v], v, lws, st);
+                }
+                h->tuning.push_back({key, evi});
+            }
         }
         MARK("finish", lv);
         td_launch_finish(Md, nm, L.nmax, lws, st);
@@ -589,6 +714,24 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     }
     MARK("end", -1);
 #undef MARK
+    if (graph) {
+        cudaGraph_t gr = nullptr;
+        cap.active = false;
+        CU(cudaStreamEndCapture(st, &gr));
+        cudaGraphExec_t ex = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&ex, gr, 0);
+        cudaGraphDestroy(gr);
+        if (ie != cudaSuccess) return TDEIG_ECUDA;
+        G.exec = ex;
+        G.N = P.N;
+        G.d = d; G.e = e; G.lam = lam_out; G.Q = Q_out;
+        G.mode = mode;
+        G.ws = h->ws;
+        G.status = status;
+        G.scale = B.scale;
+        G.batch = batch;
+        CU(cudaGraphLaunch(ex, st));
+    }
 
     if (!l_dev) CU(cudaMemcpyAsync(lam_out, B.Lfinal, R * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (Q_out && !q_dev)
@@ -602,10 +745,25 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     }
     CU(cudaStreamSynchronize(st));
     CU(cudaGetLastError());
+    // autotuner: keep the fastest tile shape of every level class timed in this solve
+    for (auto& t : h->tuning) {
+        int best = 0;
+        float bt = 3.0e38f;
+        for (int v = 0; v < TD_GEMM_VARIANTS; v++) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, h->tune_ev[t.second[v]], h->tune_ev[t.second[v + 1]]);
+            if (ms < bt) { bt = ms; best = v; }
+        }
+        h->tuned[t.first] = best;
+    }
+    h->tuning.clear();
+    for (cudaEvent_t ev : h->tune_ev) cudaEventDestroy(ev);
+    h->tune_ev.clear();
     std::vector<double> sc(batch);
     CU(cudaMemcpy(sc.data(), B.scale, batch * sizeof(double), cudaMemcpyDeviceToHost));
     double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     h->stats = stats_json(h, P, kh, gh, hss_js, secs, hstat[0]);
+    if (graph) h->stats.insert(1, "\"graph\":\"captured\",");
     {
         char lb[64];
         snprintf(lb, sizeof(lb), ",\"launches\":%lld}", g_td_launches - launches0);
@@ -644,7 +802,32 @@ extern "C" int tdeig_solve_batched(tdeig_handle h, int64_t batch, const int64_t*
     if (R == 0) return TDEIG_OK;
     if (!d_cat || !lambda_cat || (E > 0 && !e_cat)) return TDEIG_EINVAL;
     CU(cudaSetDevice(h->device));
-    return solve_impl(h, batch, N_each, d_cat, E > 0 ? e_cat : nullptr, lambda_cat, Q_cat, mode);
+    // Members are solved in consecutive chunks whose eigenvector blocks total at
+    // most TD_BATCH_CHUNK elements, which bounds the workspace (about five such
+    // buffers) however large the batch is.
+    const int64_t chunk_elems = TD_BATCH_CHUNK;
+    int64_t b0 = 0, r0 = 0, e0 = 0, q0 = 0;
+    int worst = TDEIG_OK, nchunks = 0;
+    std::string js = "[";
+    while (b0 < batch) {
+        int64_t b1 = b0, qs = 0, rs = 0, es = 0;
+        while (b1 < batch && (b1 == b0 || qs + N_each[b1] * N_each[b1] <= chunk_elems)) {
+            qs += N_each[b1] * N_each[b1];
+            rs += N_each[b1];
+            es += N_each[b1] > 0 ? N_each[b1] - 1 : 0;
+            b1++;
+        }
+        int rc = solve_impl(h, b1 - b0, N_each + b0, d_cat + r0, (E > 0) ? e_cat + e0 : nullptr,
+                            lambda_cat + r0, Q_cat ? Q_cat + q0 : nullptr, mode);
+        if (rc == TDEIG_EINVAL || rc == TDEIG_ENOMEM || rc == TDEIG_ECUDA) return rc;
+        if (rc != TDEIG_OK) worst = rc;
+        if (b0 > 0) js += ",";
+        js += h->stats;
+        nchunks++;
+        b0 = b1; r0 += rs; e0 += es; q0 += qs;
+    }
+    if (nchunks > 1) h->stats = "{\"chunks\":" + js + "]}";
+    return worst;
 }
 
 // ---------------------------------------------------------------------------

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libtdeig.so")
 
 MODE_DENSE, MODE_ADC1, MODE_ADC2 = 0, 1, 2
 PREC_FP64, PREC_SPLIT = 0 << 8, 1 << 8
+FLAG_GRAPH = 1 << 12
 _MODES = {"dense": MODE_DENSE, "adc1": MODE_ADC1, "adc2": MODE_ADC2}
 _PRECS = {"fp64": PREC_FP64, "split": PREC_SPLIT}
 
@@ -86,10 +87,10 @@ def default_options():
     return o
 
 
-def mode_code(mode="dense", prec="fp64"):
+def mode_code(mode="dense", prec="fp64", graph=False):
     if isinstance(mode, int):
-        return mode
-    return _MODES[mode] | _PRECS[prec]
+        return mode | (FLAG_GRAPH if graph else 0)
+    return _MODES[mode] | _PRECS[prec] | (FLAG_GRAPH if graph else 0)
 
 
 # --------------------------------------------------------------------------
@@ -172,7 +173,8 @@ class Solver:
         """The C call itself on raw pointers; returns the status."""
         return lib().tdeig_solve(self.h, d_ptr, e_ptr, int(N), lam_ptr, q_ptr, int(mode))
 
-    def solve(self, d, e, mode="dense", prec="fp64", vectors=True, out=None, check=True):
+    def solve(self, d, e, mode="dense", prec="fp64", vectors=True, out=None, check=True,
+              graph=False):
         """Eigendecomposition of tridiag(e, d, e): returns (lam, Q), Q[:, j] <-> lam[j]."""
         d = _as_f64(d)
         e = _as_f64(e)
@@ -183,12 +185,12 @@ class Solver:
         else:
             lam, Q = out
         st = lib().tdeig_solve(self.h, _ptr(d), _ptr(e) if N > 1 else None, N, _ptr(lam), _ptr(Q),
-                               mode_code(mode, prec))
+                               mode_code(mode, prec, graph))
         if check and st != OK:
             raise TdeigError(st, "tdeig_solve")
         return lam, Q
 
-    def solve_batched(self, ds, es, mode="dense", prec="fp64"):
+    def solve_batched(self, ds, es, mode="dense", prec="fp64", graph=False, out=None):
         """Independent matrices (lists of numpy arrays / CPU or CUDA tensors)."""
         sizes = [int(x.shape[0]) for x in ds]
         if _is_torch(ds[0]):
@@ -204,7 +206,7 @@ class Solver:
             Qc = np.empty(sum(n * n for n in sizes))
         Ns = (_i64 * len(sizes))(*sizes)
         st = lib().tdeig_solve_batched(self.h, len(sizes), Ns, _ptr(dcat), _ptr(ecat), _ptr(lam),
-                                       _ptr(Qc), mode_code(mode, prec))
+                                       _ptr(Qc), mode_code(mode, prec, graph))
         if st != OK:
             raise TdeigError(st, "tdeig_solve_batched")
         outs = []

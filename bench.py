@@ -1,15 +1,20 @@
 """Benchmark: full eigendecomposition of a symmetric tridiagonal matrix on GB300.
 
 Headline workload: Toeplitz(2, 1) of order N = 16384 (Sec. 5, Example 3), all
-eigenvalues and eigenvectors, accelerated DC (HSS update) against plain dense
-DC on the same GPU, orthogonality / residual required <= 1e-10.
+eigenvalues and eigenvectors, accelerated DC (ADC2: randomized HSS update,
+split-precision tensor-core products for Algorithm 3) against plain dense DC on
+the same GPU (FP64 products and split products), orthogonality / residual
+required <= 1e-10.
 
 One step = one full eigendecomposition through the C ABI (tdeig_solve) with
 inputs and outputs resident in HBM.  Between timed steps the L2 is flushed by
-writing a 256 MiB buffer outside the timed events.  Under torchrun every rank
-solves its own copy (independent replicas; no collective on the data path).
+writing a 256 MiB buffer outside the timed events.  The timed steps run with
+per-kernel CUDA events inside the library (TDEIG_FLAG_PROFILE); the roofline
+of the dominant kernel is computed from them.  Under torchrun every rank solves
+its own copy (independent replicas; no collective on the data path).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py --workload batched    # 4096 uneven matrices, one batched call per step
 """
 import argparse
 import json
@@ -24,9 +29,11 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC ="full eigendecomp time at N=16384: ADC vs plain DC on GB300, orth/resid ≤1e-10"
-FP64_FMA_PER_SM_CLK = 2          # measured: FP64 FMA chain throughput 1.19-1.20 TFLOP/s
+METRIC = "full eigendecomp time at N=16384: ADC vs plain DC on GB300, orth/resid ≤1e-10"
 N_SMS = 152
+SM_MHZ = 2070.0
+FP64_FMA_PER_SM_CLK = 2          # measured: FP64 FMA chain throughput 1.19-1.20 TFLOP/s
+MMA_SYNC_BF16_TFLOPS = 600.0     # measured: mma.sync m16n8k16 BF16, register operands
 
 
 def parse():
@@ -35,13 +42,15 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="single", choices=["single", "batched"])
     p.add_argument("--n", type=int, default=16384)
     p.add_argument("--matrix", default="toeplitz", choices=["toeplitz", "random"])
     p.add_argument("--mode", default="adc2", choices=["adc1", "adc2", "dense"])
-    p.add_argument("--prec", default="fp64", choices=["fp64", "split"])
+    p.add_argument("--prec", default="split", choices=["fp64", "split"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-dense-compare", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-profile", action="store_true")
     p.add_argument("--stats-out", default=None)
     return p.parse_args()
 
@@ -62,6 +71,10 @@ def peaks():
 
 
 def workload_name(args):
+    if args.workload == "batched":
+        return ("4096 tridiagonals, N uniform on [64, 2048] (seed 3), even members U[-1,1], odd "
+                "members glued Wilkinson W21 (coupling 1e-8); %s update, %s products"
+                % (args.mode.upper(), args.prec))
     m = "Toeplitz(2,1)" if args.matrix == "toeplitz" else "random (a~U[-1,1], b~U[0.5,1], seed 1)"
     return "%s N=%d full eigendecomposition, %s update, %s products" % (
         m, args.n, args.mode.upper(), args.prec)
@@ -119,58 +132,70 @@ class Clocks:
 
 
 # --------------------------------------------------------------------------
-# roofline of the dominant kernel, from the library's per-stage events
+# roofline of the dominant kernel, from the library's per-kernel events
 # --------------------------------------------------------------------------
-def stage_work(stats):
-    """Algorithmic work per stage launch (per level): flops of the dense update
-    product 2 (n1 (K1 + Km) + n2 (K - K1)) K per merge."""
-    out = {}
-    for L in stats["levels"]:
-        fl = 0.0
+def dense_update_flops(st):
+    """Algorithmic flops of the block-structured dense update: per merge
+    2 (n1 (K1 + Km) + n2 (K - K1)) K."""
+    fl = 0.0
+    for L in st.get("levels", []):
+        if "update" not in L["ms"]:
+            continue
         for n, n1, K, K1, Km in L["merges"]:
             fl += 2.0 * (n1 * (K1 + Km) + (n - n1) * (K - K1)) * K
-        out[L["height"]] = {"update_flops": fl}
-    return out
+    return fl
 
 
-def roofline(stats_list):
-    """Dominant stage over the timed steps and its achieved rate."""
-    tot = {}
+def grouped_flops(st):
+    """FP64 flops of the grouped products (HSS sampling and construction, and
+    Algorithm 3 when it is not split)."""
+    fl = 0.0
+    for h in st.get("hss", []):
+        f = h.get("flops")
+        if f:
+            fl += f["dense"] + f["sample"] + f["build"]
+            if st.get("split_tensor_flops", 0.0) == 0.0:
+                fl += f["mult"]
+    return fl
+
+
+def roofline(stats_list, pk):
+    kern = {}
     for st in stats_list:
-        for k, v in st["stage_ms"].items():
-            tot[k] = tot.get(k, 0.0) + v
-    dom = max(tot, key=tot.get)
-    fp64_peak = N_SMS * 2070e6 * 2 * FP64_FMA_PER_SM_CLK / 1e12
-    res = {"kernel": dom, "share": tot[dom] / sum(tot.values()),
-           "stage_share": {k: v / sum(tot.values()) for k, v in tot.items()}}
-    fl = ms = 0.0
-    n_launch = 0
-    if dom == "update":
-        for st in stats_list:
-            work = stage_work(st)
-            for L in st["levels"]:
-                if "update" in L["ms"]:
-                    fl += work[L["height"]]["update_flops"]
-                    ms += L["ms"]["update"]
-                    n_launch += 1
-        res["kernel"] = "k_gemm_f64 (dense update)"
-    elif dom in ("hss_mult", "hss_sample", "hss_build"):
-        key = dom[4:]
-        for st in stats_list:
-            fl += sum(h["flops"][key] for h in st.get("hss", []) if "flops" in h)
-            for L in st["levels"]:
-                if dom in L["ms"]:
-                    ms += L["ms"][dom]
-                    n_launch += 1
-        res["kernel"] = "k_gemm_grouped (%s)" % {"mult": "Algorithm 3 HSS x matrix",
-                                                  "sample": "sampling Y, Z",
-                                                  "build": "Algorithm 2 products"}[key]
-    if fl > 0 and ms > 0:
+        for k, v in st.get("kernels", {}).items():
+            a = kern.setdefault(k, [0.0, 0])
+            a[0] += v["ms"]
+            a[1] += v["launches"]
+    if not kern:
+        return None
+    total = sum(v[0] for v in kern.values())
+    dom = max(kern, key=lambda k: kern[k][0])
+    ms, launches = kern[dom]
+    fp64_peak = N_SMS * SM_MHZ * 1e6 * 2 * FP64_FMA_PER_SM_CLK / 1e12
+    res = {"kernel": dom, "share": ms / total, "launches": launches,
+           "avg_launch_ms": ms / max(launches, 1),
+           "kernel_share": {k: round(v[0] / total, 4) for k, v in
+                            sorted(kern.items(), key=lambda x: -x[1][0])},
+           "traffic": None}
+    fl = None
+    if dom == "k_gemm_f64":
+        fl = sum(dense_update_flops(s) for s in stats_list)
+        peak, bound, note = fp64_peak, "alu", (
+            "FP64 FMA issue: 152 SMs x 2070 MHz x 2 FMA/clk/SM (measured FMA-chain probe "
+            "1.20 TFLOP/s; cuBLAS DGEMM 1.10)")
+    elif dom == "k_gemm_grouped":
+        fl = sum(grouped_flops(s) for s in stats_list)
+        peak, bound, note = fp64_peak, "alu", "FP64 FMA issue peak, as for k_gemm_f64"
+    elif dom == "k_split_gemm":
+        fl = sum(s.get("split_tensor_flops", 0.0) for s in stats_list)
+        peak = pk.get("bf16_tflops", 1900.0)
+        bound, note = "tensor", (
+            "measured bf16 (cuBLAS burst) %.0f TFLOP/s; mma.sync m16n8k16 measured ceiling "
+            "%.0f TFLOP/s" % (peak, MMA_SYNC_BF16_TFLOPS))
+    if fl:
         ach = fl / (ms / 1e3) / 1e12
-        res.update({"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                    "frac": ach / fp64_peak, "traffic": None, "stage_launches": n_launch,
-                    "peak_note": "FP64 FMA issue: 152 SMs x 2070 MHz x 2 FMA/clk/SM (measured "
-                                 "FMA-chain probe 1.20 TFLOP/s; cuBLAS DGEMM 1.10)"})
+        res.update({"bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "peak_note": note + " (of measured)"})
     return res
 
 
@@ -204,8 +229,8 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": workload_name(args), "n": args.n, "matrix": args.matrix,
-                       "mode": args.mode, "precision": "fp64"},
+            "config": {"workload": workload_name(args) + " (CPU oracle, FP64)", "n": args.n,
+                       "matrix": args.matrix, "mode": args.mode, "precision": "fp64"},
             "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
                              "sample": "full N=%d solve per step (warm-up steps at N=1024)"
                                        % args.n},
@@ -238,14 +263,20 @@ def main():
 
     stream = torch.cuda.Stream(device=dev)
     solver = tdeig.Solver(stream=stream.cuda_stream)
+    flush = torch.empty(32 * 1024 * 1024, dtype=torch.float64, device=dev)   # 256 MiB
+    mode = tdeig.mode_code(args.mode, args.prec)
+    prof = 0 if args.no_profile else (1 << 13)
+
+    if args.workload == "batched":
+        return run_batched(args, torch, dist, world, rank, local, dev, stream, solver, flush,
+                           tdeig, mode, prof)
+
     a, b = matrix(args, rank)
     N = args.n
     d_d = torch.from_numpy(a).to(dev)
     e_d = torch.from_numpy(b).to(dev)
     lam = torch.empty(N, dtype=torch.float64, device=dev)
     Qt = torch.empty((N, N), dtype=torch.float64, device=dev)   # holds Q^T (column-major Q)
-    flush = torch.empty(32 * 1024 * 1024, dtype=torch.float64, device=dev)   # 256 MiB
-    mode = tdeig.mode_code(args.mode, args.prec)
 
     def one(m):
         st = solver.solve_raw(d_d.data_ptr(), e_d.data_ptr(), N, lam.data_ptr(), Qt.data_ptr(), m)
@@ -282,10 +313,8 @@ def main():
             dist.all_reduce(tot, op=dist.ReduceOp.MAX)
         return float(tot.item()) / steps, stats, ck
 
-    ms_step, stats, clocks = timed(mode, args.steps, args.warmup)
+    ms_step, stats, clocks = timed(mode | prof, args.steps, args.warmup)
     launches = sum(int(s.get("launches", 0)) for s in stats)
-
-    # accuracy of the timed result (Q and lambda of the last step)
     acc = accuracy(a, b, lam, Qt, dev)
 
     out = {"metric": METRIC, "value": ms_step / 1e3, "unit": "s", "n_gpus": world,
@@ -296,17 +325,22 @@ def main():
                       "mode": args.mode, "precision": args.prec, "leaf": 32,
                       "hss_threshold": 2000, "hss_leaf": 128, "tol": 1e-12, "oversample": 10,
                       "l2": "flushed between timed steps (256 MiB write outside the events)",
+                      "timing": "CUDA events on the solve's stream; per-kernel events inside "
+                                "the library during the timed steps",
                       "parallelism": "replicas" if world > 1 else "single GPU"},
            "accuracy": acc, "stage_ms": stats[-1]["stage_ms"], "clocks": clocks,
            "gpu_launches": launches}
 
     if not args.no_dense_compare and args.mode != "dense":
-        ms_d, st_d, _ = timed(tdeig.mode_code("dense", "fp64"), 1, 1)
-        acc_d = accuracy(a, b, lam, Qt, dev)
-        out["plain_dc"] = {"value": ms_d / 1e3, "unit": "s", "accuracy": acc_d,
-                           "stage_ms": st_d[-1]["stage_ms"]}
-        out["speedup_vs_plain_dc"] = ms_d / ms_step
-    out["roofline"] = roofline(stats)
+        out["plain_dc"] = {}
+        for pr in ("fp64", "split"):
+            ms_d, st_d, _ = timed(tdeig.mode_code("dense", pr), 1, 1)
+            out["plain_dc"][pr] = {"value": ms_d / 1e3, "unit": "s",
+                                   "accuracy": accuracy(a, b, lam, Qt, dev),
+                                   "stage_ms": st_d[-1]["stage_ms"]}
+        out["speedup_vs_plain_dc"] = {pr: out["plain_dc"][pr]["value"] / (ms_step / 1e3)
+                                      for pr in ("fp64", "split")}
+    out["roofline"] = roofline(stats, peaks())
 
     if not args.no_e2e:
         out["e2e"] = e2e(args, a, b, solver, mode)
@@ -320,6 +354,58 @@ def main():
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def run_batched(args, torch, dist, world, rank, local, dev, stream, solver, flush, tdeig, mode,
+                prof):
+    """configs: 4096 independent uneven tridiagonals in one tdeig_solve_batched call per step."""
+    import ctypes
+    from paper_1510_04591_gb300 import inputs
+    ms_list = inputs.batch(4096, 3, 64, 2048)
+    sizes = [len(x) for x, _ in ms_list]
+    d = torch.from_numpy(np.concatenate([x for x, _ in ms_list])).to(dev)
+    e = torch.from_numpy(np.concatenate([y for _, y in ms_list])).to(dev)
+    lam = torch.empty(sum(sizes), dtype=torch.float64, device=dev)
+    Q = torch.empty(sum(n * n for n in sizes), dtype=torch.float64, device=dev)
+    Ns = (ctypes.c_int64 * len(sizes))(*sizes)
+    L = tdeig.lib()
+
+    def one(m):
+        st = L.tdeig_solve_batched(solver.h, len(sizes), Ns, d.data_ptr(), e.data_ptr(),
+                                   lam.data_ptr(), Q.data_ptr(), m)
+        if st != 0:
+            raise tdeig.TdeigError(st, "tdeig_solve_batched")
+        return json.loads(solver.stats())
+
+    for _ in range(args.warmup):
+        one(mode)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    ms = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush_l2(flush)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one(mode)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    ck = clocks.stop()
+    v = float(np.mean(ms)) / 1e3
+    out = {"metric": "batched eigendecomposition time, 4096 uneven tridiagonals", "value": v,
+           "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": workload_name(args), "members": len(sizes),
+                      "rows": int(sum(sizes)), "q_entries": int(sum(n * n for n in sizes))},
+           "clocks": ck, "matrices_per_s": len(sizes) / v}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    solver.close()
     return 0
 
 
@@ -383,8 +469,8 @@ def cpu_baseline(args, a, b):
     dc.solve(a, b, dc.Options(mode=mode))
     v = time.perf_counter() - t
     return {"value": v, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "one full N=%d solve (C routines with OpenMP over roots, numpy BLAS "
-                      "products, all host threads)" % args.n}
+            "sample": "one full N=%d solve in %s mode, FP64 (C routines with OpenMP over "
+                      "roots, numpy BLAS products, all host threads)" % (args.n, args.mode)}
 
 
 if __name__ == "__main__":

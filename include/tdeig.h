@@ -52,7 +52,11 @@ enum {
      * (every level of every matrix) in a CUDA graph on the first call and
      * replay it on later calls with the same sizes and buffers.  Ignored
      * otherwise (those modes read deflated sizes back to the host). */
-    TDEIG_FLAG_GRAPH = 1 << 12
+    TDEIG_FLAG_GRAPH = 1 << 12,
+    /* Time every kernel launch of the solve with CUDA events on the solve's
+     * stream; tdeig_last_stats then lists per kernel its launches and device
+     * milliseconds under "kernels".  Not combined with TDEIG_FLAG_GRAPH. */
+    TDEIG_FLAG_PROFILE = 1 << 13
 };
 
 enum {

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #define TD_EPS 1.1102230246251565e-16  // unit roundoff 2^-53
 #define TD_SECULAR_MAXIT 64            // secular iteration cap per root
 #define TD_STATUS_NOTCONV 1
@@ -59,6 +61,19 @@ struct LevelWS {
 
 // Number of kernels launched by this library (host counter, read per solve).
 extern long long g_td_launches;
+
+// Per-kernel timing of a solve made with TDEIG_FLAG_PROFILE: td_prof_begin
+// records an event before a launch, td_prof_end one after it (and counts the
+// launch).  Events are kept in launch order; one profiled solve at a time.
+struct TdProf {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<const char*> name;   // name at the index of each "after" event
+    size_t n = 0;
+};
+extern TdProf g_td_prof;
+void td_prof_begin(cudaStream_t st);
+void td_prof_end(cudaStream_t st, const char* name);
 
 // Host-side launchers (kernels_dc.cu).
 void td_launch_scale_input(const double* d, const double* e, const int64_t* mrow0, const int64_t* mN,

@@ -26,6 +26,30 @@
 #define TD_NOALLOC_MAX_DEVICES 64
 
 long long g_td_launches = 0;
+TdProf g_td_prof;
+
+static cudaEvent_t prof_next(const char* name)
+{
+    if (g_td_prof.n >= g_td_prof.ev.size()) {
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        g_td_prof.ev.push_back(e);
+        g_td_prof.name.push_back(nullptr);
+    }
+    g_td_prof.name[g_td_prof.n] = name;
+    return g_td_prof.ev[g_td_prof.n++];
+}
+
+void td_prof_begin(cudaStream_t st)
+{
+    if (g_td_prof.on) cudaEventRecord(prof_next(nullptr), st);
+}
+
+void td_prof_end(cudaStream_t st, const char* name)
+{
+    g_td_launches++;
+    if (g_td_prof.on) cudaEventRecord(prof_next(name), st);
+}
 
 // ---------------------------------------------------------------------------
 // Input scaling: A[g] = d[g] / s_b, Bc[g] = e (row g, g+1) / s_b within member b.
@@ -89,10 +113,13 @@ void td_launch_scale_input(const double* d, const double* e, const int64_t* mrow
                            int members, double* A, double* Bc, double* scale, int64_t R,
                            cudaStream_t st)
 {
-    k_member_max<<<members, 256, 0, st>>>(d, e, mrow0, mN, scale); g_td_launches++;
-    if (R > 0)
+    td_prof_begin(st); k_member_max<<<members, 256, 0, st>>>(d, e, mrow0, mN, scale); td_prof_end(st, "k_member_max");
+    if (R > 0) {
+        td_prof_begin(st);
         k_scale_copy<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(d, e, mrow0, mN, members, scale, A,
-                                                                 Bc, R); g_td_launches++;
+                                                                 Bc, R);
+        td_prof_end(st, "k_scale_copy");
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -179,7 +206,7 @@ void td_launch_leaf(const LeafDesc* leaves, int nleaves, const double* A, const 
                     int* status, cudaStream_t st)
 {
     if (nleaves <= 0) return;
-    k_leaf<<<td_cdiv(nleaves, LEAF_WARPS), 32 * LEAF_WARPS, 0, st>>>(leaves, nleaves, A, Bc, status); g_td_launches++;
+    td_prof_begin(st); k_leaf<<<td_cdiv(nleaves, LEAF_WARPS), 32 * LEAF_WARPS, 0, st>>>(leaves, nleaves, A, Bc, status); td_prof_end(st, "k_leaf");
 }
 
 // ---------------------------------------------------------------------------
@@ -452,11 +479,11 @@ void td_launch_merge_level(const MergeDesc* M, int nmerge, int nmax, int rows, i
                            const LevelWS& ws, int* status, int use_hss_mask, cudaStream_t st)
 {
     (void)rows; (void)total_tiles; (void)status; (void)use_hss_mask;
-    k_prep<<<nmerge, PREP_NT, 0, st>>>(M, ws); g_td_launches++;
+    td_prof_begin(st); k_prep<<<nmerge, PREP_NT, 0, st>>>(M, ws); td_prof_end(st, "k_prep");
     dim3 gw(td_cdiv(nmax, 256) * td_cdiv(nmax, 32), nmerge);
-    k_build_w<<<gw, 256, 0, st>>>(M, ws); g_td_launches++;
+    td_prof_begin(st); k_build_w<<<gw, 256, 0, st>>>(M, ws); td_prof_end(st, "k_build_w");
     dim3 gr(td_cdiv(nmax, 128), nmerge);
-    k_rotate<<<gr, 128, 0, st>>>(M, ws); g_td_launches++;
+    td_prof_begin(st); k_rotate<<<gr, 128, 0, st>>>(M, ws); td_prof_end(st, "k_rotate");
 }
 
 // ---------------------------------------------------------------------------
@@ -566,7 +593,7 @@ void td_launch_secular(const MergeDesc* M, int nmerge, int rows, const LevelWS& 
                        cudaStream_t st)
 {
     if (rows <= 0) return;
-    k_secular<<<td_cdiv(rows, 8), 256, 0, st>>>(M, nmerge, rows, ws, status); g_td_launches++;
+    td_prof_begin(st); k_secular<<<td_cdiv(rows, 8), 256, 0, st>>>(M, nmerge, rows, ws, status); td_prof_end(st, "k_secular");
 }
 
 // ---------------------------------------------------------------------------
@@ -654,7 +681,7 @@ void td_launch_lowner_cauchy(const MergeDesc* M, int nmerge, int rows, int kmax,
                              int write_qhat, cudaStream_t st)
 {
     if (rows <= 0) return;
-    k_lowner<<<td_cdiv(rows, 8), 256, 0, st>>>(M, nmerge, rows, ws); g_td_launches++;
+    td_prof_begin(st); k_lowner<<<td_cdiv(rows, 8), 256, 0, st>>>(M, nmerge, rows, ws); td_prof_end(st, "k_lowner");
     size_t sm = (size_t)kmax * sizeof(double);
     if (sm <= CAUCHY_SMEM_MAX) {
         static bool attr = false;
@@ -663,9 +690,9 @@ void td_launch_lowner_cauchy(const MergeDesc* M, int nmerge, int rows, int kmax,
                                  CAUCHY_SMEM_MAX);
             attr = true;
         }
-        k_cauchy<true><<<rows, CAUCHY_NT, sm, st>>>(M, nmerge, rows, ws, write_qhat); g_td_launches++;
+        td_prof_begin(st); k_cauchy<true><<<rows, CAUCHY_NT, sm, st>>>(M, nmerge, rows, ws, write_qhat); td_prof_end(st, "k_cauchy");
     } else {
-        k_cauchy<false><<<rows, CAUCHY_NT, 0, st>>>(M, nmerge, rows, ws, write_qhat); g_td_launches++;
+        td_prof_begin(st); k_cauchy<false><<<rows, CAUCHY_NT, 0, st>>>(M, nmerge, rows, ws, write_qhat); td_prof_end(st, "k_cauchy");
     }
 }
 
@@ -740,7 +767,7 @@ __global__ void k_copy_defl(const MergeDesc* M, LevelWS ws)
 void td_launch_finish(const MergeDesc* M, int nmerge, int nmax, const LevelWS& ws, cudaStream_t st)
 {
     dim3 g(td_cdiv(nmax, 256) * td_cdiv(nmax, 32), nmerge);
-    k_copy_defl<<<g, 256, 0, st>>>(M, ws); g_td_launches++;
+    td_prof_begin(st); k_copy_defl<<<g, 256, 0, st>>>(M, ws); td_prof_end(st, "k_copy_defl");
 }
 
 // ---------------------------------------------------------------------------
@@ -844,19 +871,20 @@ void td_launch_update_dense(const MergeDesc* M, const int* toff, int nmerge, int
                             int variant, const LevelWS& ws, cudaStream_t st)
 {
     if (total_tiles <= 0) return;
+    td_prof_begin(st);
     switch (variant) {
     case 1: k_gemm_f64<32, 32><<<total_tiles, 256, 0, st>>>(M, toff, nmerge, ws); break;
     case 2: k_gemm_f64<128, 64><<<total_tiles, 256, 0, st>>>(M, toff, nmerge, ws); break;
     case 3: k_gemm_f64<64, 32><<<total_tiles, 256, 0, st>>>(M, toff, nmerge, ws); break;
     default: k_gemm_f64<64, 64><<<total_tiles, 256, 0, st>>>(M, toff, nmerge, ws); break;
     }
-    g_td_launches++;
+    td_prof_end(st, "k_gemm_f64");
 }
 
 // Order kernel launcher (separate so the HSS path can reuse it).
 void td_launch_order(const MergeDesc* M, int nmerge, const LevelWS& ws, cudaStream_t st)
 {
-    k_order<<<nmerge, PREP_NT, 0, st>>>(M, ws); g_td_launches++;
+    td_prof_begin(st); k_order<<<nmerge, PREP_NT, 0, st>>>(M, ws); td_prof_end(st, "k_order");
 }
 
 // Stage entry points: one rank-one problem of size K placed as merge 0.
@@ -872,7 +900,7 @@ __global__ void k_stage_init(LevelWS ws, int K, double rho)
 
 void td_launch_stage_init(const LevelWS& ws, int K, double rho, cudaStream_t st)
 {
-    k_stage_init<<<td_cdiv(std::max(K, 1), 256), 256, 0, st>>>(ws, K, rho); g_td_launches++;
+    td_prof_begin(st); k_stage_init<<<td_cdiv(std::max(K, 1), 256), 256, 0, st>>>(ws, K, rho); td_prof_end(st, "k_stage_init");
 }
 
 // ---------------------------------------------------------------------------

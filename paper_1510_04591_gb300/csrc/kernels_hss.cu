@@ -118,8 +118,9 @@ double hss_launch_gemm(const std::vector<GemmDesc>& gin, GemmDesc* dev, cudaStre
     }
     if (g.empty()) return 0.0;
     cudaMemcpyAsync(dev, g.data(), g.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice, st);
+    td_prof_begin(st);
     k_gemm_grouped<<<tiles, HSS_NT, 0, st>>>(dev, (int)g.size());
-    g_td_launches++;
+    td_prof_end(st, "k_gemm_grouped");
     return flops;
 }
 
@@ -163,8 +164,9 @@ static void launch_fill(std::vector<FillDesc>& F, FillDesc* dev, cudaStream_t st
     }
     if (f.empty()) return;
     cudaMemcpyAsync(dev, f.data(), f.size() * sizeof(FillDesc), cudaMemcpyHostToDevice, st);
+    td_prof_begin(st);
     k_cauchy_fill<<<tiles, HSS_NT, 0, st>>>(dev, (int)f.size());
-    g_td_launches++;
+    td_prof_end(st, "k_cauchy_fill");
 }
 
 // ---------------------------------------------------------------------------
@@ -186,8 +188,9 @@ static void launch_gather(const std::vector<GatherDesc>& G, GatherDesc* dev, cud
         if (d.nr > 0 && d.ncols > 0) g.push_back(d);
     if (g.empty()) return;
     cudaMemcpyAsync(dev, g.data(), g.size() * sizeof(GatherDesc), cudaMemcpyHostToDevice, st);
+    td_prof_begin(st);
     k_gather_rows<<<dim3(8, (unsigned)g.size()), HSS_NT, 0, st>>>(dev, (int)g.size());
-    g_td_launches++;
+    td_prof_end(st, "k_gather_rows");
 }
 
 // ---------------------------------------------------------------------------
@@ -695,8 +698,9 @@ static int srrsc_levels(const tdeig_options& opt, std::vector<HMerge>& H, int Lm
         if (S.off > S.cap || sd.size() > 8192) return TDEIG_ENOMEM;
         launch_fill(fills, dfill, st);
         HCU(cudaMemcpyAsync(dsr, sd.data(), sd.size() * sizeof(SrrscDesc), cudaMemcpyHostToDevice, st));
+        td_prof_begin(st);
         k_srrsc<<<(unsigned)sd.size(), SR_NT, 0, st>>>(dsr, opt.tol, status);
-        g_td_launches++;
+        td_prof_end(st, "k_srrsc");
         HCU(cudaGetLastError());
         for (auto& h : H) {
             if (l > h.L) continue;
@@ -802,9 +806,10 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
         }
         RankDesc* drd = b0.take<RankDesc>(rd.size());
         HCU(cudaMemcpyAsync(drd, rd.data(), rd.size() * sizeof(RankDesc), cudaMemcpyHostToDevice, st));
+        td_prof_begin(st);
         k_rank_estimate<<<td_cdiv((int)rd.size(), 64), 64, 0, st>>>(drd, (int)rd.size(), opt.rank_eps,
                                                                    opt.rank_cap, opt.boundary_shift);
-        g_td_launches++;
+        td_prof_end(st, "k_rank_estimate");
         for (auto& h : H) {
             HCU(cudaMemcpyAsync(h.bounds.data(), h.dev_bounds, h.bounds.size() * sizeof(int),
                                 cudaMemcpyDeviceToHost, st));
@@ -910,9 +915,10 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
     for (auto& h : H) {
         if (adc1) break;
         const int64_t tot = (int64_t)h.K * h.s;
+        td_prof_begin(st);
         k_philox_omega<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(h.Om, h.K, h.s, opt.seed,
                                                                       (unsigned)h.node_id);
-        g_td_launches++;
+        td_prof_end(st, "k_philox_omega");
         GemmDesc g;
         memset(&g, 0, sizeof(g));
         g.A = h.qhat; g.lda = h.K; g.B = h.Om; g.ldb = h.K; g.C = h.Y; g.ldc = h.K;
@@ -1046,8 +1052,9 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
                 cudaFuncSetAttribute(k_id, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
                 attr = true;
             }
+            td_prof_begin(st);
             k_id<<<(unsigned)ids.size(), HSS_NT, sm, st>>>(did, (int)ids.size(), opt.tol);
-            g_td_launches++;
+            td_prof_end(st, "k_id");
             HCU(cudaGetLastError());
         }
         // ranks back to the host

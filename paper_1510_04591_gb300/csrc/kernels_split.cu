@@ -307,6 +307,8 @@ __global__ void __launch_bounds__(256) k_split_gemm(const SplitGemmDesc* G, int 
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
+double g_split_tensor_flops = 0.0;
+
 void split_free(SplitWS& w)
 {
     if (w.base) cudaFree(w.base);
@@ -326,13 +328,14 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
     // scratch: slices and exponents of both operands of every problem, descriptors
     size_t bytes = al256(g.size() * 2 * sizeof(SliceDesc)) + al256(g.size() * sizeof(SplitGemmDesc));
     std::vector<int> betas(g.size()), ss(g.size()), kps(g.size());
-    double flops = 0.0;
+    double flops = 0.0, tflops = 0.0;
     for (size_t i = 0; i < g.size(); i++) {
         split_params(std::max(g[i].Kd, 1), &betas[i], &ss[i]);
         kps[i] = std::max(SG_BK, ((g[i].Kd + SG_BK - 1) / SG_BK) * SG_BK);
         bytes += al256((size_t)ss[i] * g[i].M * kps[i] * 2) + al256((size_t)ss[i] * g[i].N * kps[i] * 2);
         bytes += al256((size_t)g[i].M * 4) + al256((size_t)g[i].N * 4);
         flops += 2.0 * g[i].M * g[i].N * g[i].Kd;
+        tflops += 2.0 * g[i].M * g[i].N * g[i].Kd * (ss[i] * (ss[i] + 1) / 2);
     }
     if (bytes > ws.cap) {
         cudaStreamSynchronize(st);
@@ -392,10 +395,16 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
         return 0.0;
     }
     const unsigned ry = (unsigned)td_cdiv(maxrows, 32);
+    td_prof_begin(st);
     k_slice_exp<<<dim3(ry, (unsigned)sl.size()), 256, 0, st>>>(dsl);
+    td_prof_end(st, "k_slice_exp");
+    td_prof_begin(st);
     k_slice<<<dim3((unsigned)(maxkp / 32), ry, (unsigned)sl.size()), 256, 0, st>>>(dsl);
+    td_prof_end(st, "k_slice");
+    td_prof_begin(st);
     k_split_gemm<<<tiles, 256, 0, st>>>(dsg, (int)sg.size());
-    g_td_launches += 3;
+    td_prof_end(st, "k_split_gemm");
+    g_split_tensor_flops += tflops;
     if (cudaGetLastError() != cudaSuccess) *rc = TDEIG_ECUDA;
     return flops;
 }

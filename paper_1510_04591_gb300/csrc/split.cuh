@@ -26,6 +26,8 @@ struct SplitWS {
 #define TD_SPLIT_BITS 40
 
 double split_launch_gemm(const std::vector<GemmDesc>& g, SplitWS& ws, cudaStream_t st, int* rc);
+// Tensor-core work issued by split products so far: 2 M N K per slice pair.
+extern double g_split_tensor_flops;
 void split_free(SplitWS& ws);
 // beta and s used for a contraction of length K.
 void split_params(int K, int* beta, int* s);

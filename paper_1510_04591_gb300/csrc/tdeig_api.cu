@@ -442,11 +442,18 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     const int variant = mode & TDEIG_MODE_MASK;
     const int prec = mode & TDEIG_PREC_MASK;
     if (variant > TDEIG_MODE_ADC2 ||
-        (mode & ~(TDEIG_MODE_MASK | TDEIG_PREC_MASK | TDEIG_FLAG_GRAPH)))
+        (mode & ~(TDEIG_MODE_MASK | TDEIG_PREC_MASK | TDEIG_FLAG_GRAPH | TDEIG_FLAG_PROFILE)))
         return TDEIG_EINVAL;
     if (prec != TDEIG_PREC_FP64 && prec != TDEIG_PREC_SPLIT) return TDEIG_EINVAL;
     auto t_start = std::chrono::steady_clock::now();
     const long long launches0 = g_td_launches;
+    const double split_flops0 = g_split_tensor_flops;
+    // per-kernel events only for this solve (see TDEIG_FLAG_PROFILE)
+    struct ProfOff {
+        ~ProfOff() { g_td_prof.on = false; }
+    } prof_off;
+    g_td_prof.on = false;
+    g_td_prof.n = 0;
 
     Plan P;
     P.members = (int)batch;
@@ -601,6 +608,7 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
         cap.active = true;
     }
     CU(cudaMemsetAsync(status, 0, 64 * sizeof(int), st));
+    g_td_prof.on = (mode & TDEIG_FLAG_PROFILE) && !graph;
 
     // Stage timing: an event before each stage and one at the end, on the
     // handle's stream; read after the final synchronisation (not in graph mode).
@@ -764,6 +772,38 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     h->stats = stats_json(h, P, kh, gh, hss_js, secs, hstat[0]);
     if (graph) h->stats.insert(1, "\"graph\":\"captured\",");
+    {
+        // per-kernel device time of a profiled solve: "after" event minus "before"
+        std::string kj;
+        char kb[200];
+        if (g_td_prof.on) {
+            std::vector<std::pair<std::string, std::pair<double, int>>> agg;
+            for (size_t i = 1; i < g_td_prof.n; i++) {
+                if (!g_td_prof.name[i] || g_td_prof.name[i - 1]) continue;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, g_td_prof.ev[i - 1], g_td_prof.ev[i]);
+                bool found = false;
+                for (auto& a : agg)
+                    if (a.first == g_td_prof.name[i]) {
+                        a.second.first += ms;
+                        a.second.second++;
+                        found = true;
+                    }
+                if (!found) agg.push_back({g_td_prof.name[i], {ms, 1}});
+            }
+            kj = ",\"kernels\":{";
+            for (size_t i = 0; i < agg.size(); i++) {
+                snprintf(kb, sizeof(kb), "%s\"%s\":{\"ms\":%.6f,\"launches\":%d}", i ? "," : "",
+                         agg[i].first.c_str(), agg[i].second.first, agg[i].second.second);
+                kj += kb;
+            }
+            kj += "}";
+        }
+        snprintf(kb, sizeof(kb), ",\"split_tensor_flops\":%.6e", g_split_tensor_flops - split_flops0);
+        kj += kb;
+        h->stats.pop_back();
+        h->stats += kj + "}";
+    }
     {
         char lb[64];
         snprintf(lb, sizeof(lb), ",\"launches\":%lld}", g_td_launches - launches0);

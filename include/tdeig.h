@@ -56,7 +56,18 @@ enum {
     /* Time every kernel launch of the solve with CUDA events on the solve's
      * stream; tdeig_last_stats then lists per kernel its launches and device
      * milliseconds under "kernels".  Not combined with TDEIG_FLAG_GRAPH. */
-    TDEIG_FLAG_PROFILE = 1 << 13
+    TDEIG_FLAG_PROFILE = 1 << 13,
+    /* ADC2: record, for every node of every HSS tree, its features and the
+     * rank its interpolative decompositions found (tdeig_rank_records). */
+    TDEIG_FLAG_RECORD = 1 << 14,
+    /* ADC2: seed the sampling rank of each HSS merge with the model given to
+     * tdeig_set_rank_model (TDEIG_EINVAL when none is set): r = ceil(exp(max
+     * over the merge's nodes of the prediction) - 1), clamped to [1, rank_cap].
+     * When an ID of the merge stops at the sample size r + oversample with
+     * more rows than that (its sampled residual is then not certified) and the
+     * rank estimate of eq. (bounds) is larger than r, the merge is rebuilt with
+     * the estimate; stats report "seed" per merge and "mlp_fallbacks". */
+    TDEIG_FLAG_MLP_SEED = 1 << 15
 };
 
 enum {
@@ -142,6 +153,70 @@ int tdeig_secular(tdeig_handle h, int64_t K, const double* d, const double* z, d
 int tdeig_lowner_cauchy(tdeig_handle h, int64_t K, const double* d, const double* gamma,
                         const double* mu, const double* z, double rho,
                         double* uhat, double* v, double* Qhat);
+
+/* ---------------------------------------------------------------------- */
+/* Learned rank seed for ADC2 (not in the paper; it replaces the rank       */
+/* estimate of eq. (bounds) as the first guess of the sampling rank r,      */
+/* with that estimate kept as the fallback).                                */
+/* Features of an HSS node spanning rows [s0, s1) of a merge of size n with */
+/* K survivors (all logarithms of positive quantities):                     */
+/*   0 log2(s1 - s0)                 block size                             */
+/*   1 log10(min gap / spread)       gaps gamma_i, mu_i inside the block    */
+/*   2 log10(median gap / spread)                                           */
+/*   3 log10(boundary dist / spread) min over the block's boundaries of     */
+/*                                   (d_b - d_{b-1}) + gamma_b (Sec. 4.1)   */
+/*   4 log10(sum of uhat_i^2 in the block)   u mass                         */
+/*   5 (n - K) / n                   deflated fraction                      */
+/*   6 log2(K)                                                              */
+/* spread = lambda_K - d_1.  Target: ln(rank + 1).                          */
+/* Model: 7 -> 64 -> 64 -> 1, ReLU, weights and activations rounded to BF16,*/
+/* FP32 accumulation.  Parameters (float, row-major out x in):              */
+/*   W1[64][7] b1[64] W2[64][64] b2[64] W3[64] b3[1]                        */
+/* Inputs are standardised with mean[7], std[7] before the first layer.     */
+/* All arrays below are host or device float arrays of the stated sizes.    */
+/* ---------------------------------------------------------------------- */
+#define TDEIG_MLP_IN 7
+#define TDEIG_MLP_HIDDEN 64
+#define TDEIG_MLP_PARAMS (64 * 7 + 64 + 64 * 64 + 64 + 64 + 1)
+
+/* y[i] = model(X[i, :]) for n samples (X row-major n x 7). */
+int tdeig_mlp_forward(tdeig_handle h, const float* params, const float* mean, const float* std,
+                      const float* X, int64_t n, float* y);
+
+/* Loss 0.5 mean_i (model(X_i) - t_i)^2 and its gradient with respect to the
+ * parameters (TDEIG_MLP_PARAMS floats), by the backward kernel. */
+int tdeig_mlp_grad(tdeig_handle h, const float* params, const float* mean, const float* std,
+                   const float* X, const float* t, int64_t n, float* loss, float* grad);
+
+/* Adam training on the GPU: `epochs` passes over the n samples in shuffled
+ * minibatches of `batch`; params holds the initial values on entry and the
+ * trained ones on return; *final_loss is the loss on all samples afterwards. */
+int tdeig_mlp_train(tdeig_handle h, float* params, const float* mean, const float* std,
+                    const float* X, const float* t, int64_t n, int epochs, int batch, float lr,
+                    uint64_t seed, float* final_loss);
+
+/* Model used by TDEIG_FLAG_MLP_SEED (copied into the handle); params NULL
+ * removes it. */
+int tdeig_set_rank_model(tdeig_handle h, const float* params, const float* mean, const float* std);
+
+/* Features (above) of nb HSS nodes of one merge: d, gamma, mu, uhat are the K
+ * deflated poles, the gaps gamma_i = lambda_i - d_i and mu_i = d_{i+1} -
+ * lambda_i (as tdeig_secular returns them) and the Lowner vector (host or
+ * device double arrays); n >= K is the merge size; ranges (host int array,
+ * 2 nb entries) holds each node's [s0, s1) with 0 <= s0 < s1 <= K; out (host
+ * or device float array) receives nb x 7 features, row-major.  The median gap
+ * is the centre of its bin in a histogram of 0.025-decade bins over
+ * [1e-24, 100) (values outside fall in the end bins). */
+int tdeig_node_features(tdeig_handle h, int64_t K, int64_t n, const double* d, const double* gamma,
+                        const double* mu, const double* uhat, int64_t nb, const int* ranges,
+                        float* out);
+
+/* Records of the last solve made with TDEIG_FLAG_RECORD: 8 floats per HSS node
+ * (the 7 features, then ln(rank + 1) with rank = max of the row and column ID
+ * ranks); nodes whose ID stopped at the sample size are left out (their rank
+ * is only a lower bound).  Copies at most cap records into buf (host) and
+ * returns how many exist, or a negative status. */
+int tdeig_rank_records(tdeig_handle h, float* buf, int64_t cap);
 
 /* Largest K accepted by tdeig_secular_noalloc. */
 #define TDEIG_NOALLOC_MAX_K 65536

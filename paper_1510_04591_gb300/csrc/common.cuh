@@ -56,6 +56,8 @@ struct LevelWS {
     int* gemmW;        // column of W used at product position p: survIdx[gemmCol[p]]
     int *K, *nrot;     // per merge
     int* kgrp;         // per merge: K1, Km
+    int* ordr;         // final ordering of an unsorted merge: rank of each value
+    int* unsorted;     // per merge: 1 when the deflated poles are not ascending
     double* rho;       // per merge, after normalisation of z
 };
 
@@ -93,7 +95,7 @@ void td_gemm_tiles(int variant, int n, int* bm, int* bn);
 void td_launch_update_dense(const MergeDesc* M, const int* toff, int nmerge, int total_tiles,
                             int variant, const LevelWS& ws, cudaStream_t st);
 void td_launch_finish(const MergeDesc* M, int nmerge, int nmax, const LevelWS& ws, cudaStream_t st);
-void td_launch_order(const MergeDesc* M, int nmerge, const LevelWS& ws, cudaStream_t st);
+void td_launch_order(const MergeDesc* M, int nmerge, int nmax, const LevelWS& ws, cudaStream_t st);
 
 // Largest total of N^2 (eigenvector entries) solved in one batched pass.
 #define TD_BATCH_CHUNK ((int64_t)1 << 30)

@@ -106,8 +106,16 @@ void hss_free(HssWS& w);
 // construction, multiplication) on the solve's stream.  With split != NULL the
 // sampling and Algorithm 3 products run as split-precision tensor-core products.
 struct SplitWS;
+// Learned rank seed of ADC2 (TDEIG_FLAG_MLP_SEED / TDEIG_FLAG_RECORD).
+struct HssLearn {
+    const float* model = nullptr;        // device: params | mean | std (seed only)
+    bool seed = false, record = false;
+    std::vector<float>* records = nullptr;   // 8 floats per recorded node
+    int fallbacks = 0;                   // merges rebuilt with the estimate
+};
 int hss_update_level(const tdeig_options& opt, int variant, int prec,
                      const std::vector<MergeDesc>& merges, const MergeDesc* dev_merges,
                      const std::vector<int>& K, const LevelWS& lws, HssWS& hws, int* status,
                      cudaStream_t st, std::string& stats,
-                     const std::function<int(const char*)>& mark, SplitWS* split);
+                     const std::function<int(const char*)>& mark, SplitWS* split,
+                     HssLearn* learn);

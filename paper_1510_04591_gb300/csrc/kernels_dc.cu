@@ -436,12 +436,12 @@ __global__ void __launch_bounds__(PREP_NT) k_prep(const MergeDesc* M, LevelWS ws
 }
 
 // W[:, c] = column src[c] of diag(Q1, Q2), for the sorted order c.
+// Grid: (merge, 256-row tile, 32-column tile).
 __global__ void k_build_w(const MergeDesc* M, LevelWS ws)
 {
-    MergeDesc md = M[blockIdx.y];
+    MergeDesc md = M[blockIdx.x];
     const int n = md.n, n1 = md.n1, n2 = n - n1;
-    const int rtiles = td_cdiv(n, 256);
-    const int rt = blockIdx.x % rtiles, ct = blockIdx.x / rtiles;
+    const int rt = blockIdx.y, ct = blockIdx.z;
     if (ct * 32 >= n) return;
     const int r = rt * 256 + threadIdx.x;
     if (r >= n) return;
@@ -459,12 +459,13 @@ __global__ void k_build_w(const MergeDesc* M, LevelWS ws)
 }
 
 // Deflation rotations, in sweep order, one row per thread.
+// Grid: (merge, 128-row tile).
 __global__ void k_rotate(const MergeDesc* M, LevelWS ws)
 {
-    MergeDesc md = M[blockIdx.y];
-    const int nrot = ws.nrot[blockIdx.y];
+    MergeDesc md = M[blockIdx.x];
+    const int nrot = ws.nrot[blockIdx.x];
     const int n = md.n, g0 = md.g0;
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y * blockDim.x + threadIdx.x;
     if (nrot == 0 || r >= n) return;
     for (int t = 0; t < nrot; t++) {
         int j = ws.rot_j[g0 + t], i = ws.rot_i[g0 + t];
@@ -480,9 +481,9 @@ void td_launch_merge_level(const MergeDesc* M, int nmerge, int nmax, int rows, i
 {
     (void)rows; (void)total_tiles; (void)status; (void)use_hss_mask;
     td_prof_begin(st); k_prep<<<nmerge, PREP_NT, 0, st>>>(M, ws); td_prof_end(st, "k_prep");
-    dim3 gw(td_cdiv(nmax, 256) * td_cdiv(nmax, 32), nmerge);
+    dim3 gw(nmerge, td_cdiv(nmax, 256), td_cdiv(nmax, 32));
     td_prof_begin(st); k_build_w<<<gw, 256, 0, st>>>(M, ws); td_prof_end(st, "k_build_w");
-    dim3 gr(td_cdiv(nmax, 128), nmerge);
+    dim3 gr(nmerge, td_cdiv(nmax, 128));
     td_prof_begin(st); k_rotate<<<gr, 128, 0, st>>>(M, ws); td_prof_end(st, "k_rotate");
 }
 
@@ -700,6 +701,13 @@ void td_launch_lowner_cauchy(const MergeDesc* M, int nmerge, int rows, int kmax,
 // Final ordering: new eigenvalues lambda (ascending) and deflated d merged into
 // ascending order, new ones first on ties (stable).  Positions feed the GEMM
 // epilogue and the deflated-column copy.
+//
+// When the deflated poles are ascending (no rotation moved one past another)
+// each position is a binary search, one CTA per merge (k_order).  Otherwise
+// k_order only flags the merge and the position of each of the n values (the
+// K new ones, then the n - K deflated ones) is its rank in the order (value,
+// then that index), counted in parallel by k_order_count and written by
+// k_order_place.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(PREP_NT) k_order(const MergeDesc* M, LevelWS ws)
 {
@@ -714,46 +722,84 @@ __global__ void __launch_bounds__(PREP_NT) k_order(const MergeDesc* M, LevelWS w
     // are the deflated values ascending?
     double bad = 0.0;
     for (int l = threadIdx.x; l + 1 < nd; l += blockDim.x)
-        if (ds[dfl[l + 1]] < ds[dfl[l]]) bad = 1.0;
+        if (!(ds[dfl[l + 1]] >= ds[dfl[l]])) bad = 1.0;
     const bool sorted = blk_max(bad, red) == 0.0;
+    if (threadIdx.x == 0) ws.unsorted[blockIdx.x] = sorted ? 0 : 1;
+    if (!sorted) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) ws.ordr[g0 + i] = 0;
+        return;
+    }
     const double scale = md.scale_ptr ? *md.scale_ptr : 1.0;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         double v = lk[k];
-        int cnt = 0;
-        if (sorted) {
-            int lo = 0, hi = nd;
-            while (lo < hi) { int mid = (lo + hi) >> 1; if (ds[dfl[mid]] < v) lo = mid + 1; else hi = mid; }
-            cnt = lo;
-        } else {
-            for (int l = 0; l < nd; l++) cnt += (ds[dfl[l]] < v);
-        }
-        ws.posNew[g0 + k] = k + cnt;
-        md.lam_out[k + cnt] = v * scale;
+        int lo = 0, hi = nd;   // count of deflated < v
+        while (lo < hi) { int mid = (lo + hi) >> 1; if (ds[dfl[mid]] < v) lo = mid + 1; else hi = mid; }
+        ws.posNew[g0 + k] = k + lo;
+        md.lam_out[k + lo] = v * scale;
     }
     for (int l = threadIdx.x; l < nd; l += blockDim.x) {
         double v = ds[dfl[l]];
         int lo = 0, hi = K;   // count of new <= v
         while (lo < hi) { int mid = (lo + hi) >> 1; if (lk[mid] <= v) lo = mid + 1; else hi = mid; }
-        int rank = l;
-        if (!sorted) {
-            rank = 0;
-            for (int q = 0; q < nd; q++) {
-                double u = ds[dfl[q]];
-                rank += (u < v) || (u == v && q < l);
-            }
-        }
-        ws.posDefl[g0 + l] = rank + lo;
-        md.lam_out[rank + lo] = v * scale;
+        ws.posDefl[g0 + l] = l + lo;
+        md.lam_out[l + lo] = v * scale;
     }
 }
 
+#define ORD_CH 2048
+
+__device__ __forceinline__ double order_value(const LevelWS& ws, int g0, int K, int i)
+{
+    return i < K ? ws.lamK[g0 + i] : ws.dsort[g0 + ws.deflIdx[g0 + i - K]];
+}
+
+// Grid: (merge, 256-value tile, ORD_CH-value chunk).  Each thread counts the
+// values of the chunk that precede its own value.
+__global__ void __launch_bounds__(256) k_order_count(const MergeDesc* M, LevelWS ws)
+{
+    __shared__ double sv[ORD_CH];
+    if (!ws.unsorted[blockIdx.x]) return;
+    const int n = M[blockIdx.x].n, g0 = M[blockIdx.x].g0;
+    const int K = ws.K[blockIdx.x];
+    const int i0 = blockIdx.y * 256, j0 = blockIdx.z * ORD_CH;
+    if (i0 >= n || j0 >= n) return;
+    const int jn = min(ORD_CH, n - j0);
+    for (int j = threadIdx.x; j < jn; j += 256) sv[j] = order_value(ws, g0, K, j0 + j);
+    __syncthreads();
+    const int i = i0 + threadIdx.x;
+    if (i >= n) return;
+    const double v = order_value(ws, g0, K, i);
+    int c = 0;
+    // values of the chunk strictly before i in index order win ties
+    const int jt = min(max(i - j0, 0), jn);
+    for (int j = 0; j < jt; j++) c += (sv[j] <= v);
+    for (int j = jt; j < jn; j++) c += (sv[j] < v);
+    atomicAdd(&ws.ordr[g0 + i], c);
+}
+
+// Grid: (merge, 256-value tile).
+__global__ void __launch_bounds__(256) k_order_place(const MergeDesc* M, LevelWS ws)
+{
+    if (!ws.unsorted[blockIdx.x]) return;
+    const MergeDesc& md = M[blockIdx.x];
+    const int n = md.n, g0 = md.g0;
+    const int K = ws.K[blockIdx.x];
+    const int i = blockIdx.y * 256 + threadIdx.x;
+    if (i >= n) return;
+    const double scale = md.scale_ptr ? *md.scale_ptr : 1.0;
+    const int pos = min(max(ws.ordr[g0 + i], 0), n - 1);
+    if (i < K) ws.posNew[g0 + i] = pos;
+    else ws.posDefl[g0 + i - K] = pos;
+    md.lam_out[pos] = order_value(ws, g0, K, i) * scale;
+}
+
+// Grid: (merge, 256-row tile, 32-column tile).
 __global__ void k_copy_defl(const MergeDesc* M, LevelWS ws)
 {
-    MergeDesc md = M[blockIdx.y];
+    MergeDesc md = M[blockIdx.x];
     const int n = md.n, g0 = md.g0;
-    const int nd = n - ws.K[blockIdx.y];
-    const int rtiles = td_cdiv(n, 256);
-    const int rt = blockIdx.x % rtiles, ct = blockIdx.x / rtiles;
+    const int nd = n - ws.K[blockIdx.x];
+    const int rt = blockIdx.y, ct = blockIdx.z;
     if (ct * 32 >= nd) return;
     const int r = rt * 256 + threadIdx.x;
     if (r >= n) return;
@@ -766,7 +812,7 @@ __global__ void k_copy_defl(const MergeDesc* M, LevelWS ws)
 
 void td_launch_finish(const MergeDesc* M, int nmerge, int nmax, const LevelWS& ws, cudaStream_t st)
 {
-    dim3 g(td_cdiv(nmax, 256) * td_cdiv(nmax, 32), nmerge);
+    dim3 g(nmerge, td_cdiv(nmax, 256), td_cdiv(nmax, 32));
     td_prof_begin(st); k_copy_defl<<<g, 256, 0, st>>>(M, ws); td_prof_end(st, "k_copy_defl");
 }
 
@@ -882,9 +928,13 @@ void td_launch_update_dense(const MergeDesc* M, const int* toff, int nmerge, int
 }
 
 // Order kernel launcher (separate so the HSS path can reuse it).
-void td_launch_order(const MergeDesc* M, int nmerge, const LevelWS& ws, cudaStream_t st)
+void td_launch_order(const MergeDesc* M, int nmerge, int nmax, const LevelWS& ws, cudaStream_t st)
 {
     td_prof_begin(st); k_order<<<nmerge, PREP_NT, 0, st>>>(M, ws); td_prof_end(st, "k_order");
+    dim3 gc(nmerge, td_cdiv(nmax, 256), td_cdiv(nmax, ORD_CH));
+    td_prof_begin(st); k_order_count<<<gc, 256, 0, st>>>(M, ws); td_prof_end(st, "k_order_count");
+    dim3 gp(nmerge, td_cdiv(nmax, 256));
+    td_prof_begin(st); k_order_place<<<gp, 256, 0, st>>>(M, ws); td_prof_end(st, "k_order_place");
 }
 
 // Stage entry points: one rank-one problem of size K placed as merge 0.

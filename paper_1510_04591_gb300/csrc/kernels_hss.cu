@@ -21,6 +21,7 @@
 
 #include "hss.cuh"
 #include "split.cuh"
+#include "mlp.cuh"
 
 #define HSS_NT 256
 
@@ -574,6 +575,9 @@ struct HNode {
 
 struct HMerge {
     int mi = 0, K = 0, n = 0, L = 0, r = 0, s = 0, mcap = 0, node_id = 0;
+    int r_est = 0;     // rank estimate of eq. (bounds)
+    int seed = 0;      // 0 estimate, 1 learned seed, 2 learned seed rejected -> estimate
+    size_t feat0 = 0;  // first node of this merge in the feature array
     std::vector<int> bounds;
     std::vector<HNode> nodes;
     double *Om = nullptr, *Y = nullptr, *Z = nullptr;
@@ -722,11 +726,29 @@ static int leaf_levels(int K, int m)
     return std::max(1, L);
 }
 
+// An ID that stopped at the sample size s with more than s rows: its rank is
+// only a lower bound and the sampled residual of the node is not certified.
+static bool node_saturated(const HMerge& h, int l, int q)
+{
+    const HNode& nd = h.nodes[hidx(l, q)];
+    int mu, mv;
+    if (l == h.L) {
+        mu = mv = nd.r1 - nd.r0;
+    } else {
+        const HNode& c1 = h.nodes[hidx(l + 1, 2 * q)];
+        const HNode& c2 = h.nodes[hidx(l + 1, 2 * q + 1)];
+        mu = c1.kU + c2.kU;
+        mv = c1.kV + c2.kV;
+    }
+    return (nd.kU >= h.s && mu > h.s) || (nd.kV >= h.s && mv > h.s);
+}
+
 int hss_update_level(const tdeig_options& opt, int variant, int prec,
                      const std::vector<MergeDesc>& merges, const MergeDesc* dev_merges,
                      const std::vector<int>& Kv, const LevelWS& lws, HssWS& hws, int* status,
                      cudaStream_t st, std::string& js,
-                     const std::function<int(const char*)>& mark, SplitWS* split)
+                     const std::function<int(const char*)>& mark, SplitWS* split,
+                     HssLearn* learn)
 {
     int prc = TDEIG_OK;
     auto run = [&](const std::vector<GemmDesc>& gv, GemmDesc* dev) -> double {
@@ -778,7 +800,13 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
     // small scratch for descriptors, bounds, ranks
     size_t desc_bytes = 1 << 20;
     for (auto& h : H) desc_bytes += ((1 << h.L) + 8) * 64 * 4;
-    int rc = grow(hws, desc_bytes + 64 * 1024, st);
+    const bool adc2 = (variant == TDEIG_MODE_ADC2);
+    const bool want_feat = learn && adc2 && (learn->record || (learn->seed && learn->model));
+    size_t nfeat = 0;   // HSS nodes (all levels) of all merges
+    for (auto& h : H) { h.feat0 = nfeat; nfeat += ((size_t)2 << h.L) - 2; }
+    const size_t feat_bytes =
+        want_feat ? nfeat * (sizeof(NodeFeatDesc) + (MLP_IN + 1) * sizeof(float)) + 4096 : 0;
+    int rc = grow(hws, 4096 * sizeof(GemmDesc) + desc_bytes + feat_bytes + 64 * 1024, st);
     if (rc) return rc;
     Bump b0{hws.base, 0, hws.cap};
     GemmDesc* dgemm = b0.take<GemmDesc>(4096);
@@ -816,8 +844,67 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
             HCU(cudaMemcpyAsync(&h.r, h.dev_r, sizeof(int), cudaMemcpyDeviceToHost, st));
         }
         HCU(cudaStreamSynchronize(st));
+        for (auto& h : H) h.r_est = h.r;
     }
 
+    // ---- node features and the learned seed (ADC2) ------------------------
+    std::vector<float> feat_h;
+    if (want_feat) {
+        std::vector<NodeFeatDesc> fd;
+        fd.reserve(nfeat);
+        NodeFeatDesc* dfd = b0.take<NodeFeatDesc>(nfeat);
+        float* dX = b0.take<float>(nfeat * MLP_IN);
+        float* dy = b0.take<float>(nfeat);
+        if (b0.off > b0.cap) return TDEIG_ENOMEM;
+        for (auto& h : H)
+            for (int l = 1; l <= h.L; l++) {
+                const int w = 1 << (h.L - l);
+                for (int q = 0; q < (1 << l); q++) {
+                    NodeFeatDesc f;
+                    f.d = h.d; f.gam = h.gam; f.mu = h.mu; f.uh = h.uh;
+                    f.K = h.K; f.n = h.n;
+                    f.s0 = h.bounds[q * w]; f.s1 = h.bounds[(q + 1) * w];
+                    f.out = dX + (h.feat0 + hidx(l, q) - 1) * MLP_IN;
+                    fd.push_back(f);
+                }
+            }
+        HCU(cudaMemcpyAsync(dfd, fd.data(), fd.size() * sizeof(NodeFeatDesc), cudaMemcpyHostToDevice, st));
+        mlp_launch_features(dfd, (int)fd.size(), st);
+        std::vector<float> yh;
+        if (learn->seed && learn->model) {
+            mlp_launch(learn->model, learn->model + MLP_P, learn->model + MLP_P + MLP_IN, dX, nullptr,
+                       nullptr, (int)nfeat, (int)nfeat, dy, nullptr, nullptr, st);
+            yh.resize(nfeat);
+            HCU(cudaMemcpyAsync(yh.data(), dy, nfeat * sizeof(float), cudaMemcpyDeviceToHost, st));
+        }
+        if (learn->record) {
+            feat_h.resize(nfeat * MLP_IN);
+            HCU(cudaMemcpyAsync(feat_h.data(), dX, nfeat * MLP_IN * sizeof(float), cudaMemcpyDeviceToHost, st));
+        }
+        HCU(cudaStreamSynchronize(st));
+        HCU(cudaGetLastError());
+        if (!yh.empty()) {
+            // r = ceil(exp(max over the merge's nodes of the predicted ln(rank + 1)) - 1)
+            for (auto& h : H) {
+                float ymax = -1e30f;
+                for (size_t i = h.feat0; i < h.feat0 + ((size_t)2 << h.L) - 2; i++) ymax = fmaxf(ymax, yh[i]);
+                const double rr = ceil(exp(std::min((double)ymax, 10.0)) - 1.0);
+                h.r = (int)std::max(1.0, std::min((double)opt.rank_cap, rr));
+                h.seed = 1;
+            }
+        }
+    }
+
+    // A merge seeded by the model is accepted unless one of its IDs reached the
+    // sample size with more rows than that (its sampled residual is then not
+    // certified); such a merge is rebuilt with the estimate when the estimate
+    // samples more, else kept (the estimate would have reached the same bound).
+    Bump B{hws.base, 0, hws.cap};
+    FillDesc* dfill = nullptr;
+    IdDesc* did = nullptr;
+    GatherDesc* dgat = nullptr;
+    int Lmax = 0;
+    for (int attempt = 0;; attempt++) {
     // ---- sizes and allocation ---------------------------------------------
     size_t total = b0.off + 1024;
     for (auto& h : H) {
@@ -850,10 +937,10 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
         dgemm = b0.take<GemmDesc>(4096);
         b0.take<int>(desc_bytes / 8);
     }
-    Bump B{hws.base, b0.off, hws.cap};
-    FillDesc* dfill = B.take<FillDesc>(8192);
-    IdDesc* did = B.take<IdDesc>(8192);
-    GatherDesc* dgat = B.take<GatherDesc>(8192);
+    B = Bump{hws.base, b0.off, hws.cap};
+    dfill = B.take<FillDesc>(8192);
+    did = B.take<IdDesc>(8192);
+    dgat = B.take<GatherDesc>(8192);
     for (auto& h : H) {
         const int s = h.s, K = h.K, nn = h.n;
         h.Om = B.take<double>((size_t)K * s);
@@ -901,7 +988,7 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
     }
     if (B.off > B.cap) return TDEIG_ENOMEM;
 
-    int Lmax = 0;
+    Lmax = 0;
     for (auto& h : H) Lmax = std::max(Lmax, h.L);
     if (adc1) {
         if ((rc = mark("hss_build"))) return rc;
@@ -1119,6 +1206,34 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
         }
         launch_fill(fills, dfill, st);
     }
+    bool again = false;
+    for (auto& h : H) {
+        if (h.seed != 1 || adc1) continue;
+        bool sat = false;
+        for (int l = 1; l <= h.L; l++)
+            for (int q = 0; q < (1 << l); q++) sat |= node_saturated(h, l, q);
+        if (sat && h.r_est > h.r) {
+            h.r = h.r_est;
+            h.seed = 2;
+            again = true;
+            if (learn) learn->fallbacks++;
+        }
+    }
+    if (!again) break;
+    }   // attempts
+
+    if (learn && learn->record && adc2 && !feat_h.empty()) {
+        // features and ln(rank + 1) of every node whose rank the IDs certified
+        for (auto& h : H)
+            for (int l = 1; l <= h.L; l++)
+                for (int q = 0; q < (1 << l); q++) {
+                    if (node_saturated(h, l, q)) continue;
+                    const HNode& nd = h.nodes[hidx(l, q)];
+                    const float* f = feat_h.data() + (h.feat0 + hidx(l, q) - 1) * MLP_IN;
+                    learn->records->insert(learn->records->end(), f, f + MLP_IN);
+                    learn->records->push_back((float)log((double)std::max(nd.kU, nd.kV) + 1.0));
+                }
+    }
 
     if ((rc = mark("hss_mult"))) return rc;
     // ---- Algorithm 3: X H with X = W[:, surv] (n x K) ----------------------
@@ -1240,8 +1355,11 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
                 ksum += nd.kU + nd.kV;
                 cnt += 2;
             }
-        snprintf(buf, sizeof(buf), "%s{\"n\":%d,\"K\":%d,\"L\":%d,\"r\":%d,\"s\":%d,\"kmax\":%d,\"kmean\":%.2f}",
-                 js.empty() ? "" : ",", h.n, h.K, h.L, h.r, h.s, kmax, cnt ? ksum / cnt : 0.0);
+        snprintf(buf, sizeof(buf),
+                 "%s{\"n\":%d,\"K\":%d,\"L\":%d,\"r\":%d,\"s\":%d,\"kmax\":%d,\"kmean\":%.2f,"
+                 "\"r_est\":%d,\"seed\":%d}",
+                 js.empty() ? "" : ",", h.n, h.K, h.L, h.r, h.s, kmax, cnt ? ksum / cnt : 0.0, h.r_est,
+                 h.seed);
         js += buf;
     }
     return prc;

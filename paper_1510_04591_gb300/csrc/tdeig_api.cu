@@ -15,6 +15,7 @@
 #include "common.cuh"
 #include "hss.cuh"
 #include "split.cuh"
+#include "mlp.cuh"
 
 struct LevelPlan {
     std::vector<MergeDesc> merges;
@@ -73,6 +74,9 @@ struct tdeig_ctx {
     std::vector<std::pair<int, std::vector<int>>> tuning;   // level key -> event indices of a trial
     std::vector<cudaEvent_t> tune_ev;  // events of the trials of the current solve
     GraphEntry graph;                  // the last captured solve
+    float* mlp = nullptr;              // rank model on the device: params, mean, std
+    std::vector<float> records;        // TDEIG_FLAG_RECORD output of the last solve
+    int mlp_fallbacks = 0;             // merges rebuilt with the estimate in the last solve
 };
 
 static const char* kStatusMsg[] = {
@@ -148,6 +152,7 @@ extern "C" int tdeig_destroy(tdeig_handle h)
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     for (cudaEvent_t e : h->tune_ev) cudaEventDestroy(e);
     if (h->graph.exec) cudaGraphExecDestroy(h->graph.exec);
+    if (h->mlp) cudaFree(h->mlp);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
     return TDEIG_OK;
@@ -331,8 +336,8 @@ static void build_plan(Plan& P, const Bufs& B, int leaf)
 
 static size_t level_ws_bytes(int64_t R, int64_t Mmax)
 {
-    return (size_t)R * (12 * sizeof(double) + 10 * sizeof(int)) + Mmax * (4 * sizeof(int) + 8) +
-           32 * 256;
+    return (size_t)R * (12 * sizeof(double) + 11 * sizeof(int)) + Mmax * (5 * sizeof(int) + 8) +
+           34 * 256;
 }
 
 static void carve_level_ws(Arena& a, LevelWS& w, int64_t R, int64_t Mmax)
@@ -362,6 +367,8 @@ static void carve_level_ws(Arena& a, LevelWS& w, int64_t R, int64_t Mmax)
     w.K = a.take<int>(Mmax);
     w.nrot = a.take<int>(Mmax);
     w.kgrp = a.take<int>(2 * Mmax);
+    w.ordr = a.take<int>(R);
+    w.unsorted = a.take<int>(Mmax);
     w.rho = a.take<double>(Mmax);
 }
 
@@ -421,6 +428,8 @@ static std::string stats_json(tdeig_ctx* h, const Plan& P, const std::vector<int
              status);
     js += buf;
     if (!hss_js.empty()) js += ",\"hss\":[" + hss_js + "]";
+    snprintf(buf, sizeof(buf), ",\"mlp_fallbacks\":%d", h->mlp_fallbacks);
+    js += buf;
     js += "}";
     return js;
 }
@@ -442,8 +451,10 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     const int variant = mode & TDEIG_MODE_MASK;
     const int prec = mode & TDEIG_PREC_MASK;
     if (variant > TDEIG_MODE_ADC2 ||
-        (mode & ~(TDEIG_MODE_MASK | TDEIG_PREC_MASK | TDEIG_FLAG_GRAPH | TDEIG_FLAG_PROFILE)))
+        (mode & ~(TDEIG_MODE_MASK | TDEIG_PREC_MASK | TDEIG_FLAG_GRAPH | TDEIG_FLAG_PROFILE |
+                  TDEIG_FLAG_RECORD | TDEIG_FLAG_MLP_SEED)))
         return TDEIG_EINVAL;
+    if ((mode & TDEIG_FLAG_MLP_SEED) && !h->mlp) return TDEIG_EINVAL;
     if (prec != TDEIG_PREC_FP64 && prec != TDEIG_PREC_SPLIT) return TDEIG_EINVAL;
     auto t_start = std::chrono::steady_clock::now();
     const long long launches0 = g_td_launches;
@@ -637,6 +648,11 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     CU(cudaGetLastError());
 
     std::string hss_js;
+    HssLearn learn;
+    learn.model = h->mlp;
+    learn.seed = (mode & TDEIG_FLAG_MLP_SEED) != 0;
+    learn.record = (mode & TDEIG_FLAG_RECORD) != 0;
+    learn.records = &h->records;
     for (size_t li = 0; li < P.levels.size(); li++) {
         LevelPlan& L = P.levels[li];
         const int nm = (int)L.merges.size();
@@ -667,12 +683,12 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
         MARK("lowner_cauchy", lv);
         td_launch_lowner_cauchy(Md, nm, L.rows, L.kmax, lws, any_hss ? 1 : 2, st);
         MARK("order", lv);
-        td_launch_order(Md, nm, lws, st);
+        td_launch_order(Md, nm, L.nmax, lws, st);
         MARK(any_hss ? "hss_update" : "update", lv);
         if (any_hss) {
             rc = hss_update_level(h->opt, variant, prec, L.merges, Md, Kh, lws, h->hss, status, st,
                                   hss_js, [&](const char* nm) { return mark(nm, lv); },
-                                  split ? &h->split : nullptr);
+                                  split ? &h->split : nullptr, &learn);
             if (rc) return rc;
         } else if (split) {
             // block-structured update as split-precision tensor-core products
@@ -770,6 +786,7 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     std::vector<double> sc(batch);
     CU(cudaMemcpy(sc.data(), B.scale, batch * sizeof(double), cudaMemcpyDeviceToHost));
     double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    h->mlp_fallbacks = learn.fallbacks;
     h->stats = stats_json(h, P, kh, gh, hss_js, secs, hstat[0]);
     if (graph) h->stats.insert(1, "\"graph\":\"captured\",");
     {
@@ -824,6 +841,7 @@ extern "C" int tdeig_solve(tdeig_handle h, const double* d, const double* e, int
     if (N == 0) return TDEIG_OK;
     if (!d || !lambda_out || (N > 1 && !e)) return TDEIG_EINVAL;
     CU(cudaSetDevice(h->device));
+    h->records.clear();
     return solve_impl(h, 1, &N, d, N > 1 ? e : nullptr, lambda_out, Q_out, mode);
 }
 
@@ -842,6 +860,7 @@ extern "C" int tdeig_solve_batched(tdeig_handle h, int64_t batch, const int64_t*
     if (R == 0) return TDEIG_OK;
     if (!d_cat || !lambda_cat || (E > 0 && !e_cat)) return TDEIG_EINVAL;
     CU(cudaSetDevice(h->device));
+    h->records.clear();
     // Members are solved in consecutive chunks whose eigenvector blocks total at
     // most TD_BATCH_CHUNK elements, which bounds the workspace (about five such
     // buffers) however large the batch is.
@@ -971,6 +990,230 @@ extern "C" int tdeig_lowner_cauchy(tdeig_handle h, int64_t K, const double* d, c
     CU(cudaGetLastError());
     if ((rc = copy_out(uhat, lws.uhat, K, st)) || (rc = copy_out(v, lws.vv, K, st))) return rc;
     if (Qhat && !qdev) CU(cudaMemcpyAsync(Qhat, qbuf, K * K * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    return TDEIG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Learned rank seed: model entry points
+// ---------------------------------------------------------------------------
+namespace {
+// A small device scratch for the model calls, freed on scope exit.
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+};
+
+int upload_f(float* dst, const float* src, int64_t n, cudaStream_t st)
+{
+    cudaMemcpyKind k = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    return cudaMemcpyAsync(dst, src, n * sizeof(float), k, st) == cudaSuccess ? TDEIG_OK : TDEIG_ECUDA;
+}
+
+int download_f(float* dst, const float* src, int64_t n, cudaStream_t st)
+{
+    cudaMemcpyKind k = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    return cudaMemcpyAsync(dst, src, n * sizeof(float), k, st) == cudaSuccess ? TDEIG_OK : TDEIG_ECUDA;
+}
+}  // namespace
+
+// layout of a model scratch: params | mean | std | grad | m | v | loss | X | t | y | perm
+static int model_scratch(DevBuf& b, int64_t n, float** P, float** mean, float** sd, float** grad,
+                         float** m, float** v, float** loss, float** X, float** t, float** y,
+                         int** perm)
+{
+    const size_t f = 6 * (size_t)MLP_P + 2 * MLP_IN + 64 + (size_t)n * (MLP_IN + 2) + 256;
+    if (cudaMalloc(&b.p, f * sizeof(float) + (size_t)n * sizeof(int) + 1024) != cudaSuccess) {
+        cudaGetLastError();
+        return TDEIG_ENOMEM;
+    }
+    float* q = (float*)b.p;
+    *P = q; q += MLP_P;
+    *grad = q; q += MLP_P;
+    *m = q; q += MLP_P;
+    *v = q; q += MLP_P;
+    *mean = q; q += MLP_IN;
+    *sd = q; q += MLP_IN;
+    *loss = q; q += 64;
+    *X = q; q += (size_t)n * MLP_IN;
+    *t = q; q += n;
+    *y = q; q += n;
+    *perm = (int*)q;
+    return TDEIG_OK;
+}
+
+extern "C" int tdeig_mlp_forward(tdeig_handle h, const float* params, const float* mean,
+                                 const float* std, const float* X, int64_t n, float* y)
+{
+    if (!h || !params || !mean || !std || n < 0 || (n > 0 && (!X || !y)) || n > (1 << 26))
+        return TDEIG_EINVAL;
+    if (n == 0) return TDEIG_OK;
+    CU(cudaSetDevice(h->device));
+    cudaStream_t st = h->stream;
+    DevBuf b;
+    float *P, *M, *S, *G, *Mm, *Vv, *L, *Xd, *Td, *Yd;
+    int* perm;
+    int rc = model_scratch(b, n, &P, &M, &S, &G, &Mm, &Vv, &L, &Xd, &Td, &Yd, &perm);
+    if (rc) return rc;
+    if ((rc = upload_f(P, params, MLP_P, st)) || (rc = upload_f(M, mean, MLP_IN, st)) ||
+        (rc = upload_f(S, std, MLP_IN, st)) || (rc = upload_f(Xd, X, n * MLP_IN, st)))
+        return rc;
+    mlp_launch(P, M, S, Xd, nullptr, nullptr, (int)n, (int)n, Yd, nullptr, nullptr, st);
+    CU(cudaGetLastError());
+    if ((rc = download_f(y, Yd, n, st))) return rc;
+    CU(cudaStreamSynchronize(st));
+    return TDEIG_OK;
+}
+
+extern "C" int tdeig_mlp_grad(tdeig_handle h, const float* params, const float* mean,
+                              const float* std, const float* X, const float* t, int64_t n,
+                              float* loss, float* grad)
+{
+    if (!h || !params || !mean || !std || !X || !t || !loss || !grad || n < 1 || n > (1 << 26))
+        return TDEIG_EINVAL;
+    CU(cudaSetDevice(h->device));
+    cudaStream_t st = h->stream;
+    DevBuf b;
+    float *P, *M, *S, *G, *Mm, *Vv, *L, *Xd, *Td, *Yd;
+    int* perm;
+    int rc = model_scratch(b, n, &P, &M, &S, &G, &Mm, &Vv, &L, &Xd, &Td, &Yd, &perm);
+    if (rc) return rc;
+    if ((rc = upload_f(P, params, MLP_P, st)) || (rc = upload_f(M, mean, MLP_IN, st)) ||
+        (rc = upload_f(S, std, MLP_IN, st)) || (rc = upload_f(Xd, X, n * MLP_IN, st)) ||
+        (rc = upload_f(Td, t, n, st)))
+        return rc;
+    CU(cudaMemsetAsync(G, 0, MLP_P * sizeof(float), st));
+    CU(cudaMemsetAsync(L, 0, sizeof(float), st));
+    mlp_launch(P, M, S, Xd, Td, nullptr, (int)n, (int)n, nullptr, G, L, st);
+    CU(cudaGetLastError());
+    if ((rc = download_f(grad, G, MLP_P, st)) || (rc = download_f(loss, L, 1, st))) return rc;
+    CU(cudaStreamSynchronize(st));
+    return TDEIG_OK;
+}
+
+extern "C" int tdeig_mlp_train(tdeig_handle h, float* params, const float* mean, const float* std,
+                               const float* X, const float* t, int64_t n, int epochs, int batch,
+                               float lr, uint64_t seed, float* final_loss)
+{
+    if (!h || !params || !mean || !std || !X || !t || n < 1 || n > (1 << 26) || epochs < 0 ||
+        batch < 1 || !(lr > 0.0f))
+        return TDEIG_EINVAL;
+    CU(cudaSetDevice(h->device));
+    cudaStream_t st = h->stream;
+    DevBuf b;
+    float *P, *M, *S, *G, *Mm, *Vv, *L, *Xd, *Td, *Yd;
+    int* perm;
+    int rc = model_scratch(b, n, &P, &M, &S, &G, &Mm, &Vv, &L, &Xd, &Td, &Yd, &perm);
+    if (rc) return rc;
+    if ((rc = upload_f(P, params, MLP_P, st)) || (rc = upload_f(M, mean, MLP_IN, st)) ||
+        (rc = upload_f(S, std, MLP_IN, st)) || (rc = upload_f(Xd, X, n * MLP_IN, st)) ||
+        (rc = upload_f(Td, t, n, st)))
+        return rc;
+    CU(cudaMemsetAsync(Mm, 0, 2 * MLP_P * sizeof(float), st));
+    CU(cudaMemsetAsync(G, 0, MLP_P * sizeof(float), st));
+    std::vector<int> order(n);
+    for (int64_t i = 0; i < n; i++) order[i] = (int)i;
+    uint64_t s = seed ? seed : 0x9E3779B97F4A7C15ull;
+    int step = 0;
+    for (int ep = 0; ep < epochs; ep++) {
+        for (int64_t i = n - 1; i > 0; i--) {   // Fisher-Yates with a 64-bit LCG
+            s = s * 6364136223846793005ull + 1442695040888963407ull;
+            const int64_t j = (int64_t)((s >> 33) % (uint64_t)(i + 1));
+            std::swap(order[i], order[j]);
+        }
+        CU(cudaMemcpyAsync(perm, order.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+        CU(cudaStreamSynchronize(st));   // order is rewritten next epoch
+        for (int64_t b0 = 0; b0 < n; b0 += batch) {
+            const int nb = (int)std::min<int64_t>(batch, n - b0);
+            mlp_launch(P, M, S, Xd, Td, perm + b0, nb, nb, nullptr, G, nullptr, st);
+            mlp_launch_adam(P, G, Mm, Vv, lr, ++step, st);   // clears G
+        }
+    }
+    CU(cudaMemsetAsync(G, 0, MLP_P * sizeof(float), st));
+    CU(cudaMemsetAsync(L, 0, sizeof(float), st));
+    mlp_launch(P, M, S, Xd, Td, nullptr, (int)n, (int)n, nullptr, G, L, st);
+    CU(cudaGetLastError());
+    float lh = 0.0f;
+    if ((rc = download_f(params, P, MLP_P, st))) return rc;
+    CU(cudaMemcpyAsync(&lh, L, sizeof(float), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (final_loss) *final_loss = lh;
+    return TDEIG_OK;
+}
+
+extern "C" int tdeig_set_rank_model(tdeig_handle h, const float* params, const float* mean,
+                                    const float* std)
+{
+    if (!h) return TDEIG_EINVAL;
+    CU(cudaSetDevice(h->device));
+    if (!params) {
+        if (h->mlp) cudaFree(h->mlp);
+        h->mlp = nullptr;
+        return TDEIG_OK;
+    }
+    if (!mean || !std) return TDEIG_EINVAL;
+    if (!h->mlp && cudaMalloc(&h->mlp, (MLP_P + 2 * MLP_IN) * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        h->mlp = nullptr;
+        return TDEIG_ENOMEM;
+    }
+    int rc;
+    if ((rc = upload_f(h->mlp, params, MLP_P, h->stream)) ||
+        (rc = upload_f(h->mlp + MLP_P, mean, MLP_IN, h->stream)) ||
+        (rc = upload_f(h->mlp + MLP_P + MLP_IN, std, MLP_IN, h->stream)))
+        return rc;
+    CU(cudaStreamSynchronize(h->stream));
+    return TDEIG_OK;
+}
+
+extern "C" int tdeig_rank_records(tdeig_handle h, float* buf, int64_t cap)
+{
+    if (!h || cap < 0 || (cap > 0 && !buf)) return TDEIG_EINVAL;
+    const int64_t n = (int64_t)h->records.size() / (MLP_IN + 1);
+    const int64_t c = std::min(n, cap);
+    if (c > 0) memcpy(buf, h->records.data(), (size_t)c * (MLP_IN + 1) * sizeof(float));
+    return (int)n;
+}
+
+extern "C" int tdeig_node_features(tdeig_handle h, int64_t K, int64_t n, const double* d,
+                                   const double* gamma, const double* mu, const double* uhat,
+                                   int64_t nb, const int* ranges, float* out)
+{
+    if (!h || K < 1 || K > (1 << 26) || n < K || nb < 0 || nb > (1 << 20)) return TDEIG_EINVAL;
+    if (!d || !gamma || !mu || !uhat || (nb > 0 && (!ranges || !out))) return TDEIG_EINVAL;
+    for (int64_t i = 0; i < nb; i++)
+        if (ranges[2 * i] < 0 || ranges[2 * i] >= ranges[2 * i + 1] || ranges[2 * i + 1] > K)
+            return TDEIG_EINVAL;
+    if (nb == 0) return TDEIG_OK;
+    CU(cudaSetDevice(h->device));
+    cudaStream_t st = h->stream;
+    DevBuf b;
+    const size_t bytes = 4 * (size_t)K * sizeof(double) + nb * sizeof(NodeFeatDesc) +
+                         nb * MLP_IN * sizeof(float) + 1024;
+    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return TDEIG_ENOMEM;
+    }
+    double* dd = (double*)b.p;
+    double *dg = dd + K, *dm = dd + 2 * K, *du = dd + 3 * K;
+    NodeFeatDesc* dfd = (NodeFeatDesc*)(du + K);
+    float* dout = (float*)(dfd + nb);
+    int rc;
+    if ((rc = copy_in(dd, d, K, st)) || (rc = copy_in(dg, gamma, K, st)) ||
+        (rc = copy_in(dm, mu, K, st)) || (rc = copy_in(du, uhat, K, st)))
+        return rc;
+    std::vector<NodeFeatDesc> fd(nb);
+    for (int64_t i = 0; i < nb; i++) {
+        NodeFeatDesc& f = fd[i];
+        f.d = dd; f.gam = dg; f.mu = dm; f.uh = du;
+        f.K = (int)K; f.n = (int)std::min<int64_t>(n, INT32_MAX);
+        f.s0 = ranges[2 * i]; f.s1 = ranges[2 * i + 1];
+        f.out = dout + i * MLP_IN;
+    }
+    CU(cudaMemcpyAsync(dfd, fd.data(), nb * sizeof(NodeFeatDesc), cudaMemcpyHostToDevice, st));
+    mlp_launch_features(dfd, (int)nb, st);
+    CU(cudaGetLastError());
+    if ((rc = download_f(out, dout, nb * MLP_IN, st))) return rc;
     CU(cudaStreamSynchronize(st));
     return TDEIG_OK;
 }

@@ -19,6 +19,11 @@ LIB_PATH = os.path.join(_HERE, "libtdeig.so")
 MODE_DENSE, MODE_ADC1, MODE_ADC2 = 0, 1, 2
 PREC_FP64, PREC_SPLIT = 0 << 8, 1 << 8
 FLAG_GRAPH = 1 << 12
+FLAG_PROFILE = 1 << 13
+FLAG_RECORD = 1 << 14
+FLAG_MLP_SEED = 1 << 15
+MLP_IN, MLP_HIDDEN = 7, 64
+MLP_PARAMS = MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN + 1
 _MODES = {"dense": MODE_DENSE, "adc1": MODE_ADC1, "adc2": MODE_ADC2}
 _PRECS = {"fp64": PREC_FP64, "split": PREC_SPLIT}
 
@@ -73,6 +78,19 @@ def lib():
         L.tdeig_lowner_cauchy.restype = ctypes.c_int
         L.tdeig_secular_noalloc.argtypes = [_i64, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp]
         L.tdeig_secular_noalloc.restype = ctypes.c_int
+        L.tdeig_mlp_forward.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _vp]
+        L.tdeig_mlp_forward.restype = ctypes.c_int
+        L.tdeig_mlp_grad.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]
+        L.tdeig_mlp_grad.restype = ctypes.c_int
+        L.tdeig_mlp_train.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _i64, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_float, ctypes.c_uint64, _vp]
+        L.tdeig_mlp_train.restype = ctypes.c_int
+        L.tdeig_set_rank_model.argtypes = [_vp, _vp, _vp, _vp]
+        L.tdeig_set_rank_model.restype = ctypes.c_int
+        L.tdeig_rank_records.argtypes = [_vp, _vp, _i64]
+        L.tdeig_rank_records.restype = ctypes.c_int
+        L.tdeig_node_features.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp]
+        L.tdeig_node_features.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -174,7 +192,7 @@ class Solver:
         return lib().tdeig_solve(self.h, d_ptr, e_ptr, int(N), lam_ptr, q_ptr, int(mode))
 
     def solve(self, d, e, mode="dense", prec="fp64", vectors=True, out=None, check=True,
-              graph=False):
+              graph=False, flags=0):
         """Eigendecomposition of tridiag(e, d, e): returns (lam, Q), Q[:, j] <-> lam[j]."""
         d = _as_f64(d)
         e = _as_f64(e)
@@ -185,12 +203,12 @@ class Solver:
         else:
             lam, Q = out
         st = lib().tdeig_solve(self.h, _ptr(d), _ptr(e) if N > 1 else None, N, _ptr(lam), _ptr(Q),
-                               mode_code(mode, prec, graph))
+                               mode_code(mode, prec, graph) | flags)
         if check and st != OK:
             raise TdeigError(st, "tdeig_solve")
         return lam, Q
 
-    def solve_batched(self, ds, es, mode="dense", prec="fp64", graph=False, out=None):
+    def solve_batched(self, ds, es, mode="dense", prec="fp64", graph=False, out=None, flags=0):
         """Independent matrices (lists of numpy arrays / CPU or CUDA tensors)."""
         sizes = [int(x.shape[0]) for x in ds]
         if _is_torch(ds[0]):
@@ -206,7 +224,7 @@ class Solver:
             Qc = np.empty(sum(n * n for n in sizes))
         Ns = (_i64 * len(sizes))(*sizes)
         st = lib().tdeig_solve_batched(self.h, len(sizes), Ns, _ptr(dcat), _ptr(ecat), _ptr(lam),
-                                       _ptr(Qc), mode_code(mode, prec, graph))
+                                       _ptr(Qc), mode_code(mode, prec, graph) | flags)
         if st != OK:
             raise TdeigError(st, "tdeig_solve_batched")
         outs = []
@@ -241,3 +259,76 @@ class Solver:
         if st != OK:
             raise TdeigError(st, "tdeig_lowner_cauchy")
         return uh, v, Qh
+
+    # ----------------------------------------------------------------------
+    # learned rank seed (float32 host arrays; the model runs in the library)
+    # ----------------------------------------------------------------------
+    def mlp_forward(self, params, mean, std, X):
+        params, mean, std, X = (_as_f32(a) for a in (params, mean, std, X))
+        n = X.shape[0]
+        y = np.empty(n, dtype=np.float32)
+        st = lib().tdeig_mlp_forward(self.h, _ptr(params), _ptr(mean), _ptr(std), _ptr(X), n,
+                                     _ptr(y))
+        if st != OK:
+            raise TdeigError(st, "tdeig_mlp_forward")
+        return y
+
+    def mlp_grad(self, params, mean, std, X, t):
+        params, mean, std, X, t = (_as_f32(a) for a in (params, mean, std, X, t))
+        loss = np.zeros(1, dtype=np.float32)
+        grad = np.empty(MLP_PARAMS, dtype=np.float32)
+        st = lib().tdeig_mlp_grad(self.h, _ptr(params), _ptr(mean), _ptr(std), _ptr(X), _ptr(t),
+                                  X.shape[0], _ptr(loss), _ptr(grad))
+        if st != OK:
+            raise TdeigError(st, "tdeig_mlp_grad")
+        return float(loss[0]), grad
+
+    def mlp_train(self, params, mean, std, X, t, epochs=100, batch=256, lr=1e-3, seed=1):
+        """Adam on the GPU; returns (trained params, final loss)."""
+        p = _as_f32(params).copy()
+        mean, std, X, t = (_as_f32(a) for a in (mean, std, X, t))
+        loss = np.zeros(1, dtype=np.float32)
+        st = lib().tdeig_mlp_train(self.h, _ptr(p), _ptr(mean), _ptr(std), _ptr(X), _ptr(t),
+                                   X.shape[0], int(epochs), int(batch), float(lr), int(seed),
+                                   _ptr(loss))
+        if st != OK:
+            raise TdeigError(st, "tdeig_mlp_train")
+        return p, float(loss[0])
+
+    def set_rank_model(self, params=None, mean=None, std=None):
+        if params is None:
+            st = lib().tdeig_set_rank_model(self.h, None, None, None)
+        else:
+            params, mean, std = (_as_f32(a) for a in (params, mean, std))
+            self._model = (params, mean, std)
+            st = lib().tdeig_set_rank_model(self.h, _ptr(params), _ptr(mean), _ptr(std))
+        if st != OK:
+            raise TdeigError(st, "tdeig_set_rank_model")
+
+    def node_features(self, d, gamma, mu, uhat, n, ranges):
+        """Features (len(ranges) x 7, float32) of the nodes [s0, s1) of one merge."""
+        d, gamma, mu, uhat = (np.ascontiguousarray(_as_f64(a)) if not _is_torch(a) else _as_f64(a)
+                              for a in (d, gamma, mu, uhat))
+        rg = np.ascontiguousarray(np.asarray(ranges, dtype=np.int32).reshape(-1, 2))
+        out = np.empty((rg.shape[0], MLP_IN), dtype=np.float32)
+        st = lib().tdeig_node_features(self.h, d.shape[0], int(n), _ptr(d), _ptr(gamma), _ptr(mu),
+                                       _ptr(uhat), rg.shape[0], _ptr(rg), _ptr(out))
+        if st != OK:
+            raise TdeigError(st, "tdeig_node_features")
+        return out
+
+    def rank_records(self):
+        """(features n x 7, ln(rank + 1) n) recorded by the last TDEIG_FLAG_RECORD solve."""
+        n = lib().tdeig_rank_records(self.h, None, 0)
+        if n < 0:
+            raise TdeigError(n, "tdeig_rank_records")
+        buf = np.empty((n, MLP_IN + 1), dtype=np.float32)
+        if n:
+            lib().tdeig_rank_records(self.h, _ptr(buf), n)
+        return buf[:, :MLP_IN].copy(), buf[:, MLP_IN].copy()
+
+
+def _as_f32(x):
+    if _is_torch(x):
+        x = x.detach().cpu().numpy()
+    return np.ascontiguousarray(x, dtype=np.float32)

@@ -315,60 +315,88 @@ __global__ void __launch_bounds__(PREP_NT) k_prep(const MergeDesc* M, LevelWS ws
     }
     __syncthreads();
 
-    // Sequential sweep by warp 0: 32 entries are prefetched per step and
-    // consumed in order through shuffles; lane 0 issues the stores.
+    // Deflation sweep by warp 0, 32 entries per batch.  The sweep's only carried
+    // state is the last survivor (index, d, z, support mask): entry i either
+    // deflates by type 1 (independent of the state), or is tested against the
+    // state and becomes the new survivor (after a rotation when the test holds).
+    // Each lane decides its entry against its predecessor's current final state
+    // and the batch repeats until no decision changes: since every decision
+    // depends only on the predecessor's, round k settles the first k candidates,
+    // so the fixpoint (reached in at most 32 rounds, typically 1-2) is exactly
+    // the sequential sweep, with the same arithmetic per decision.
     if (threadIdx.x < 32) {
+        const unsigned FULL = 0xffffffffu;
         const int lane = threadIdx.x;
+        const unsigned below = (1u << lane) - 1u;
         const double tau = s_tau;
         int j = -1, nrot = 0, mj = 0;
         double dj = 0.0, zj = 0.0;
         for (int base = 0; base < n; base += 32) {
-            int idx = base + lane;
-            double dl = (idx < n) ? ws.dsort[g0 + idx] : 0.0;
-            double zl = (idx < n) ? ws.zsort[g0 + idx] : 0.0;
-            int sl = (idx < n) ? ws.src[g0 + idx] : 0;
-            int cnt = min(32, n - base);
-            for (int e = 0; e < cnt; e++) {
-                double di = __shfl_sync(0xffffffffu, dl, e);
-                double zi = __shfl_sync(0xffffffffu, zl, e);
-                int mi = (__shfl_sync(0xffffffffu, sl, e) < n1) ? 1 : 2;
-                int i = base + e;
-                if (rho * fabs(zi) <= tau) {
-                    if (lane == 0) { ws.zsort[g0 + i] = 0.0; ws.keep[g0 + i] = 0; }
-                    continue;
-                }
-                if (j < 0) {
-                    if (lane == 0) ws.keep[g0 + i] = mi;
-                    j = i; dj = di; zj = zi; mj = mi;
-                    continue;
-                }
-                double t = di - dj;
-                double r = hypot(zi, zj);
-                double c = zi / r, s = zj / r;
-                if (fabs(t * c * s) <= tau) {
-                    double djn = c * c * dj + s * s * di;
-                    double din = s * s * dj + c * c * di;
-                    if (lane == 0) {
-                        ws.dsort[g0 + j] = djn;
-                        ws.zsort[g0 + j] = 0.0;
-                        ws.keep[g0 + j] = 0;
-                        ws.rot_j[g0 + nrot] = j;
-                        ws.rot_i[g0 + nrot] = i;
-                        ws.rot_c[g0 + nrot] = c;
-                        ws.rot_s[g0 + nrot] = s;
+            const int i = base + lane;
+            const bool valid = i < n;
+            const double d0 = valid ? ws.dsort[g0 + i] : 0.0;
+            const double z0 = valid ? ws.zsort[g0 + i] : 0.0;
+            const int m0 = valid ? ((ws.src[g0 + i] < n1) ? 1 : 2) : 0;
+            const bool type1 = valid && (rho * fabs(z0) <= tau);
+            const bool cand = valid && !type1;
+            const unsigned cmask = __ballot_sync(FULL, cand);
+            const unsigned pm = cmask & below;
+            const int pl = pm ? 31 - __clz(pm) : -1;   // predecessor lane; -1: carried survivor
+            const bool has_pred = pl >= 0 || j >= 0;
+            double fd = d0, fz = z0, c = 0.0, sn = 0.0, djn = 0.0;
+            int fm = m0;
+            bool rot = false;
+            for (int it = 0; it < 33; it++) {
+                double pd = __shfl_sync(FULL, fd, pl < 0 ? 0 : pl);
+                double pz = __shfl_sync(FULL, fz, pl < 0 ? 0 : pl);
+                int pmk = __shfl_sync(FULL, fm, pl < 0 ? 0 : pl);
+                if (pl < 0) { pd = dj; pz = zj; pmk = mj; }
+                bool nr = false;
+                double nd = d0, nz = z0, nc = 0.0, ns = 0.0, nj = 0.0;
+                int nm = m0;
+                if (cand && has_pred) {
+                    const double t = d0 - pd;
+                    const double r = hypot(z0, pz);
+                    const double cc = z0 / r, ss = pz / r;
+                    if (fabs(t * cc * ss) <= tau) {
+                        nr = true;
+                        nj = cc * cc * pd + ss * ss * d0;
+                        nd = ss * ss * pd + cc * cc * d0;
+                        nz = r;
+                        nm = m0 | pmk;
+                        nc = cc;
+                        ns = ss;
                     }
-                    nrot++;
-                    di = din;
-                    zi = r;
-                    mi |= mj;
                 }
-                if (lane == 0) {
-                    ws.keep[g0 + i] = mi;
-                    ws.dsort[g0 + i] = di;
-                    ws.zsort[g0 + i] = zi;
-                }
-                j = i; dj = di; zj = zi; mj = mi;
+                const bool changed = nr != rot || nd != fd || nz != fz || nm != fm;
+                rot = nr; fd = nd; fz = nz; fm = nm; c = nc; sn = ns; djn = nj;
+                if (!__any_sync(FULL, changed)) break;
             }
+            if (type1) { ws.zsort[g0 + i] = 0.0; ws.keep[g0 + i] = 0; }
+            if (cand) { ws.keep[g0 + i] = fm; ws.dsort[g0 + i] = fd; ws.zsort[g0 + i] = fz; }
+            __syncwarp();
+            const unsigned rmask = __ballot_sync(FULL, rot);
+            if (rot) {
+                // the predecessor deflates: rotated d, zero z; rotations keep sweep order
+                const int pj = pl >= 0 ? base + pl : j;
+                const int slot = nrot + __popc(rmask & below);
+                ws.dsort[g0 + pj] = djn;
+                ws.zsort[g0 + pj] = 0.0;
+                ws.keep[g0 + pj] = 0;
+                ws.rot_j[g0 + slot] = pj;
+                ws.rot_i[g0 + slot] = i;
+                ws.rot_c[g0 + slot] = c;
+                ws.rot_s[g0 + slot] = sn;
+            }
+            nrot += __popc(rmask);
+            if (cmask) {
+                const int L = 31 - __clz(cmask);
+                j = base + L;
+                dj = __shfl_sync(FULL, fd, L);
+                zj = __shfl_sync(FULL, fz, L);
+                mj = __shfl_sync(FULL, fm, L);
+            }
+            __syncwarp();
         }
         if (lane == 0) ws.nrot[blockIdx.x] = nrot;
     }

@@ -15,6 +15,7 @@ its own copy (independent replicas; no collective on the data path).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
   python bench.py --workload batched    # 4096 uneven matrices, one batched call per step
+  python bench.py --workload seed       # learned rank seed vs the rank estimate, N=32768
 """
 import argparse
 import json
@@ -42,7 +43,7 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="single", choices=["single", "batched"])
+    p.add_argument("--workload", default="single", choices=["single", "batched", "seed"])
     p.add_argument("--n", type=int, default=16384)
     p.add_argument("--matrix", default="toeplitz", choices=["toeplitz", "random"])
     p.add_argument("--mode", default="adc2", choices=["adc1", "adc2", "dense"])
@@ -71,6 +72,10 @@ def peaks():
 
 
 def workload_name(args):
+    if args.workload == "seed":
+        return ("random (a~U[-1,1], b~U[0.5,1], held-out seed 1001) N=32768 full "
+                "eigendecomposition, ADC2 update from K > 256, FP64 products: learned rank seed "
+                "vs the rank estimate")
     if args.workload == "batched":
         return ("4096 tridiagonals, N uniform on [64, 2048] (seed 3), even members U[-1,1], odd "
                 "members glued Wilkinson W21 (coupling 1e-8); %s update, %s products"
@@ -270,6 +275,9 @@ def main():
     if args.workload == "batched":
         return run_batched(args, torch, dist, world, rank, local, dev, stream, solver, flush,
                            tdeig, mode, prof)
+    if args.workload == "seed":
+        solver.close()
+        return run_seed(args, torch, dist, world, rank, local, dev, stream, flush, tdeig)
 
     a, b = matrix(args, rank)
     N = args.n
@@ -406,6 +414,79 @@ def run_batched(args, torch, dist, world, rank, local, dev, stream, solver, flus
     if rank == 0:
         print(json.dumps(out), flush=True)
     solver.close()
+    return 0
+
+
+def run_seed(args, torch, dist, world, rank, local, dev, stream, flush, tdeig):
+    """Learned sampling-rank seed against the rank estimate of eq. (bounds) on the
+    few-deflation random class at N = 32768 (deflation leaves K of a few hundred
+    per merge, so HSS runs from K > 256).  value: model-seeded solve time."""
+    from paper_1510_04591_gb300 import inputs, rank_model
+    N = 32768
+    a, b = inputs.uniform(N, 1001 + rank, lo_b=0.5, hi_b=1.0)
+    d_d = torch.from_numpy(a).to(dev)
+    e_d = torch.from_numpy(b).to(dev)
+    lam = torch.empty(N, dtype=torch.float64, device=dev)
+    Qt = torch.empty((N, N), dtype=torch.float64, device=dev)
+    solver = tdeig.Solver(stream=stream.cuda_stream, hss_threshold=256)
+    solver.set_rank_model(*rank_model.load())
+    base = tdeig.mode_code("adc2", "fp64")
+    res = {}
+    ck = None
+    for name, fl in (("estimate", 0), ("model", tdeig.FLAG_MLP_SEED)):
+        m = base | fl
+        for _ in range(args.warmup):
+            solver.solve_raw(d_d.data_ptr(), e_d.data_ptr(), N, lam.data_ptr(), Qt.data_ptr(), m)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        clocks = Clocks(local)
+        clocks.start()
+        ms = []
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush_l2(flush)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = solver.solve_raw(d_d.data_ptr(), e_d.data_ptr(), N, lam.data_ptr(),
+                                  Qt.data_ptr(), m)
+            e1.record(stream)
+            e1.synchronize()
+            if st != 0:
+                raise tdeig.TdeigError(st, "tdeig_solve")
+            ms.append(e0.elapsed_time(e1))
+        c = clocks.stop()
+        ck = ck or c
+        stt = json.loads(solver.stats())
+        hm = [h for h in stt.get("hss", []) if "K" in h]
+        res[name] = {"value": float(np.mean(ms)) / 1e3, "unit": "s",
+                     "accuracy": accuracy(a, b, lam, Qt, dev),
+                     "hss_merges": len(hm),
+                     "sampled_columns_sum_K_s": int(sum(h["K"] * h["s"] for h in hm)),
+                     "mean_sample_size": float(np.mean([h["s"] for h in hm])) if hm else 0.0,
+                     "ids_at_sample_size": int(sum(h["kmax"] >= h["s"] for h in hm)),
+                     "fallbacks": stt.get("mlp_fallbacks", 0),
+                     "stage_ms": {k: round(v, 3) for k, v in stt.get("stage_ms", {}).items()}}
+    solver.close()
+    v = res["model"]["value"]
+    t_max = torch.tensor([v], device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    out = {"metric": "learned rank seed: ADC2 eigendecomposition time, N=32768 random",
+           "value": float(t_max.item()), "unit": "s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": float(t_max.item()) * 1e3,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": workload_name(args), "n": N, "hss_threshold": 256,
+                      "hss_leaf": 128, "oversample": 10,
+                      "l2": "flushed between timed steps (256 MiB write outside the events)"},
+           "clocks": ck, "estimate": res["estimate"], "model": res["model"],
+           "speedup_vs_estimate": res["estimate"]["value"] / res["model"]["value"]}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
     return 0
 
 

@@ -46,7 +46,16 @@ enum {
     TDEIG_MODE_ADC2 = 2,
     TDEIG_MODE_MASK = 0xff,
     TDEIG_PREC_FP64 = 0 << 8,     /* FP64 products */
-    TDEIG_PREC_SPLIT = 1 << 8,    /* split-precision tensor-core products */
+    /* Split-precision tensor-core products (tcgen05, FP32 accumulation): the
+     * dense update and Algorithm 3 from six 7-bit BF16 digit slices per operand
+     * (about 42 bits), ADC2 sampling from eight (56 bits). */
+    TDEIG_PREC_SPLIT = 1 << 8,
+    /* Two BF16 slices (hi + lo, 16 bits) for the update and Algorithm 3;
+     * sampling in FP64.  A precision-study variant: orthogonality ~1e-5. */
+    TDEIG_PREC_BF16X2 = 2 << 8,
+    /* Two FP16 slices (hi + lo, 22 bits; FP32 accumulation rounds); sampling in
+     * FP64.  A precision-study variant. */
+    TDEIG_PREC_FP16X2 = 3 << 8,
     TDEIG_PREC_MASK = 0xf << 8,
     /* DENSE | FP64 with device buffers only: capture the whole launch sequence
      * (every level of every matrix) in a CUDA graph on the first call and

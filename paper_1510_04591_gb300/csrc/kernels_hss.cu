@@ -751,15 +751,17 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
                      HssLearn* learn)
 {
     int prc = TDEIG_OK;
+    const int split_kind = prec == TDEIG_PREC_BF16X2 ? SPLIT_BF16X2
+                           : prec == TDEIG_PREC_FP16X2 ? SPLIT_FP16X2 : SPLIT_OZAKI;
     auto run = [&](const std::vector<GemmDesc>& gv, GemmDesc* dev) -> double {
         if (!split) return hss_launch_gemm(gv, dev, st);
         int r = TDEIG_OK;
-        double f = split_launch_gemm(gv, *split, st, &r);
+        double f = split_launch_gemm(gv, *split, st, &r, status, split_kind, TD_SPLIT_BITS);
         if (r && !prc) prc = r;
         return f;
     };
     double fl_dense = 0.0, fl_sample = 0.0, fl_build = 0.0, fl_mult = 0.0;
-    (void)prec; (void)dev_merges; (void)status;
+    (void)dev_merges;
     const int p_over = opt.oversample;
     std::vector<HMerge> H;
     std::vector<GemmDesc> dense;   // merges of this level that stay dense
@@ -1014,10 +1016,17 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
         g.transA = 1; g.C = h.Z;
         gl.push_back(g);
     }
-    // Sampling stays FP64 in every precision mode: Phi = Y - D Omega cancels the
-    // dominant near-diagonal part of Y exactly, so slice errors in Y would be
-    // amplified relative to Phi and inflate the ID ranks.
-    fl_sample += hss_launch_gemm(gl, dgemm, st);
+    // Phi = Y - D Omega cancels the dominant near-diagonal part of Y, so slice
+    // errors in Y are amplified relative to Phi: split sampling keeps 56 bits
+    // (as accurate as an FP64 product of this length); the two-slice variants
+    // sample in FP64.
+    if (split && prec == TDEIG_PREC_SPLIT) {
+        int r = TDEIG_OK;
+        fl_sample += split_launch_gemm(gl, *split, st, &r, status, SPLIT_OZAKI, TD_SAMPLE_BITS);
+        if (r) return r;
+    } else {
+        fl_sample += hss_launch_gemm(gl, dgemm, st);
+    }
 
     if (!adc1 && (rc = mark("hss_build"))) return rc;
     // ---- Algorithm 2, levels L..1 -------------------------------------------

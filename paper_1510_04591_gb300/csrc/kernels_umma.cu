@@ -1,0 +1,357 @@
+// Split-precision FP64 products on the fifth-generation tensor cores (tcgen05).
+//
+// Operands come as BF16 slices (kernels_split.cu): row i of op(A) is
+// 2^(e_i - beta) sum_p S_p[i, :] with S_p = t_p 2^(-beta p) and t_p a signed
+// beta-bit integer digit, likewise the columns of op(B) (BF16 or FP16 slices).
+// A slice-pair product S_p S_q^T is then an integer sum scaled by
+// 2^(-beta (p+q)).  One CTA computes a 128 x 64 output tile:
+//   * every k-block of 16 brings all s slices of both operands into shared
+//     memory (cp.async, canonical K-major core-matrix layout without swizzle)
+//     through a 2- or 3-stage ring;
+//   * one thread issues tcgen05.mma (M 128, N 64, K 16, 16-bit in, FP32 out) for
+//     every pair p + q <= s - 1 into one of five TMEM accumulators: levels
+//     p+q = 0..3 each stay exact over a k-chunk of the problem's `chunk`
+//     (e.g. 4 pairs x 127^2 x 256 < 2^24 for 7-bit digits), levels >= 4 share
+//     the fifth (their FP32 rounding is 2^-52 of the leading term);
+//   * after every k-chunk the accumulators are read back with
+//     tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e. tile rows) and
+//     summed into a per-thread double-float (FP32 hi + lo) row of 64 values;
+//   * the epilogue writes alpha 2^(e_i + f_j - 2 beta)(hi + lo) + betac C in FP64.
+// TMEM (512 columns) is allocated after the first loads are issued and freed
+// right after the last drain, so a second resident CTA loads while this one
+// computes, and computes while this one writes its tile.
+// MMA completion is tracked with one mbarrier per stage (tcgen05.commit); every
+// wait is bounded (about one second of SM clock), after which the kernel sets
+// TD_STATUS_TIMEOUT, waits for its own copies, frees its TMEM and returns.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "split.cuh"
+
+#define UM_NT 128
+#define UM_LBO 128                       // bytes between core matrices adjacent in K
+#define UM_SBO (UM_BK / 8 * 128)         // bytes between core matrices adjacent in M / N
+#define UM_KCH (UM_BK / 8)               // 16-byte chunks per row and k-block
+#define UM_ASLICE (UM_BM * UM_BK * 2)    // one A slice of one stage: 8 KiB
+#define UM_BSLICE (UM_BN * UM_BK * 2)    // one B slice of one stage: 4 KiB
+#define UM_NACC 5                        // accumulators: levels 0, 1, 2, 3 and >= 4
+#define UM_TMEM_COLS 512                 // 5 x 64 FP32 columns, rounded up to a power of two
+#define UM_WAIT_CYCLES (1LL << 31)       // bounded waits: ~1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void um_cp16(uint32_t dst, const void* src, bool valid)
+{
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(n)
+                 : "memory");
+}
+
+// Shared-memory matrix descriptor: start address, leading (K) and stride (M/N)
+// byte offsets, fixed version bits 0b001 at bit 46, no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(UM_LBO >> 4) << 16;
+    d |= (uint64_t)(UM_SBO >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and B
+// both BF16 (bits 7-9 and 10-12 = 1) or both FP16 (0), both K-major, N >> 3 at
+// bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t umma_idesc(int M, int N, int f16)
+{
+    return (1u << 4) | ((f16 ? 0u : 1u) << 7) | ((f16 ? 0u : 1u) << 10) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_f16kind(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before()
+{
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after()
+{
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity))
+        if (clock64() - t0 > UM_WAIT_CYCLES) return false;
+    return true;
+}
+
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes (one row per thread).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// f 2^k as an FP64 value, built from f's bits with integer operations (FP64
+// instructions issue at 1/64 of the FP32 rate on this part).  Exact; float
+// subnormals (|f| < 2^-126, far below the rounding of the sum) become 0.
+__device__ __forceinline__ double f2d_scaled(float f, int k)
+{
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xFFu;
+    const uint64_t bits = ((uint64_t)(b >> 31) << 63) | ((uint64_t)(e + (1023 - 127) + k) << 52) |
+                          ((uint64_t)(b & 0x7FFFFFu) << 29);
+    return e ? __longlong_as_double((long long)bits) : 0.0;
+}
+
+extern __shared__ __align__(1024) unsigned char um_smem[];
+
+__global__ void __launch_bounds__(UM_NT, 2)
+    k_split_umma(const SplitGemmDesc* G, int ng, int smax, int nst, int* status)
+{
+    __shared__ __align__(8) uint64_t bar[3];
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int lo = 0, hi = ng - 1;
+    const int bid = blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (G[mid].tile0 <= bid) lo = mid; else hi = mid - 1;
+    }
+    const SplitGemmDesc& g = G[lo];
+    const int M = g.M, N = g.N, Kp = g.Kp, s = g.s;
+    const int local = bid - g.tile0;
+    const int tm = local % g.tiles_m, tn = local / g.tiles_m;
+    const int row0 = tm * UM_BM, col0 = tn * UM_BN;
+    if (row0 >= M || col0 >= N) return;   // whole CTA, before any allocation
+    int kb0 = 0, kb1 = Kp;
+    if (g.rsplit > 0) {
+        if (row0 >= g.rsplit) kb0 = (g.kbot_beg / UM_BK) * UM_BK;
+        if (row0 + UM_BM <= g.rsplit) kb1 = min(Kp, ((g.ktop_end + UM_BK - 1) / UM_BK) * UM_BK);
+    }
+    const int nkb = kb1 > kb0 ? (kb1 - kb0) / UM_BK : 0;
+    const uint32_t stage_bytes = (uint32_t)smax * (UM_ASLICE + UM_BSLICE);
+    const uint32_t sbase = smem_u32(um_smem);
+
+    if (tid == 0) {
+        for (int i = 0; i < 3; i++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bar[i])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+
+    auto load = [&](int stg, int k0) {
+        const uint32_t sa = sbase + (uint32_t)stg * stage_bytes;
+        const uint32_t sb = sa + (uint32_t)smax * UM_ASLICE;
+        for (int p = 0; p < s; p++) {
+            const __nv_bfloat16* Ap = g.SA + (size_t)p * M * Kp;
+            const __nv_bfloat16* Bp = g.SB + (size_t)p * N * Kp;
+#pragma unroll
+            for (int i = 0; i < UM_BM * UM_KCH / UM_NT; i++) {   // A: 128 rows x UM_KCH chunks
+                const int ch = tid + UM_NT * i;
+                const int r = ch / UM_KCH, c = ch % UM_KCH;
+                const int gr = row0 + r;
+                const bool v = gr < M;
+                um_cp16(sa + p * UM_ASLICE + (r >> 3) * UM_SBO + c * UM_LBO + (r & 7) * 16,
+                        Ap + (size_t)(v ? gr : 0) * Kp + k0 + c * 8, v);
+            }
+#pragma unroll
+            for (int i = 0; i < UM_BN * UM_KCH / UM_NT; i++) {   // B: 64 rows x UM_KCH chunks
+                const int ch = tid + UM_NT * i;
+                const int r = ch / UM_KCH, c = ch % UM_KCH;
+                const int gc = col0 + r;
+                const bool v = gc < N;
+                um_cp16(sb + p * UM_BSLICE + (r >> 3) * UM_SBO + c * UM_LBO + (r & 7) * 16,
+                        Bp + (size_t)(v ? gc : 0) * Kp + k0 + c * 8, v);
+            }
+        }
+    };
+
+    float hs[UM_BN], ls[UM_BN];
+#pragma unroll
+    for (int c = 0; c < UM_BN; c++) { hs[c] = 0.0f; ls[c] = 0.0f; }
+    for (int i = 0; i < nst - 1; i++) {
+        if (i < nkb) load(i, kb0 + i * UM_BK);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        // blocks while the other resident CTA holds the columns
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(&tmem_slot)),
+                     "r"(UM_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    bool held = true;
+    const uint32_t idesc = umma_idesc(UM_BM, UM_BN, g.f16);
+    const int chunk = g.chunk;
+    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+    unsigned started = 0;
+    int kchunk = 0;
+    bool fail = false;
+    for (int it = 0; it < nkb; it++) {
+        const int stg = it % nst;
+        if (nst == 3) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = sbase + (uint32_t)stg * stage_bytes;
+            const uint32_t b0 = a0 + (uint32_t)smax * UM_ASLICE;
+            for (int kk = 0; kk < UM_BK / 16; kk++)
+                for (int p = 0; p < s; p++)
+                    for (int q = 0; p + q < s; q++) {
+                        const int L = min(p + q, UM_NACC - 1);
+                        umma_f16kind(tmem + L * UM_BN,
+                                  umma_desc(a0 + p * UM_ASLICE + kk * 2 * UM_LBO),
+                                  umma_desc(b0 + q * UM_BSLICE + kk * 2 * UM_LBO), idesc,
+                                  (started >> L) & 1u);
+                        started |= 1u << L;
+                    }
+            umma_commit(smem_u32(&bar[stg]));
+        }
+        const int nxt = it + nst - 1;
+        bool ok = true;
+        if (nxt < nkb && it >= 1) {
+            // the ring slot of stage nxt was read by the MMAs of iteration it - 1
+            const int pv = it - 1;
+            ok = mbar_wait(smem_u32(&bar[pv % nst]), (uint32_t)((pv / nst) & 1));
+        }
+        if (__syncthreads_or(!ok)) { fail = true; break; }
+        if (nxt < nkb) load(nxt % nst, kb0 + nxt * UM_BK);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        kchunk += UM_BK;
+        if (kchunk >= chunk || it == nkb - 1) {
+            ok = mbar_wait(smem_u32(&bar[stg]), (uint32_t)((it / nst) & 1));
+            if (__syncthreads_or(!ok)) { fail = true; break; }
+            tc_fence_after();
+#pragma unroll
+            for (int L = 0; L < UM_NACC; L++)
+#pragma unroll
+                for (int cg = 0; cg < UM_BN / 16; cg++) {
+                    if (L >= s) continue;   // level L exists only for s > L
+                    float v[16];
+                    tmem_ld16(trow + L * UM_BN + cg * 16, v);
+#pragma unroll
+                    for (int c = 0; c < 16; c++) {
+                        // double-float accumulation (two-sum)
+                        const float h = hs[cg * 16 + c], x = v[c];
+                        const float sm = h + x;
+                        const float bb = sm - h;
+                        ls[cg * 16 + c] += (h - (sm - bb)) + (x - bb);
+                        hs[cg * 16 + c] = sm;
+                    }
+                }
+            tc_fence_before();
+            __syncthreads();   // TMEM read before the next chunk overwrites it
+            started = 0;
+            kchunk = 0;
+            if (it == nkb - 1 && warp == 0) {
+                asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                             "r"(UM_TMEM_COLS)
+                             : "memory");
+            }
+            if (it == nkb - 1) held = false;
+        }
+    }
+
+    if (!fail) {
+        const int row = row0 + 32 * warp + lane;
+        if (row < M) {
+            const int er = g.ea[row] - 2 * g.beta;
+            const double alpha = g.alpha, betac = g.betac;
+#pragma unroll
+            for (int c = 0; c < UM_BN; c++) {
+                const int col = col0 + c;
+                if (col < N) {
+                    const int k = er + g.eb[col];
+                    double v = f2d_scaled(hs[c], k) + f2d_scaled(ls[c], k);
+                    if (alpha != 1.0) v *= alpha;
+                    double* out = g.C + (size_t)(g.ccol ? g.ccol[col] : col) * g.ldc + row;
+                    *out = betac != 0.0 ? fma(betac, *out, v) : v;
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicOr(status, TD_STATUS_TIMEOUT);
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    if (held) {   // no k-block, or a bounded wait expired
+        tc_fence_before();
+        __syncthreads();
+        if (warp == 0)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                         "r"(UM_TMEM_COLS)
+                         : "memory");
+    }
+}
+
+size_t umma_smem_bytes(int smax, int* nstages)
+{
+    const size_t stage = (size_t)smax * (UM_ASLICE + UM_BSLICE);
+    const int n = (3 * stage <= 220 * 1024) ? 3 : 2;
+    if (nstages) *nstages = n;
+    return n * stage + 1024;   // + alignment slack of the dynamic base
+}
+
+void umma_launch(const SplitGemmDesc* dev, int ng, int tiles, int smax, int* status,
+                 cudaStream_t st)
+{
+    if (tiles <= 0) return;
+    int nst = 0;
+    const size_t smem = umma_smem_bytes(smax, &nst);
+    static size_t attr = 0;
+    if (smem > attr) {
+        cudaFuncSetAttribute(k_split_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = smem;
+    }
+    td_prof_begin(st);
+    k_split_umma<<<tiles, UM_NT, smem, st>>>(dev, ng, smax, nst, status);
+    td_prof_end(st, "k_split_umma");
+}

@@ -1,33 +1,84 @@
 // Split-precision products on the tensor cores (internal interface).
 //
-// C = alpha op(A) op(B) + beta C for FP64 operands, computed from BF16 slices:
-// every row i of op(A) is scaled by 2^-e_i (e_i the exponent bound of the row)
-// and cut into s signed beta-bit integer digits t_p (|t_p| < 2^beta), so that
-//   op(A)[i, k] ~= 2^e_i sum_p t_p[i, k] 2^(-beta (p+1))
-// (likewise the columns of op(B) with 2^f_j).  beta is the largest value with
-// (2^beta - 1)^2 K <= 2^24, so each slice-pair product sum_k t_p t_q is an
-// integer that FP32 accumulation on the tensor cores represents exactly.  Pairs
-// with p + q <= s - 1 are accumulated per output entry in a double-float (FP32
-// hi + lo) sum, converted to FP64 and scaled by 2^(e_i + f_j) at the end.
-// Dropped pairs and truncated digits bound the error by about
-// 2^(e_i + f_j) K 2^(-beta s) per entry.
+// C = alpha op(A) op(B) + beta C for FP64 operands, computed from 16-bit
+// slices: every row i of op(A) is scaled by 2^-e_i (e_i its exponent bound)
+// and cut into s signed beta-bit integer digits t_p, stored as t_p 2^(-beta p)
+// (exact in BF16 for beta <= 8, in FP16 for beta <= 11), so that
+//   op(A)[i, k] ~= 2^(e_i - beta) sum_p S_p[i, k]
+// (likewise the columns of op(B) with 2^f_j).  A slice-pair product S_p S_q^T
+// is an integer sum scaled by 2^(-beta (p + q)); pairs with p + q <= s - 1
+// are accumulated on the tensor cores in FP32, one accumulator per level
+// p + q in {0, 1, 2, 3} (exact while the level's integer sum stays below 2^24,
+// which bounds the k-range, `chunk`, summed before a drain) and one for the
+// levels >= 4, drained into a double-float (FP32 hi + lo) sum, converted to
+// FP64 and scaled by 2^(e_i + f_j - 2 beta).  Dropped pairs and truncated
+// digits bound the error by about 2^(e_i + f_j) K 2^(-beta s) per entry.
+// Kinds: SPLIT_OZAKI (beta 7, s = ceil(bits / 7)), SPLIT_BF16X2 (beta 8, s 2:
+// a hi + lo pair), SPLIT_FP16X2 (FP16 slices, beta 11, s 2; its FP32
+// accumulation is not exact).
 #pragma once
+
+#include <cuda_bf16.h>
 
 #include <vector>
 
 #include "hss.cuh"
+
+// element (r, k) of the operand being sliced: X[r*sr + col(k)*sk], col(k) = gk ? gk[k] : k
+struct SliceDesc {
+    const double* X;
+    const int* gk;
+    long long sr, sk;
+    int rows, K, Kp, s, beta;
+    int f16;            // slices are FP16 (else BF16)
+    __nv_bfloat16* S;   // slice p, row r at S + (p * rows + r) * Kp (16-bit values)
+    int* e;             // exponent bound per row: max |row| < 2^e
+};
+
+// One slice-pair product C = alpha 2^(ea+eb) sum_{p+q<=s-1} ... + betac C.
+struct SplitGemmDesc {
+    const __nv_bfloat16* SA;   // s slices of op(A), M x Kp each
+    const __nv_bfloat16* SB;   // s slices of op(B)^T, N x Kp each
+    const int* ea;
+    const int* eb;
+    int M, N, Kp, s, beta;
+    double* C;
+    int ldc;
+    const int* ccol;
+    double alpha, betac;
+    int rsplit, ktop_end, kbot_beg;   // block-structured update: k ranges of the row halves
+    int chunk, f16;                   // k-range summed exactly before a drain; FP16 slices
+    int tile0, tiles_m;
+};
+
+// Tensor-core (tcgen05) slice-pair products: tile 128 x 64 per CTA, five TMEM
+// accumulators (levels p+q = 0, 1, 2, 3 and >= 4).
+#define UM_BM 128
+#define UM_BN 64
+#define UM_BK 16
+
+enum { SPLIT_OZAKI = 0, SPLIT_BF16X2 = 1, SPLIT_FP16X2 = 2 };
+struct SplitPrec {
+    int beta, s, chunk, f16;
+};
+SplitPrec split_prec(int kind, int bits);
+void umma_launch(const SplitGemmDesc* dev, int ng, int tiles, int smax, int* status,
+                 cudaStream_t st);
+size_t umma_smem_bytes(int smax, int* nstages);
 
 struct SplitWS {
     char* base = nullptr;
     size_t cap = 0;
 };
 
-// Number of significant bits the slices keep (beta * s >= this).
+// Significant bits the slices keep (beta * s >= this): products feeding the
+// eigenvectors, and the sampling products of ADC2 (Phi = Y - D Omega cancels).
 #define TD_SPLIT_BITS 40
+#define TD_SAMPLE_BITS 56
 
-double split_launch_gemm(const std::vector<GemmDesc>& g, SplitWS& ws, cudaStream_t st, int* rc);
+// status: device word that receives TD_STATUS_TIMEOUT when a bounded wait expires.
+double split_launch_gemm(const std::vector<GemmDesc>& g, SplitWS& ws, cudaStream_t st, int* rc,
+                         int* status, int kind, int bits);
 // Tensor-core work issued by split products so far: 2 M N K per slice pair.
 extern double g_split_tensor_flops;
 void split_free(SplitWS& ws);
-// beta and s used for a contraction of length K.
-void split_params(int K, int* beta, int* s);

@@ -455,7 +455,9 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
                   TDEIG_FLAG_RECORD | TDEIG_FLAG_MLP_SEED)))
         return TDEIG_EINVAL;
     if ((mode & TDEIG_FLAG_MLP_SEED) && !h->mlp) return TDEIG_EINVAL;
-    if (prec != TDEIG_PREC_FP64 && prec != TDEIG_PREC_SPLIT) return TDEIG_EINVAL;
+    if (prec != TDEIG_PREC_FP64 && prec != TDEIG_PREC_SPLIT && prec != TDEIG_PREC_BF16X2 &&
+        prec != TDEIG_PREC_FP16X2)
+        return TDEIG_EINVAL;
     auto t_start = std::chrono::steady_clock::now();
     const long long launches0 = g_td_launches;
     const double split_flops0 = g_split_tensor_flops;
@@ -667,7 +669,7 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
         MARK("secular", lv);
         td_launch_secular(Md, nm, L.rows, lws, status, st);
         bool any_hss = false;
-        const bool split = (prec == TDEIG_PREC_SPLIT);
+        const bool split = (prec != TDEIG_PREC_FP64);
         std::vector<int> Kh, Gh;
         const bool hss_level = variant != TDEIG_MODE_DENSE && L.nmax > h->opt.hss_threshold;
         if (hss_level || split) {
@@ -706,7 +708,10 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
                 g.rsplit = m.n1; g.ktop_end = Gh[2 * i] + Gh[2 * i + 1]; g.kbot_beg = Gh[2 * i];
                 gd.push_back(g);
             }
-            split_launch_gemm(gd, h->split, st, &rc);
+            split_launch_gemm(gd, h->split, st, &rc, status,
+                              prec == TDEIG_PREC_BF16X2 ? SPLIT_BF16X2
+                              : prec == TDEIG_PREC_FP16X2 ? SPLIT_FP16X2 : SPLIT_OZAKI,
+                              TD_SPLIT_BITS);
             if (rc) return rc;
         } else {
             // Autotuner: the first solve of a level class times every tile shape

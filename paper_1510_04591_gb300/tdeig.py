@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtdeig.so")
 
 MODE_DENSE, MODE_ADC1, MODE_ADC2 = 0, 1, 2
-PREC_FP64, PREC_SPLIT = 0 << 8, 1 << 8
+PREC_FP64, PREC_SPLIT, PREC_BF16X2, PREC_FP16X2 = 0 << 8, 1 << 8, 2 << 8, 3 << 8
 FLAG_GRAPH = 1 << 12
 FLAG_PROFILE = 1 << 13
 FLAG_RECORD = 1 << 14
@@ -25,7 +25,7 @@ FLAG_MLP_SEED = 1 << 15
 MLP_IN, MLP_HIDDEN = 7, 64
 MLP_PARAMS = MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN + 1
 _MODES = {"dense": MODE_DENSE, "adc1": MODE_ADC1, "adc2": MODE_ADC2}
-_PRECS = {"fp64": PREC_FP64, "split": PREC_SPLIT}
+_PRECS = {"fp64": PREC_FP64, "split": PREC_SPLIT, "bf16x2": PREC_BF16X2, "fp16x2": PREC_FP16X2}
 
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ETIMEOUT, ENOTIMPL = 0, -1, -2, -3, -4, -5, -6
 

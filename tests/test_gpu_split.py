@@ -75,3 +75,27 @@ def test_split_matches_fp64_products_closely():
     assert np.max(np.abs(lam64 - lam32)) <= 1e-10 * 4
     sg = np.sign(np.sum(Q64 * Q32, axis=0))
     assert np.max(np.abs(Q64 - Q32 * sg)) <= 1e-7
+
+
+@pytest.mark.parametrize("gen", ["toeplitz", "uniform"])
+def test_two_slice_variants(gen):
+    """Precision study variants: BF16 hi + lo (16 bits) and FP16 hi + lo (22 bits,
+    FP32 accumulation rounds).  Their error is set by the slice precision:
+    orthogonality about N^(1/2) 2^-16 and 2^-22 respectively, against 2^-42 for
+    the six-slice products; eigenvalues stay FP64-accurate to 1e-6."""
+    N = 1024
+    a, b = inputs.toeplitz(N) if gen == "toeplitz" else inputs.uniform(N, 5)
+    lam_d, _ = dc.solve(a, b)
+    res = {}
+    with solver() as s:
+        for prec in ("split", "fp16x2", "bf16x2"):
+            lam, Q = gpu(s, a, b, "dense", prec)
+            assert np.all(np.isfinite(lam)) and np.all(np.isfinite(Q))
+            res[prec] = (metrics.orthogonality(Q), metrics.residual(a, b, lam, Q),
+                         metrics.eig_error(lam, lam_d))
+    print(gen, res)
+    assert res["split"][0] <= 1e-10
+    assert res["fp16x2"][0] <= 1e-5 and res["bf16x2"][0] <= 1e-3
+    assert res["split"][0] < res["fp16x2"][0] < res["bf16x2"][0]
+    for prec in ("fp16x2", "bf16x2"):
+        assert res[prec][2] <= 1e-3

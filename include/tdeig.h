@@ -163,6 +163,19 @@ int tdeig_lowner_cauchy(tdeig_handle h, int64_t K, const double* d, const double
                         const double* mu, const double* z, double rho,
                         double* uhat, double* v, double* Qhat);
 
+/* Split-precision product (the products of TDEIG_PREC_SPLIT / _BF16X2 /
+ * _FP16X2 in isolation, not in the paper): C = op(A) op(B) with op(A) M x K,
+ * op(B) K x N; A, B, C column-major FP64 with leading dimensions lda, ldb, ldc
+ * (host or device); transA / transB select the transposes.  prec is one of
+ * TDEIG_PREC_SPLIT, _BF16X2, _FP16X2; bits (SPLIT only, 8..56) is the number
+ * of significant bits kept per operand row / column (the solver uses 40 for
+ * the eigenvector products and 56 for ADC2 sampling).  C is overwritten.
+ * TDEIG_EINVAL on bad sizes or arguments, TDEIG_ETIMEOUT if a bounded device
+ * wait expired. */
+int tdeig_split_gemm(tdeig_handle h, int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
+                     int transA, const double* B, int64_t ldb, int transB, double* C, int64_t ldc,
+                     int prec, int bits);
+
 /* ---------------------------------------------------------------------- */
 /* Learned rank seed for ADC2 (not in the paper; it replaces the rank       */
 /* estimate of eq. (bounds) as the first guess of the sampling rank r,      */

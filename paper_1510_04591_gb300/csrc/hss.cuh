@@ -32,6 +32,9 @@ struct GemmDesc {
     // optional block structure (split products only): rows < rsplit use k < ktop_end,
     // rows >= rsplit use k >= kbot_beg (the other entries of op(A) are zero); 0 = none
     int rsplit, ktop_end, kbot_beg;
+    // optional (split products only): entry (r, k) of op(A) is taken as zero when
+    // amask[r] == amask[k] (ADC2 sampling of the off-diagonal part of Qhat)
+    const int* amask;
 };
 
 // out[a + b ld] = uhat[row] v[col] / (d[row] - lambda[col]) (Remark 1), for

@@ -581,6 +581,7 @@ struct HMerge {
     std::vector<int> bounds;
     std::vector<HNode> nodes;
     double *Om = nullptr, *Y = nullptr, *Z = nullptr;
+    int* leaf_of = nullptr;   // HSS leaf of every row (masked split sampling)
     std::vector<double*> G, F;      // per level 1..L: n x 2^l s, ld n
     const double *d, *gam, *mu, *uh, *v, *qhat;
     const int *surv, *posNew;
@@ -915,7 +916,7 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
         for (int q = 0; q < (1 << h.L); q++) mc = std::max(mc, h.bounds[q + 1] - h.bounds[q]);
         h.mcap = mc;
         const size_t s = h.s, nl = (size_t)1 << h.L, K = h.K, n = h.n, two_s = 2 * s;
-        total += 3 * K * s * 8;                                // Om, Y, Z
+        total += 3 * K * s * 8 + K * 4 + 256;                  // Om, Y, Z, leaf_of
         total += nl * (2 * mc * s + (size_t)mc * mc) * 8;       // leaves U, V, D
         total += 2 * nl * (4 * two_s * s) * 8;                 // parents Phi, Theta, U, V, Ystk, Zstk
         total += 2 * nl * (s * s) * 8;                         // B
@@ -948,6 +949,7 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
         h.Om = B.take<double>((size_t)K * s);
         h.Y = B.take<double>((size_t)K * s);
         h.Z = B.take<double>((size_t)K * s);
+        h.leaf_of = B.take<int>((size_t)K);
         h.nodes.assign((size_t)2 << h.L, HNode());
         for (int l = 1; l <= h.L; l++) {
             for (int q = 0; q < (1 << l); q++) {
@@ -1000,6 +1002,22 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
 
     if (!adc1 && (rc = mark("hss_sample"))) return rc;
     // ---- sampling: Omega, Y = A Omega, Z = A^T Omega (Omega(1) = Omega(2)) --
+    // Split sampling multiplies the off-diagonal part of Qhat (the leaf blocks
+    // masked to zero), which is Phi / Theta of the leaves directly.  A split
+    // product of the whole Qhat carries errors relative to the row and column
+    // maxima (the large near-diagonal entries), far above the small
+    // off-diagonal entries that Phi = Y - D Omega keeps after the cancellation.
+    const bool masked = split && prec == TDEIG_PREC_SPLIT && !adc1;
+    std::vector<std::vector<int>> leaf_ids;
+    if (masked) {
+        for (auto& h : H) {
+            leaf_ids.emplace_back(h.K);
+            std::vector<int>& v = leaf_ids.back();
+            for (int q = 0; q < (1 << h.L); q++)
+                for (int i = h.bounds[q]; i < h.bounds[q + 1]; i++) v[i] = q;
+            HCU(cudaMemcpyAsync(h.leaf_of, v.data(), h.K * sizeof(int), cudaMemcpyHostToDevice, st));
+        }
+    }
     std::vector<GemmDesc> gl;
     for (auto& h : H) {
         if (adc1) break;
@@ -1012,15 +1030,14 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
         memset(&g, 0, sizeof(g));
         g.A = h.qhat; g.lda = h.K; g.B = h.Om; g.ldb = h.K; g.C = h.Y; g.ldc = h.K;
         g.M = h.K; g.N = h.s; g.Kd = h.K; g.alpha = 1.0;
+        g.amask = masked ? h.leaf_of : nullptr;
         gl.push_back(g);
         g.transA = 1; g.C = h.Z;
         gl.push_back(g);
     }
-    // Phi = Y - D Omega cancels the dominant near-diagonal part of Y, so slice
-    // errors in Y are amplified relative to Phi: split sampling keeps 56 bits
-    // (as accurate as an FP64 product of this length); the two-slice variants
-    // sample in FP64.
-    if (split && prec == TDEIG_PREC_SPLIT) {
+    // Split sampling keeps 56 bits (products as accurate as FP64 ones); the
+    // two-slice variants sample in FP64.
+    if (masked) {
         int r = TDEIG_OK;
         fl_sample += split_launch_gemm(gl, *split, st, &r, status, SPLIT_OZAKI, TD_SAMPLE_BITS);
         if (r) return r;
@@ -1047,14 +1064,16 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
                     f.out = nd.D; f.ld = h.mcap; f.nr = m; f.nc = m; f.r0 = nd.r0; f.c0 = nd.r0;
                     f.d = h.d; f.gam = h.gam; f.mu = h.mu; f.uhat = h.uh; f.v = h.v;
                     fills.push_back(f);
-                    GemmDesc g;
-                    memset(&g, 0, sizeof(g));
-                    g.A = nd.D; g.lda = h.mcap; g.B = h.Om + nd.r0; g.ldb = h.K;
-                    g.C = nd.Phi; g.ldc = h.K; g.M = m; g.N = s; g.Kd = m;
-                    g.alpha = -1.0; g.beta = 1.0;
-                    upd.push_back(g);            // Phi_i = Y_i - D_i Omega_i
-                    g.transA = 1; g.C = nd.Theta;
-                    upd.push_back(g);            // Theta_i = Z_i - D_i^T Omega_i
+                    if (!masked) {   // masked sampling produced Phi_i, Theta_i directly
+                        GemmDesc g;
+                        memset(&g, 0, sizeof(g));
+                        g.A = nd.D; g.lda = h.mcap; g.B = h.Om + nd.r0; g.ldb = h.K;
+                        g.C = nd.Phi; g.ldc = h.K; g.M = m; g.N = s; g.Kd = m;
+                        g.alpha = -1.0; g.beta = 1.0;
+                        upd.push_back(g);            // Phi_i = Y_i - D_i Omega_i
+                        g.transA = 1; g.C = nd.Theta;
+                        upd.push_back(g);            // Theta_i = Z_i - D_i^T Omega_i
+                    }
                     IdDesc a;
                     memset(&a, 0, sizeof(a));
                     a.Phi = nd.Phi; a.ldphi = h.K; a.m = m; a.s = s; a.rowbase = nd.r0;

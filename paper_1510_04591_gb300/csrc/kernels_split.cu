@@ -16,6 +16,7 @@
 
 __device__ __forceinline__ double slice_load(const SliceDesc& d, int r, int k)
 {
+    if (d.mask && d.mask[r] == d.mask[k]) return 0.0;
     const long long c = d.gk ? d.gk[k] : k;
     return d.X[r * d.sr + c * d.sk];
 }
@@ -72,37 +73,60 @@ __device__ __forceinline__ long long slice_mag(double x, int e, int bs)
     return mant >> (-sh);
 }
 
-__global__ void k_slice(const SliceDesc* D)
+// Grid: (64-wide k tile, 64-row tile, operand).  The tile passes through shared
+// memory (coalesced along whichever dimension of X is contiguous); then each
+// thread turns 8 consecutive k of one row into digits and writes each slice's
+// 8 values with one 16-byte store.
+#define SL_T 64
+__global__ void __launch_bounds__(256) k_slice(const SliceDesc* D)
 {
     const SliceDesc d = D[blockIdx.z];
-    const int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const int k0 = blockIdx.x * SL_T, r0 = blockIdx.y * SL_T;
     if (k0 >= d.Kp || r0 >= d.rows) return;
-    __shared__ double T[32][33];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    for (int q = ty; q < 32; q += 8) {
-        // T[row][k]; coalesced along the contiguous dimension of X
+    __shared__ double T[SL_T][SL_T + 1];
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < SL_T * SL_T; idx += 256) {
         int r, k;
-        if (d.sr == 1) { r = r0 + tx; k = k0 + q; } else { r = r0 + q; k = k0 + tx; }
+        if (d.sr == 1) { r = idx % SL_T; k = idx / SL_T; } else { k = idx % SL_T; r = idx / SL_T; }
         double v = 0.0;
-        if (r < d.rows && k < d.K) v = slice_load(d, r, k);
-        if (d.sr == 1) T[tx][q] = v; else T[q][tx] = v;
+        if (r0 + r < d.rows && k0 + k < d.K) v = slice_load(d, r0 + r, k0 + k);
+        T[r][k] = v;
     }
     __syncthreads();
     const int bs = d.beta * d.s;
     const long long mask = (1LL << d.beta) - 1;
-    for (int q = ty; q < 32; q += 8) {
-        const int r = r0 + q, k = k0 + tx;
-        if (r >= d.rows) continue;
-        const double x = T[q][tx];
-        const long long M = slice_mag(x, d.e[r], bs);
-        const float sg = (x < 0.0) ? -1.0f : 1.0f;
+#pragma unroll
+    for (int i = 0; i < (SL_T * SL_T / 8) / 256; i++) {
+        const int u = tid + 256 * i;
+        const int r = u / (SL_T / 8), kg = u % (SL_T / 8);
+        const int row = r0 + r, kk = k0 + kg * 8;
+        if (row >= d.rows || kk >= d.Kp) continue;
+        const int e = d.e[row];
+        long long Mg[8];
+        float sg[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const double x = T[r][kg * 8 + j];
+            Mg[j] = slice_mag(x, e, bs);
+            sg[j] = (x < 0.0) ? -1.0f : 1.0f;
+        }
         for (int p = 0; p < d.s; p++) {
-            const long long dig = (M >> (d.beta * (d.s - 1 - p))) & mask;
-            // t_p 2^(-beta p): exact in the slice type (beta <= 8 for BF16, <= 11 for FP16)
-            const float val = ldexpf(sg * (float)dig, -d.beta * p);
-            const size_t at = ((size_t)p * d.rows + r) * d.Kp + k;
-            if (d.f16) ((__half*)d.S)[at] = __float2half_rn(val);
-            else d.S[at] = __float2bfloat16_rn(val);
+            const float sc = __int_as_float((127 - d.beta * p) << 23);   // 2^(-beta p), exact
+            const int sh = d.beta * (d.s - 1 - p);
+            unsigned short h[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                // t_p 2^(-beta p): exact in the slice type (beta <= 8 BF16, <= 11 FP16)
+                const float val = sg[j] * (float)((Mg[j] >> sh) & mask) * sc;
+                h[j] = d.f16 ? __half_as_ushort(__float2half_rn(val))
+                             : __bfloat16_as_ushort(__float2bfloat16_rn(val));
+            }
+            uint4 w;
+            w.x = (unsigned)h[0] | ((unsigned)h[1] << 16);
+            w.y = (unsigned)h[2] | ((unsigned)h[3] << 16);
+            w.z = (unsigned)h[4] | ((unsigned)h[5] << 16);
+            w.w = (unsigned)h[6] | ((unsigned)h[7] << 16);
+            *(uint4*)(d.S + ((size_t)p * d.rows + row) * d.Kp + kk) = w;
         }
     }
 }
@@ -126,13 +150,13 @@ SplitPrec split_prec(int kind, int bits)
     SplitPrec p;
     switch (kind) {
     case SPLIT_BF16X2:   // two 8-bit digits: levels 0 and 1, 2 x 255^2 x 128 < 2^24
-        p.beta = 8; p.s = 2; p.chunk = 128; p.f16 = 0;
+        p.beta = 8; p.s = 2; p.chunk = 128; p.f16 = 0; p.nacc = 2;
         break;
     case SPLIT_FP16X2:   // two 11-bit digits: FP32 accumulation rounds
-        p.beta = 11; p.s = 2; p.chunk = UM_BK; p.f16 = 1;
+        p.beta = 11; p.s = 2; p.chunk = UM_BK; p.f16 = 1; p.nacc = 2;
         break;
-    default:             // 7-bit digits: levels 0..3 exact over 256, 4 x 127^2 x 256 < 2^24
-        p.beta = 7; p.s = (bits + 6) / 7; p.chunk = 256; p.f16 = 0;
+    default:             // 7-bit digits, s <= 8: every level exact over 128, 8 x 127^2 x 128 < 2^24
+        p.beta = 7; p.s = (bits + 6) / 7; p.chunk = 128; p.f16 = 0; p.nacc = p.s;
         break;
     }
     return p;
@@ -183,6 +207,7 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
         SliceDesc a;
         memset(&a, 0, sizeof(a));
         a.X = d.A;
+        a.mask = d.amask;
         if (!d.transA) { a.sr = 1; a.sk = d.lda; a.gk = d.acol; }
         else { a.sr = d.lda; a.sk = 1; a.gk = nullptr; }
         a.rows = d.M; a.K = d.Kd; a.Kp = kps[i]; a.s = ss[i]; a.beta = betas[i]; a.f16 = pr.f16;
@@ -223,9 +248,10 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
     k_slice_exp<<<dim3(ry, (unsigned)sl.size()), 256, 0, st>>>(dsl);
     td_prof_end(st, "k_slice_exp");
     td_prof_begin(st);
-    k_slice<<<dim3((unsigned)(maxkp / 32), ry, (unsigned)sl.size()), 256, 0, st>>>(dsl);
+    k_slice<<<dim3((unsigned)td_cdiv(maxkp, SL_T), (unsigned)td_cdiv(maxrows, SL_T),
+                   (unsigned)sl.size()), 256, 0, st>>>(dsl);
     td_prof_end(st, "k_slice");
-    umma_launch(dsg, (int)sg.size(), tiles, pr.s, status, st);
+    umma_launch(dsg, (int)sg.size(), tiles, pr.s, pr.nacc, status, st);
     g_split_tensor_flops += tflops;
     if (cudaGetLastError() != cudaSuccess) *rc = TDEIG_ECUDA;
     return flops;

@@ -9,17 +9,26 @@
 //     memory (cp.async, canonical K-major core-matrix layout without swizzle)
 //     through a 2- or 3-stage ring;
 //   * one thread issues tcgen05.mma (M 128, N 64, K 16, 16-bit in, FP32 out) for
-//     every pair p + q <= s - 1 into one of five TMEM accumulators: levels
-//     p+q = 0..3 each stay exact over a k-chunk of the problem's `chunk`
-//     (e.g. 4 pairs x 127^2 x 256 < 2^24 for 7-bit digits), levels >= 4 share
-//     the fifth (their FP32 rounding is 2^-52 of the leading term);
-//   * after every k-chunk the accumulators are read back with
-//     tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e. tile rows) and
-//     summed into a per-thread double-float (FP32 hi + lo) row of 64 values;
-//   * the epilogue writes alpha 2^(e_i + f_j - 2 beta)(hi + lo) + betac C in FP64.
-// TMEM (512 columns) is allocated after the first loads are issued and freed
-// right after the last drain, so a second resident CTA loads while this one
-// computes, and computes while this one writes its tile.
+//     every pair p + q <= s - 1 into the TMEM accumulator of its level p + q;
+//     a level's integer sum stays exact over a k-chunk of the problem's
+//     `chunk` (at most 8 pairs x 127^2 x 128 < 2^24 for 7-bit digits).  Levels
+//     are never mixed in one FP32 accumulator: measured, the tensor cores'
+//     accumulation of mixed-scale products loses far more than one rounding
+//     per add (2e-13 relative products at 56 bits when levels >= 4 shared one);
+//   * after every k-chunk the accumulators are read back with tcgen05.ld (warp w
+//     reads TMEM lanes 32 (w % 4) + 0..31, i.e. tile rows, and columns
+//     32 (w / 4) + 0..31) and summed per output entry exactly, as integers: the
+//     first UM_HI levels in one int64 and the finer ones in a second (each
+//     level shifted by beta relative to the next; a rounded FP32 sum of the
+//     fine levels was measured to cost 1e-11 relative on Cauchy-like rows,
+//     whose many small entries give the fine levels a real share);
+//   * the epilogue forms the FP64 value of both sums with integer bit
+//     operations and one FP64 add (FP64 arithmetic issues at 1/64 of the FP32
+//     rate here), times 2^(e_i + f_j - 2 beta), and writes alpha v + betac C.
+// TMEM (nacc x 64 columns, 256 or 512) is allocated after the
+// first loads are issued and freed right after the last drain, so a second
+// resident CTA loads while this one computes, and computes while this one
+// writes its tile.
 // MMA completion is tracked with one mbarrier per stage (tcgen05.commit); every
 // wait is bounded (about one second of SM clock), after which the kernel sets
 // TD_STATUS_TIMEOUT, waits for its own copies, frees its TMEM and returns.
@@ -28,14 +37,15 @@
 
 #include "split.cuh"
 
-#define UM_NT 128
+#define UM_NT 256                        // 8 warps: warp w reads TMEM lanes 32 (w % 4) + .., columns 32 (w / 4) + ..
+#define UM_CW (UM_BN / 2)                // output columns per thread
+#define UM_HI 4                          // levels in the first int64 sum (the rest in the second)
 #define UM_LBO 128                       // bytes between core matrices adjacent in K
 #define UM_SBO (UM_BK / 8 * 128)         // bytes between core matrices adjacent in M / N
 #define UM_KCH (UM_BK / 8)               // 16-byte chunks per row and k-block
 #define UM_ASLICE (UM_BM * UM_BK * 2)    // one A slice of one stage: 8 KiB
 #define UM_BSLICE (UM_BN * UM_BK * 2)    // one B slice of one stage: 4 KiB
-#define UM_NACC 5                        // accumulators: levels 0, 1, 2, 3 and >= 4
-#define UM_TMEM_COLS 512                 // 5 x 64 FP32 columns, rounded up to a power of two
+#define UM_NACC_MAX 8                    // one TMEM accumulator per level p + q < 8
 #define UM_WAIT_CYCLES (1LL << 31)       // bounded waits: ~1 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -133,23 +143,26 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
-// f 2^k as an FP64 value, built from f's bits with integer operations (FP64
-// instructions issue at 1/64 of the FP32 rate on this part).  Exact; float
-// subnormals (|f| < 2^-126, far below the rounding of the sum) become 0.
-__device__ __forceinline__ double f2d_scaled(float f, int k)
+// x 2^k as an FP64 value (x an int64): exact by integer operations when
+// |x| < 2^53, else through the rounding conversion.
+__device__ __forceinline__ double i2d_scaled(long long x, int k)
 {
-    const uint32_t b = __float_as_uint(f);
-    const uint32_t e = (b >> 23) & 0xFFu;
-    const uint64_t bits = ((uint64_t)(b >> 31) << 63) | ((uint64_t)(e + (1023 - 127) + k) << 52) |
-                          ((uint64_t)(b & 0x7FFFFFu) << 29);
-    return e ? __longlong_as_double((long long)bits) : 0.0;
+    if (x == 0) return 0.0;
+    const unsigned long long u = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
+    const int msb = 63 - __clzll((long long)u);
+    if (msb > 52) return ldexp((double)x, k);
+    const unsigned long long bits = ((unsigned long long)(x < 0) << 63) |
+                                    ((unsigned long long)(msb + 1023 + k) << 52) |
+                                    ((u << (52 - msb)) & 0xFFFFFFFFFFFFFull);
+    return __longlong_as_double((long long)bits);
 }
 
 extern __shared__ __align__(1024) unsigned char um_smem[];
 
-__global__ void __launch_bounds__(UM_NT, 2)
-    k_split_umma(const SplitGemmDesc* G, int ng, int smax, int nst, int* status)
+__global__ void __launch_bounds__(UM_NT, 1)
+    k_split_umma(const SplitGemmDesc* G, int ng, int smax, int nst, int nacc, int* status)
 {
+    const uint32_t tcols = nacc <= 4 ? 256u : 512u;
     __shared__ __align__(8) uint64_t bar[3];
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -187,18 +200,14 @@ __global__ void __launch_bounds__(UM_NT, 2)
         for (int p = 0; p < s; p++) {
             const __nv_bfloat16* Ap = g.SA + (size_t)p * M * Kp;
             const __nv_bfloat16* Bp = g.SB + (size_t)p * N * Kp;
-#pragma unroll
-            for (int i = 0; i < UM_BM * UM_KCH / UM_NT; i++) {   // A: 128 rows x UM_KCH chunks
-                const int ch = tid + UM_NT * i;
+            for (int ch = tid; ch < UM_BM * UM_KCH; ch += UM_NT) {   // A: 128 rows x UM_KCH chunks
                 const int r = ch / UM_KCH, c = ch % UM_KCH;
                 const int gr = row0 + r;
                 const bool v = gr < M;
                 um_cp16(sa + p * UM_ASLICE + (r >> 3) * UM_SBO + c * UM_LBO + (r & 7) * 16,
                         Ap + (size_t)(v ? gr : 0) * Kp + k0 + c * 8, v);
             }
-#pragma unroll
-            for (int i = 0; i < UM_BN * UM_KCH / UM_NT; i++) {   // B: 64 rows x UM_KCH chunks
-                const int ch = tid + UM_NT * i;
+            for (int ch = tid; ch < UM_BN * UM_KCH; ch += UM_NT) {   // B: 64 rows x UM_KCH chunks
                 const int r = ch / UM_KCH, c = ch % UM_KCH;
                 const int gc = col0 + r;
                 const bool v = gc < N;
@@ -208,9 +217,13 @@ __global__ void __launch_bounds__(UM_NT, 2)
         }
     };
 
-    float hs[UM_BN], ls[UM_BN];
+    long long ihi[UM_CW];   // sum over levels L < hl of I_L 2^(beta (hl - 1 - L))
+    long long ilo[UM_CW];   // sum over levels L >= hl of I_L 2^(beta (s - 1 - L))
 #pragma unroll
-    for (int c = 0; c < UM_BN; c++) { hs[c] = 0.0f; ls[c] = 0.0f; }
+    for (int c = 0; c < UM_CW; c++) { ihi[c] = 0; ilo[c] = 0; }
+    const int quarter = warp & 3, half = warp >> 2;
+    const int beta = g.beta;
+    const int hl = min(s, UM_HI);   // levels summed in the int64
     for (int i = 0; i < nst - 1; i++) {
         if (i < nkb) load(i, kb0 + i * UM_BK);
         asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -219,7 +232,7 @@ __global__ void __launch_bounds__(UM_NT, 2)
         // blocks while the other resident CTA holds the columns
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                          smem_u32(&tmem_slot)),
-                     "r"(UM_TMEM_COLS)
+                     "r"(tcols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
@@ -230,7 +243,7 @@ __global__ void __launch_bounds__(UM_NT, 2)
     bool held = true;
     const uint32_t idesc = umma_idesc(UM_BM, UM_BN, g.f16);
     const int chunk = g.chunk;
-    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+    const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(half * UM_CW);
     unsigned started = 0;
     int kchunk = 0;
     bool fail = false;
@@ -247,7 +260,7 @@ __global__ void __launch_bounds__(UM_NT, 2)
             for (int kk = 0; kk < UM_BK / 16; kk++)
                 for (int p = 0; p < s; p++)
                     for (int q = 0; p + q < s; q++) {
-                        const int L = min(p + q, UM_NACC - 1);
+                        const int L = min(p + q, nacc - 1);
                         umma_f16kind(tmem + L * UM_BN,
                                   umma_desc(a0 + p * UM_ASLICE + kk * 2 * UM_LBO),
                                   umma_desc(b0 + q * UM_BSLICE + kk * 2 * UM_LBO), idesc,
@@ -272,20 +285,24 @@ __global__ void __launch_bounds__(UM_NT, 2)
             if (__syncthreads_or(!ok)) { fail = true; break; }
             tc_fence_after();
 #pragma unroll
-            for (int L = 0; L < UM_NACC; L++)
+            for (int L = 0; L < UM_NACC_MAX; L++)
 #pragma unroll
-                for (int cg = 0; cg < UM_BN / 16; cg++) {
-                    if (L >= s) continue;   // level L exists only for s > L
+                for (int cg = 0; cg < UM_CW / 16; cg++) {
+                    if (L >= s || L >= nacc) continue;   // level L exists only for s > L
                     float v[16];
                     tmem_ld16(trow + L * UM_BN + cg * 16, v);
+                    // acc_L = I_L 2^(-beta L) with I_L an integer: exact in int64
+                    const float up = __int_as_float((127 + beta * L) << 23);
+                    if (L < hl) {
+                        const int sh = beta * (hl - 1 - L);
 #pragma unroll
-                    for (int c = 0; c < 16; c++) {
-                        // double-float accumulation (two-sum)
-                        const float h = hs[cg * 16 + c], x = v[c];
-                        const float sm = h + x;
-                        const float bb = sm - h;
-                        ls[cg * 16 + c] += (h - (sm - bb)) + (x - bb);
-                        hs[cg * 16 + c] = sm;
+                        for (int c = 0; c < 16; c++)
+                            ihi[cg * 16 + c] += __float2ll_rn(v[c] * up) << sh;
+                    } else {
+                        const int sh = beta * (s - 1 - L);
+#pragma unroll
+                        for (int c = 0; c < 16; c++)
+                            ilo[cg * 16 + c] += __float2ll_rn(v[c] * up) << sh;
                     }
                 }
             tc_fence_before();
@@ -294,7 +311,7 @@ __global__ void __launch_bounds__(UM_NT, 2)
             kchunk = 0;
             if (it == nkb - 1 && warp == 0) {
                 asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
-                             "r"(UM_TMEM_COLS)
+                             "r"(tcols)
                              : "memory");
             }
             if (it == nkb - 1) held = false;
@@ -302,16 +319,17 @@ __global__ void __launch_bounds__(UM_NT, 2)
     }
 
     if (!fail) {
-        const int row = row0 + 32 * warp + lane;
+        const int row = row0 + 32 * quarter + lane;
         if (row < M) {
-            const int er = g.ea[row] - 2 * g.beta;
+            const int er = g.ea[row] - 2 * beta;
             const double alpha = g.alpha, betac = g.betac;
 #pragma unroll
-            for (int c = 0; c < UM_BN; c++) {
-                const int col = col0 + c;
+            for (int c = 0; c < UM_CW; c++) {
+                const int col = col0 + half * UM_CW + c;
                 if (col < N) {
                     const int k = er + g.eb[col];
-                    double v = f2d_scaled(hs[c], k) + f2d_scaled(ls[c], k);
+                    double v = i2d_scaled(ihi[c], k - beta * (hl - 1)) +
+                               i2d_scaled(ilo[c], k - beta * (s - 1));
                     if (alpha != 1.0) v *= alpha;
                     double* out = g.C + (size_t)(g.ccol ? g.ccol[col] : col) * g.ldc + row;
                     *out = betac != 0.0 ? fma(betac, *out, v) : v;
@@ -327,7 +345,7 @@ __global__ void __launch_bounds__(UM_NT, 2)
         __syncthreads();
         if (warp == 0)
             asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
-                         "r"(UM_TMEM_COLS)
+                         "r"(tcols)
                          : "memory");
     }
 }
@@ -340,9 +358,10 @@ size_t umma_smem_bytes(int smax, int* nstages)
     return n * stage + 1024;   // + alignment slack of the dynamic base
 }
 
-void umma_launch(const SplitGemmDesc* dev, int ng, int tiles, int smax, int* status,
+void umma_launch(const SplitGemmDesc* dev, int ng, int tiles, int smax, int nacc, int* status,
                  cudaStream_t st)
 {
+    nacc = nacc < 2 ? 2 : nacc > UM_NACC_MAX ? UM_NACC_MAX : nacc;
     if (tiles <= 0) return;
     int nst = 0;
     const size_t smem = umma_smem_bytes(smax, &nst);
@@ -352,6 +371,6 @@ void umma_launch(const SplitGemmDesc* dev, int ng, int tiles, int smax, int* sta
         attr = smem;
     }
     td_prof_begin(st);
-    k_split_umma<<<tiles, UM_NT, smem, st>>>(dev, ng, smax, nst, status);
+    k_split_umma<<<tiles, UM_NT, smem, st>>>(dev, ng, smax, nst, nacc, status);
     td_prof_end(st, "k_split_umma");
 }

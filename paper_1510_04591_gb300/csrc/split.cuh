@@ -8,9 +8,9 @@
 // (likewise the columns of op(B) with 2^f_j).  A slice-pair product S_p S_q^T
 // is an integer sum scaled by 2^(-beta (p + q)); pairs with p + q <= s - 1
 // are accumulated on the tensor cores in FP32, one accumulator per level
-// p + q in {0, 1, 2, 3} (exact while the level's integer sum stays below 2^24,
-// which bounds the k-range, `chunk`, summed before a drain) and one for the
-// levels >= 4, drained into a double-float (FP32 hi + lo) sum, converted to
+// p + q (exact while the level's integer sum stays below 2^24, which bounds
+// the k-range, `chunk`, summed before a drain), drained into a double-float
+// (FP32 hi + lo) sum, converted to
 // FP64 and scaled by 2^(e_i + f_j - 2 beta).  Dropped pairs and truncated
 // digits bound the error by about 2^(e_i + f_j) K 2^(-beta s) per entry.
 // Kinds: SPLIT_OZAKI (beta 7, s = ceil(bits / 7)), SPLIT_BF16X2 (beta 8, s 2:
@@ -30,6 +30,7 @@ struct SliceDesc {
     const int* gk;
     long long sr, sk;
     int rows, K, Kp, s, beta;
+    const int* mask;    // optional: entry (r, k) is zero when mask[r] == mask[k]
     int f16;            // slices are FP16 (else BF16)
     __nv_bfloat16* S;   // slice p, row r at S + (p * rows + r) * Kp (16-bit values)
     int* e;             // exponent bound per row: max |row| < 2^e
@@ -51,18 +52,19 @@ struct SplitGemmDesc {
     int tile0, tiles_m;
 };
 
-// Tensor-core (tcgen05) slice-pair products: tile 128 x 64 per CTA, five TMEM
-// accumulators (levels p+q = 0, 1, 2, 3 and >= 4).
+// Tensor-core (tcgen05) slice-pair products: tile 128 x 64 per CTA, one TMEM
+// accumulator per level p + q (at most 8).
 #define UM_BM 128
 #define UM_BN 64
 #define UM_BK 16
 
 enum { SPLIT_OZAKI = 0, SPLIT_BF16X2 = 1, SPLIT_FP16X2 = 2 };
 struct SplitPrec {
-    int beta, s, chunk, f16;
+    int beta, s, chunk, f16, nacc;
 };
 SplitPrec split_prec(int kind, int bits);
-void umma_launch(const SplitGemmDesc* dev, int ng, int tiles, int smax, int* status,
+// nacc: TMEM accumulators, one per level p + q (s of them)
+void umma_launch(const SplitGemmDesc* dev, int ng, int tiles, int smax, int nacc, int* status,
                  cudaStream_t st);
 size_t umma_smem_bytes(int smax, int* nstages);
 

@@ -1222,3 +1222,58 @@ extern "C" int tdeig_node_features(tdeig_handle h, int64_t K, int64_t n, const d
     CU(cudaStreamSynchronize(st));
     return TDEIG_OK;
 }
+
+extern "C" int tdeig_split_gemm(tdeig_handle h, int64_t M, int64_t N, int64_t K, const double* A,
+                                int64_t lda, int transA, const double* B, int64_t ldb, int transB,
+                                double* C, int64_t ldc, int prec, int bits)
+{
+    if (!h || M < 0 || N < 0 || K < 0 || M > (1 << 24) || N > (1 << 24) || K > (1 << 24))
+        return TDEIG_EINVAL;
+    if (prec != TDEIG_PREC_SPLIT && prec != TDEIG_PREC_BF16X2 && prec != TDEIG_PREC_FP16X2)
+        return TDEIG_EINVAL;
+    if (prec == TDEIG_PREC_SPLIT && (bits < 8 || bits > 56)) return TDEIG_EINVAL;
+    if (M == 0 || N == 0) return TDEIG_OK;
+    if (!A || !B || !C || lda < (transA ? K : M) || ldb < (transB ? N : K) || ldc < M || lda < 1 ||
+        ldb < 1)
+        return TDEIG_EINVAL;
+    CU(cudaSetDevice(h->device));
+    cudaStream_t st = h->stream;
+    const int64_t ea = (transA ? M : K) * lda, eb = (transB ? K : N) * ldb, ec = N * ldc;
+    const bool da = is_device_ptr(A), db = is_device_ptr(B), dc = is_device_ptr(C);
+    DevBuf buf;
+    const size_t bytes = ((da ? 0 : ea) + (db ? 0 : eb) + (dc ? 0 : ec)) * sizeof(double) + 64 + 512;
+    if (cudaMalloc(&buf.p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return TDEIG_ENOMEM;
+    }
+    double* q = (double*)buf.p;
+    int* status = (int*)q;
+    q += 8;
+    const double *Ad = A, *Bd = B;
+    double* Cd = C;
+    if (!da) { CU(cudaMemcpyAsync(q, A, ea * sizeof(double), cudaMemcpyHostToDevice, st)); Ad = q; q += ea; }
+    if (!db) { CU(cudaMemcpyAsync(q, B, eb * sizeof(double), cudaMemcpyHostToDevice, st)); Bd = q; q += eb; }
+    if (!dc) { Cd = q; q += ec; }
+    CU(cudaMemsetAsync(status, 0, sizeof(int), st));
+    GemmDesc g;
+    memset(&g, 0, sizeof(g));
+    g.A = Ad; g.lda = (int)lda; g.transA = transA ? 1 : 0;
+    g.B = Bd; g.ldb = (int)ldb; g.transB = transB ? 1 : 0;
+    g.C = Cd; g.ldc = (int)ldc;
+    g.M = (int)M; g.N = (int)N; g.Kd = (int)K; g.alpha = 1.0; g.beta = 0.0;
+    int rc = TDEIG_OK;
+    if (K == 0) {
+        for (int64_t j = 0; j < N; j++) CU(cudaMemsetAsync(Cd + j * ldc, 0, M * sizeof(double), st));
+    } else {
+        split_launch_gemm(std::vector<GemmDesc>{g}, h->split, st, &rc, status,
+                          prec == TDEIG_PREC_BF16X2 ? SPLIT_BF16X2
+                          : prec == TDEIG_PREC_FP16X2 ? SPLIT_FP16X2 : SPLIT_OZAKI,
+                          prec == TDEIG_PREC_SPLIT ? bits : 16);
+        if (rc) return rc;
+    }
+    if (!dc) CU(cudaMemcpyAsync(C, Cd, ec * sizeof(double), cudaMemcpyDeviceToHost, st));
+    int hs = 0;
+    CU(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    return (hs & TD_STATUS_TIMEOUT) ? TDEIG_ETIMEOUT : TDEIG_OK;
+}

@@ -91,6 +91,9 @@ def lib():
         L.tdeig_rank_records.restype = ctypes.c_int
         L.tdeig_node_features.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp]
         L.tdeig_node_features.restype = ctypes.c_int
+        L.tdeig_split_gemm.argtypes = [_vp, _i64, _i64, _i64, _vp, _i64, ctypes.c_int, _vp, _i64,
+                                       ctypes.c_int, _vp, _i64, ctypes.c_int, ctypes.c_int]
+        L.tdeig_split_gemm.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -316,6 +319,21 @@ class Solver:
         if st != OK:
             raise TdeigError(st, "tdeig_node_features")
         return out
+
+    def split_gemm(self, A, B, prec="split", bits=40, transA=False, transB=False):
+        """op(A) op(B) through the split-precision tensor-core product (FP64 in and out)."""
+        A = np.asfortranarray(np.asarray(A, dtype=np.float64))
+        B = np.asfortranarray(np.asarray(B, dtype=np.float64))
+        M = A.shape[1] if transA else A.shape[0]
+        K = A.shape[0] if transA else A.shape[1]
+        N = B.shape[0] if transB else B.shape[1]
+        C = np.empty((M, N), dtype=np.float64, order="F")
+        st = lib().tdeig_split_gemm(self.h, M, N, K, A.ctypes.data, max(A.shape[0], 1),
+                                    int(transA), B.ctypes.data, max(B.shape[0], 1), int(transB),
+                                    C.ctypes.data, max(M, 1), _PRECS[prec], int(bits))
+        if st != OK:
+            raise TdeigError(st, "tdeig_split_gemm")
+        return C
 
     def rank_records(self):
         """(features n x 7, ln(rank + 1) n) recorded by the last TDEIG_FLAG_RECORD solve."""

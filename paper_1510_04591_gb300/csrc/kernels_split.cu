@@ -76,25 +76,30 @@ __device__ __forceinline__ long long slice_mag(double x, int e, int bs)
 // Grid: (64-wide k tile, 64-row tile, operand).  The tile passes through shared
 // memory (coalesced along whichever dimension of X is contiguous); then each
 // thread turns 8 consecutive k of one row into digits and writes each slice's
-// 8 values with one 16-byte store.
+// 8 values with one 16-byte store.  Shared rows hold 8 groups of 8 doubles,
+// each group padded to 10 doubles, so a quarter-warp's 16-byte reads of the 8
+// groups of a row fall in distinct banks (and the row stride of 82 doubles
+// keeps the transposing stores at most 2-way).  Digits come from the 64-bit
+// magnitude by 32-bit funnel shifts (beta s <= 56 < 64).
 #define SL_T 64
+#define SL_G 10   // padded group length (doubles)
 __global__ void __launch_bounds__(256) k_slice(const SliceDesc* D)
 {
     const SliceDesc d = D[blockIdx.z];
     const int k0 = blockIdx.x * SL_T, r0 = blockIdx.y * SL_T;
     if (k0 >= d.Kp || r0 >= d.rows) return;
-    __shared__ double T[SL_T][SL_T + 1];
+    __shared__ __align__(16) double T[SL_T][8 * SL_G + 2];   // +2: row stride 164 words
     const int tid = threadIdx.x;
     for (int idx = tid; idx < SL_T * SL_T; idx += 256) {
         int r, k;
         if (d.sr == 1) { r = idx % SL_T; k = idx / SL_T; } else { k = idx % SL_T; r = idx / SL_T; }
         double v = 0.0;
         if (r0 + r < d.rows && k0 + k < d.K) v = slice_load(d, r0 + r, k0 + k);
-        T[r][k] = v;
+        T[r][(k >> 3) * SL_G + (k & 7)] = v;
     }
     __syncthreads();
     const int bs = d.beta * d.s;
-    const long long mask = (1LL << d.beta) - 1;
+    const unsigned mask = (1u << d.beta) - 1u;
 #pragma unroll
     for (int i = 0; i < (SL_T * SL_T / 8) / 256; i++) {
         const int u = tid + 256 * i;
@@ -102,13 +107,17 @@ __global__ void __launch_bounds__(256) k_slice(const SliceDesc* D)
         const int row = r0 + r, kk = k0 + kg * 8;
         if (row >= d.rows || kk >= d.Kp) continue;
         const int e = d.e[row];
-        long long Mg[8];
+        unsigned mlo[8], mhi[8];
         float sg[8];
+        const double2* src = (const double2*)&T[r][kg * SL_G];
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-            const double x = T[r][kg * 8 + j];
-            Mg[j] = slice_mag(x, e, bs);
-            sg[j] = (x < 0.0) ? -1.0f : 1.0f;
+        for (int j = 0; j < 4; j++) {
+            const double2 x2 = src[j];
+            const long long m0 = slice_mag(x2.x, e, bs), m1 = slice_mag(x2.y, e, bs);
+            mlo[2 * j] = (unsigned)m0; mhi[2 * j] = (unsigned)(m0 >> 32);
+            mlo[2 * j + 1] = (unsigned)m1; mhi[2 * j + 1] = (unsigned)(m1 >> 32);
+            sg[2 * j] = (x2.x < 0.0) ? -1.0f : 1.0f;
+            sg[2 * j + 1] = (x2.y < 0.0) ? -1.0f : 1.0f;
         }
         for (int p = 0; p < d.s; p++) {
             const float sc = __int_as_float((127 - d.beta * p) << 23);   // 2^(-beta p), exact
@@ -116,17 +125,19 @@ __global__ void __launch_bounds__(256) k_slice(const SliceDesc* D)
             unsigned short h[8];
 #pragma unroll
             for (int j = 0; j < 8; j++) {
+                // bits [sh, sh + beta) of the 64-bit magnitude
+                const unsigned w = sh >= 32 ? (mhi[j] >> (sh - 32)) : __funnelshift_r(mlo[j], mhi[j], sh);
                 // t_p 2^(-beta p): exact in the slice type (beta <= 8 BF16, <= 11 FP16)
-                const float val = sg[j] * (float)((Mg[j] >> sh) & mask) * sc;
+                const float val = sg[j] * (float)(int)(w & mask) * sc;
                 h[j] = d.f16 ? __half_as_ushort(__float2half_rn(val))
                              : __bfloat16_as_ushort(__float2bfloat16_rn(val));
             }
-            uint4 w;
-            w.x = (unsigned)h[0] | ((unsigned)h[1] << 16);
-            w.y = (unsigned)h[2] | ((unsigned)h[3] << 16);
-            w.z = (unsigned)h[4] | ((unsigned)h[5] << 16);
-            w.w = (unsigned)h[6] | ((unsigned)h[7] << 16);
-            *(uint4*)(d.S + ((size_t)p * d.rows + row) * d.Kp + kk) = w;
+            uint4 w4;
+            w4.x = (unsigned)h[0] | ((unsigned)h[1] << 16);
+            w4.y = (unsigned)h[2] | ((unsigned)h[3] << 16);
+            w4.z = (unsigned)h[4] | ((unsigned)h[5] << 16);
+            w4.w = (unsigned)h[6] | ((unsigned)h[7] << 16);
+            *(uint4*)(d.S + ((size_t)p * d.rows + row) * d.Kp + kk) = w4;
         }
     }
 }

@@ -4,11 +4,12 @@
 // 2^(e_i - beta) sum_p S_p[i, :] with S_p = t_p 2^(-beta p) and t_p a signed
 // beta-bit integer digit, likewise the columns of op(B) (BF16 or FP16 slices).
 // A slice-pair product S_p S_q^T is then an integer sum scaled by
-// 2^(-beta (p+q)).  One CTA computes a 128 x 64 output tile:
+// 2^(-beta (p+q)).  One CTA (4 warps, two per SM) computes a 128 x 32 output
+// tile:
 //   * every k-block of 16 brings all s slices of both operands into shared
 //     memory (cp.async, canonical K-major core-matrix layout without swizzle)
 //     through a 2- or 3-stage ring;
-//   * one thread issues tcgen05.mma (M 128, N 64, K 16, 16-bit in, FP32 out) for
+//   * one thread issues tcgen05.mma (M 128, N 32, K 16, 16-bit in, FP32 out) for
 //     every pair p + q <= s - 1 into the TMEM accumulator of its level p + q;
 //     a level's integer sum stays exact over a k-chunk of the problem's
 //     `chunk` (at most 8 pairs x 127^2 x 128 < 2^24 for 7-bit digits).  Levels
@@ -25,7 +26,7 @@
 //   * the epilogue forms the FP64 value of both sums with integer bit
 //     operations and one FP64 add (FP64 arithmetic issues at 1/64 of the FP32
 //     rate here), times 2^(e_i + f_j - 2 beta), and writes alpha v + betac C.
-// TMEM (nacc x 64 columns, 256 or 512) is allocated after the
+// TMEM (nacc x 32 columns, 128 or 256) is allocated after the
 // first loads are issued and freed right after the last drain, so a second
 // resident CTA loads while this one computes, and computes while this one
 // writes its tile.
@@ -37,14 +38,14 @@
 
 #include "split.cuh"
 
-#define UM_NT 256                        // 8 warps: warp w reads TMEM lanes 32 (w % 4) + .., columns 32 (w / 4) + ..
-#define UM_CW (UM_BN / 2)                // output columns per thread
+#define UM_NT 128                        // 4 warps: warp w reads TMEM lanes 32 w + 0..31 (tile rows)
+#define UM_CW UM_BN                      // output columns per thread
 #define UM_HI 4                          // levels in the first int64 sum (the rest in the second)
 #define UM_LBO 128                       // bytes between core matrices adjacent in K
 #define UM_SBO (UM_BK / 8 * 128)         // bytes between core matrices adjacent in M / N
 #define UM_KCH (UM_BK / 8)               // 16-byte chunks per row and k-block
-#define UM_ASLICE (UM_BM * UM_BK * 2)    // one A slice of one stage: 8 KiB
-#define UM_BSLICE (UM_BN * UM_BK * 2)    // one B slice of one stage: 4 KiB
+#define UM_ASLICE (UM_BM * UM_BK * 2)    // one A slice of one stage: 4 KiB
+#define UM_BSLICE (UM_BN * UM_BK * 2)    // one B slice of one stage: 1 KiB
 #define UM_NACC_MAX 8                    // one TMEM accumulator per level p + q < 8
 #define UM_WAIT_CYCLES (1LL << 31)       // bounded waits: ~1 s at 2 GHz
 
@@ -143,26 +144,35 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
-// x 2^k as an FP64 value (x an int64): exact by integer operations when
-// |x| < 2^53, else through the rounding conversion.
+// x 2^k as an FP64 value (x an int64, |x| < 2^63), rounded to nearest even,
+// by integer operations only (normal results assumed: |k| stays far inside the
+// exponent range here).
 __device__ __forceinline__ double i2d_scaled(long long x, int k)
 {
     if (x == 0) return 0.0;
-    const unsigned long long u = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
-    const int msb = 63 - __clzll((long long)u);
-    if (msb > 52) return ldexp((double)x, k);
-    const unsigned long long bits = ((unsigned long long)(x < 0) << 63) |
-                                    ((unsigned long long)(msb + 1023 + k) << 52) |
-                                    ((u << (52 - msb)) & 0xFFFFFFFFFFFFFull);
-    return __longlong_as_double((long long)bits);
+    const unsigned long long sgn = (unsigned long long)(x < 0) << 63;
+    unsigned long long u = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
+    int msb = 63 - __clzll((long long)u);
+    unsigned long long m;
+    if (msb <= 52) {
+        m = u << (52 - msb);
+    } else {
+        const int sh = msb - 52;
+        m = u >> sh;
+        const unsigned long long rem = u & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (m & 1))) m++;
+        if (m >> 53) { m >>= 1; msb++; }
+    }
+    return __longlong_as_double(
+        (long long)(sgn | ((unsigned long long)(msb + 1023 + k) << 52) | (m & 0xFFFFFFFFFFFFFull)));
 }
 
 extern __shared__ __align__(1024) unsigned char um_smem[];
 
-__global__ void __launch_bounds__(UM_NT, 1)
+__global__ void __launch_bounds__(UM_NT, 2)
     k_split_umma(const SplitGemmDesc* G, int ng, int smax, int nst, int nacc, int* status)
 {
-    const uint32_t tcols = nacc <= 4 ? 256u : 512u;
+    const uint32_t tcols = nacc * UM_BN <= 128 ? 128u : 256u;   // two CTAs per SM fit
     __shared__ __align__(8) uint64_t bar[3];
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -221,7 +231,7 @@ __global__ void __launch_bounds__(UM_NT, 1)
     long long ilo[UM_CW];   // sum over levels L >= hl of I_L 2^(beta (s - 1 - L))
 #pragma unroll
     for (int c = 0; c < UM_CW; c++) { ihi[c] = 0; ilo[c] = 0; }
-    const int quarter = warp & 3, half = warp >> 2;
+    const int quarter = warp, half = 0;
     const int beta = g.beta;
     const int hl = min(s, UM_HI);   // levels summed in the int64
     for (int i = 0; i < nst - 1; i++) {
@@ -323,16 +333,28 @@ __global__ void __launch_bounds__(UM_NT, 1)
         if (row < M) {
             const int er = g.ea[row] - 2 * beta;
             const double alpha = g.alpha, betac = g.betac;
+            // uniform per launch: alpha = +-1 is a sign flip, betac = 0 / 1 a store / add
+            const int amode = alpha == 1.0 ? 0 : alpha == -1.0 ? 1 : 2;
+            const int bmode = betac == 0.0 ? 0 : betac == 1.0 ? 1 : 2;
+            // both halves in one int64 when it cannot overflow: (ihi << sh) + ilo
+            const int shc = beta * (s - hl);
 #pragma unroll
             for (int c = 0; c < UM_CW; c++) {
                 const int col = col0 + half * UM_CW + c;
                 if (col < N) {
                     const int k = er + g.eb[col];
-                    double v = i2d_scaled(ihi[c], k - beta * (hl - 1)) +
-                               i2d_scaled(ilo[c], k - beta * (s - 1));
-                    if (alpha != 1.0) v *= alpha;
+                    const long long h = ihi[c];
+                    double v;
+                    if ((h < 0 ? -h : h) < (1ll << (61 - shc)))
+                        v = i2d_scaled((h << shc) + ilo[c], k - beta * (s - 1));
+                    else
+                        v = i2d_scaled(h, k - beta * (hl - 1)) + i2d_scaled(ilo[c], k - beta * (s - 1));
+                    if (amode == 1) v = -v;
+                    else if (amode == 2) v *= alpha;
                     double* out = g.C + (size_t)(g.ccol ? g.ccol[col] : col) * g.ldc + row;
-                    *out = betac != 0.0 ? fma(betac, *out, v) : v;
+                    if (bmode == 0) *out = v;
+                    else if (bmode == 1) *out += v;
+                    else *out = fma(betac, *out, v);
                 }
             }
         }
@@ -353,7 +375,7 @@ __global__ void __launch_bounds__(UM_NT, 1)
 size_t umma_smem_bytes(int smax, int* nstages)
 {
     const size_t stage = (size_t)smax * (UM_ASLICE + UM_BSLICE);
-    const int n = (3 * stage <= 220 * 1024) ? 3 : 2;
+    const int n = (3 * stage <= 110 * 1024) ? 3 : 2;   // two CTAs per SM
     if (nstages) *nstages = n;
     return n * stage + 1024;   // + alignment slack of the dynamic base
 }

@@ -52,10 +52,10 @@ struct SplitGemmDesc {
     int tile0, tiles_m;
 };
 
-// Tensor-core (tcgen05) slice-pair products: tile 128 x 64 per CTA, one TMEM
+// Tensor-core (tcgen05) slice-pair products: tile 128 x 32 per CTA, one TMEM
 // accumulator per level p + q (at most 8).
 #define UM_BM 128
-#define UM_BN 64
+#define UM_BN 32
 #define UM_BK 16
 
 enum { SPLIT_OZAKI = 0, SPLIT_BF16X2 = 1, SPLIT_FP16X2 = 2 };

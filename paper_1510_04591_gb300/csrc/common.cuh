@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
 #include <vector>
 
 #define TD_EPS 1.1102230246251565e-16  // unit roundoff 2^-53
@@ -71,11 +72,14 @@ struct TdProf {
     bool on = false;
     std::vector<cudaEvent_t> ev;
     std::vector<const char*> name;   // name at the index of each "after" event
+    std::vector<std::string> note;   // optional shape of the launch, same index
     size_t n = 0;
 };
 extern TdProf g_td_prof;
 void td_prof_begin(cudaStream_t st);
 void td_prof_end(cudaStream_t st, const char* name);
+// Attaches a note (a JSON array of numbers) to the last profiled launch.
+void td_prof_note(const std::string& s);
 
 // Host-side launchers (kernels_dc.cu).
 void td_launch_scale_input(const double* d, const double* e, const int64_t* mrow0, const int64_t* mN,

@@ -35,14 +35,21 @@ static cudaEvent_t prof_next(const char* name)
         cudaEventCreate(&e);
         g_td_prof.ev.push_back(e);
         g_td_prof.name.push_back(nullptr);
+        g_td_prof.note.emplace_back();
     }
     g_td_prof.name[g_td_prof.n] = name;
+    g_td_prof.note[g_td_prof.n].clear();
     return g_td_prof.ev[g_td_prof.n++];
 }
 
 void td_prof_begin(cudaStream_t st)
 {
     if (g_td_prof.on) cudaEventRecord(prof_next(nullptr), st);
+}
+
+void td_prof_note(const std::string& s)
+{
+    if (g_td_prof.on && g_td_prof.n > 0) g_td_prof.note[g_td_prof.n - 1] = s;
 }
 
 void td_prof_end(cudaStream_t st, const char* name)

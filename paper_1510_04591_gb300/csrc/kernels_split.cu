@@ -3,6 +3,8 @@
 // ones of op(B); k_slice writes the digits as BF16 or FP16 slices (K
 // contiguous, padded to a multiple of 32); the products run in k_split_umma
 // (kernels_umma.cu).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
@@ -156,6 +158,40 @@ void split_free(SplitWS& w)
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 3-D map over the s slices of an operand: (k: Kp, row: rows, slice: s), 16-bit
+// elements, box (UM_BK, box_rows, s), 64-byte swizzle, zero fill past the ends.
+static bool encode_slices(CUtensorMap* m, const void* base, int Kp, int rows, int s, int box_rows)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)s};
+    const cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)rows * Kp * 2};
+    const cuuint32_t box[3] = {UM_BK, (cuuint32_t)box_rows, (cuuint32_t)s};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<void*>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 SplitPrec split_prec(int kind, int bits)
 {
     SplitPrec p;
@@ -183,7 +219,8 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
         if (d.M > 0 && d.N > 0) g.push_back(d);
     if (g.empty()) return 0.0;
     // scratch: slices and exponents of both operands of every problem, descriptors
-    size_t bytes = al256(g.size() * 2 * sizeof(SliceDesc)) + al256(g.size() * sizeof(SplitGemmDesc));
+    size_t bytes = al256(g.size() * 2 * sizeof(SliceDesc)) + al256(g.size() * sizeof(SplitGemmDesc)) +
+                   al256(g.size() * sizeof(int)) + al256(g.size() * 2 * sizeof(CUtensorMap));
     std::vector<int> betas(g.size()), ss(g.size()), kps(g.size());
     double flops = 0.0, tflops = 0.0;
     for (size_t i = 0; i < g.size(); i++) {
@@ -210,6 +247,9 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
     auto take = [&](size_t n) { char* r = p; p += al256(n); return r; };
     SliceDesc* dsl = (SliceDesc*)take(g.size() * 2 * sizeof(SliceDesc));
     SplitGemmDesc* dsg = (SplitGemmDesc*)take(g.size() * sizeof(SplitGemmDesc));
+    int* dt0 = (int*)take(g.size() * sizeof(int));
+    CUtensorMap* dtm = (CUtensorMap*)take(g.size() * 2 * sizeof(CUtensorMap));   // 256-aligned
+    std::vector<CUtensorMap> tm(g.size() * 2);
     std::vector<SliceDesc> sl;
     std::vector<SplitGemmDesc> sg;
     int maxrows = 0, maxkp = 0, tiles = 0;
@@ -242,12 +282,25 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
         s.C = d.C; s.ldc = d.ldc; s.ccol = d.ccol; s.alpha = d.alpha; s.betac = d.beta;
         s.rsplit = d.rsplit; s.ktop_end = d.ktop_end; s.kbot_beg = d.kbot_beg;
         s.chunk = pr.chunk; s.f16 = pr.f16;
+        if (!encode_slices(&tm[2 * i], a.S, kps[i], d.M, ss[i], UM_BM) ||
+            !encode_slices(&tm[2 * i + 1], b.S, kps[i], d.N, ss[i], UM_BN)) {
+            *rc = TDEIG_ECUDA;
+            return 0.0;
+        }
+        s.tmA = dtm + 2 * i;
+        s.tmB = dtm + 2 * i + 1;
         s.tiles_m = td_cdiv(d.M, UM_BM);
         s.tile0 = tiles;
         tiles += s.tiles_m * td_cdiv(d.N, UM_BN);
         sg.push_back(s);
     }
-    if (cudaMemcpyAsync(dsl, sl.data(), sl.size() * sizeof(SliceDesc), cudaMemcpyHostToDevice, st) !=
+    std::vector<int> t0(sg.size());
+    for (size_t i = 0; i < sg.size(); i++) t0[i] = sg[i].tile0;
+    if (cudaMemcpyAsync(dtm, tm.data(), tm.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(dt0, t0.data(), t0.size() * sizeof(int), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(dsl, sl.data(), sl.size() * sizeof(SliceDesc), cudaMemcpyHostToDevice, st) !=
             cudaSuccess ||
         cudaMemcpyAsync(dsg, sg.data(), sg.size() * sizeof(SplitGemmDesc), cudaMemcpyHostToDevice, st) !=
             cudaSuccess) {
@@ -262,7 +315,16 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
     k_slice<<<dim3((unsigned)td_cdiv(maxkp, SL_T), (unsigned)td_cdiv(maxrows, SL_T),
                    (unsigned)sl.size()), 256, 0, st>>>(dsl);
     td_prof_end(st, "k_slice");
-    umma_launch(dsg, (int)sg.size(), tiles, pr.s, pr.nacc, status, st);
+    umma_launch(dsg, dt0, (int)sg.size(), tiles, pr.s, pr.nacc, status, st);
+    if (g_td_prof.on) {
+        // [tiles, k-blocks over all tiles, slices, problems, tensor flops]
+        double kbl = 0.0;
+        for (size_t i = 0; i < g.size(); i++)
+            kbl += (double)sg[i].tiles_m * td_cdiv(g[i].N, UM_BN) * (kps[i] / UM_BK);
+        char nb[160];
+        snprintf(nb, sizeof(nb), "[%d,%.0f,%d,%d,%.6e]", tiles, kbl, pr.s, (int)g.size(), tflops);
+        td_prof_note(nb);
+    }
     g_split_tensor_flops += tflops;
     if (cudaGetLastError() != cudaSuccess) *rc = TDEIG_ECUDA;
     return flops;

@@ -4,48 +4,56 @@
 // 2^(e_i - beta) sum_p S_p[i, :] with S_p = t_p 2^(-beta p) and t_p a signed
 // beta-bit integer digit, likewise the columns of op(B) (BF16 or FP16 slices).
 // A slice-pair product S_p S_q^T is then an integer sum scaled by
-// 2^(-beta (p+q)).  One CTA (4 warps, two per SM) computes a 128 x 32 output
-// tile:
-//   * every k-block of 16 brings all s slices of both operands into shared
-//     memory (cp.async, canonical K-major core-matrix layout without swizzle)
-//     through a 2- or 3-stage ring;
-//   * one thread issues tcgen05.mma (M 128, N 32, K 16, 16-bit in, FP32 out) for
-//     every pair p + q <= s - 1 into the TMEM accumulator of its level p + q;
-//     a level's integer sum stays exact over a k-chunk of the problem's
-//     `chunk` (at most 8 pairs x 127^2 x 128 < 2^24 for 7-bit digits).  Levels
-//     are never mixed in one FP32 accumulator: measured, the tensor cores'
-//     accumulation of mixed-scale products loses far more than one rounding
-//     per add (2e-13 relative products at 56 bits when levels >= 4 shared one);
-//   * after every k-chunk the accumulators are read back with tcgen05.ld (warp w
-//     reads TMEM lanes 32 (w % 4) + 0..31, i.e. tile rows, and columns
-//     32 (w / 4) + 0..31) and summed per output entry exactly, as integers: the
-//     first UM_HI levels in one int64 and the finer ones in a second (each
-//     level shifted by beta relative to the next; a rounded FP32 sum of the
-//     fine levels was measured to cost 1e-11 relative on Cauchy-like rows,
-//     whose many small entries give the fine levels a real share);
-//   * the epilogue forms the FP64 value of both sums with integer bit
-//     operations and one FP64 add (FP64 arithmetic issues at 1/64 of the FP32
-//     rate here), times 2^(e_i + f_j - 2 beta), and writes alpha v + betac C.
-// TMEM (nacc x 32 columns, 128 or 256) is allocated after the
-// first loads are issued and freed right after the last drain, so a second
-// resident CTA loads while this one computes, and computes while this one
-// writes its tile.
-// MMA completion is tracked with one mbarrier per stage (tcgen05.commit); every
-// wait is bounded (about one second of SM clock), after which the kernel sets
-// TD_STATUS_TIMEOUT, waits for its own copies, frees its TMEM and returns.
+// 2^(-beta (p+q)).
+//
+// Persistent, warp-specialised kernel: one CTA per SM walks the 128 x 32 output
+// tiles of all problems of the launch (tile t, t + grid, ...).
+//   * warp 0, one thread (loader): for every k-block of 32 it fetches all s
+//     slices of both operands into a ring of shared-memory stages with two TMA
+//     copies (cp.async.bulk.tensor over 3-D maps (k, row, slice), box
+//     32 x rows x s, 64-byte swizzle: each box lands as [slice][row][64 B],
+//     the canonical K-major SWIZZLE_64B layout, 8-row groups 512 B apart; rows
+//     past the end are zero-filled; 64-byte rows keep the copies to whole
+//     sectors); a stage completes its `full` mbarrier by transaction count and
+//     is refilled after its `empty` mbarrier (tcgen05.commit of the MMAs that
+//     read it) completed;
+//   * warp 1, one thread (MMA issuer): tcgen05.mma (M 128, N 32, K 16, 16-bit
+//     in, FP32 out; the two k-steps of a block advance the descriptors' start
+//     address by 32 B inside the swizzle atom) for every pair p + q <= s - 1
+//     into the TMEM accumulator of
+//     its level p + q; a level's integer sum stays exact over a k-chunk of the
+//     problem's `chunk` (at most 8 pairs x 127^2 x 128 < 2^24 for 7-bit
+//     digits).  Levels are never mixed in one FP32 accumulator: measured, the
+//     tensor cores' accumulation of mixed-scale products loses far more than
+//     one rounding per add.  Accumulators are double-buffered (two sets of
+//     levels in 512 TMEM columns), so one chunk is drained while the next is
+//     computed;
+//   * warps 2-5 (drain / epilogue, TMEM lane = tile row): after every chunk
+//     they read the levels with tcgen05.ld and sum them per output entry
+//     exactly as integers (the first UM_HI levels in one int64, the finer ones
+//     in a second, each level shifted by beta relative to the next; a rounded
+//     FP32 sum of the fine levels was measured to cost 1e-11 relative on
+//     Cauchy-like rows), release the buffer, and at the end of a tile form the
+//     FP64 value with integer bit operations (FP64 arithmetic issues at 1/64 of
+//     the FP32 rate here), times 2^(e_i + f_j - 2 beta), and write
+//     alpha v + betac C.
+// Every wait is bounded (about one second of SM clock); on expiry the kernel
+// sets TD_STATUS_TIMEOUT, every role leaves its loop, copies in flight are
+// waited for and the TMEM is freed.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
 #include "split.cuh"
 
-#define UM_NT 128                        // 4 warps: warp w reads TMEM lanes 32 w + 0..31 (tile rows)
-#define UM_CW UM_BN                      // output columns per thread
+
+#define UM_NT 192                        // warp 0 loads, warp 1 issues MMAs, warps 2-5 drain and write
+#define UM_EPI 128                       // drain / epilogue threads (one TMEM lane = tile row each)
 #define UM_HI 4                          // levels in the first int64 sum (the rest in the second)
-#define UM_LBO 128                       // bytes between core matrices adjacent in K
-#define UM_SBO (UM_BK / 8 * 128)         // bytes between core matrices adjacent in M / N
-#define UM_KCH (UM_BK / 8)               // 16-byte chunks per row and k-block
-#define UM_ASLICE (UM_BM * UM_BK * 2)    // one A slice of one stage: 4 KiB
-#define UM_BSLICE (UM_BN * UM_BK * 2)    // one B slice of one stage: 1 KiB
+#define UM_MAXST 8                       // shared-memory ring stages
+#define UM_TCOLS 512                     // two accumulator buffers of up to 8 levels x 32 columns
+#define UM_SBO 512                       // bytes between 8-row groups (8 x 64 B, 64-byte swizzle)
+#define UM_ASLICE (UM_BM * UM_BK * 2)    // one A slice of one stage: 8 KiB
+#define UM_BSLICE (UM_BN * UM_BK * 2)    // one B slice of one stage: 2 KiB
 #define UM_NACC_MAX 8                    // one TMEM accumulator per level p + q < 8
 #define UM_WAIT_CYCLES (1LL << 31)       // bounded waits: ~1 s at 2 GHz
 
@@ -54,22 +62,37 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p)
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ void um_cp16(uint32_t dst, const void* src, bool valid)
-{
-    const int n = valid ? 16 : 0;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(n)
-                 : "memory");
-}
-
-// Shared-memory matrix descriptor: start address, leading (K) and stride (M/N)
-// byte offsets, fixed version bits 0b001 at bit 46, no swizzle.
+// Shared-memory matrix descriptor of a K-major SWIZZLE_64B operand: start
+// address, leading byte offset (unused for swizzled K-major layouts: 1), stride
+// byte offset between 8-row groups, fixed version bits 0b001 at bit 46, base
+// offset 0 (tiles are 1024-byte aligned), layout type 4 (64-byte swizzle) at
+// bit 61.
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr)
 {
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)(UM_LBO >> 4) << 16;
+    d |= (uint64_t)1 << 16;
     d |= (uint64_t)(UM_SBO >> 4) << 32;
     d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
     return d;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// 3-D TMA load of one box into shared memory, completing on `bar` by bytes.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* tmap, int x, int y, int z,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+        "%3, %4}], [%5];\n" ::"r"(dst),
+        "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
 }
 
 // Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and B
@@ -167,232 +190,319 @@ __device__ __forceinline__ double i2d_scaled(long long x, int k)
         (long long)(sgn | ((unsigned long long)(msb + 1023 + k) << 52) | (m & 0xFFFFFFFFFFFFFull)));
 }
 
-extern __shared__ __align__(1024) unsigned char um_smem[];
 
-__global__ void __launch_bounds__(UM_NT, 2)
-    k_split_umma(const SplitGemmDesc* G, int ng, int smax, int nst, int nacc, int* status)
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
 {
-    const uint32_t tcols = nacc * UM_BN <= 128 ? 128u : 256u;   // two CTAs per SM fit
-    __shared__ __align__(8) uint64_t bar[3];
-    __shared__ uint32_t tmem_slot;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar)
+                 : "memory");
+}
+
+// Problem of tile t: the last problem whose first tile is <= t.
+__device__ __forceinline__ int um_problem(const int* t0, int ng, int t)
+{
     int lo = 0, hi = ng - 1;
-    const int bid = blockIdx.x;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (G[mid].tile0 <= bid) lo = mid; else hi = mid - 1;
+        if (t0[mid] <= t) lo = mid; else hi = mid - 1;
     }
-    const SplitGemmDesc& g = G[lo];
-    const int M = g.M, N = g.N, Kp = g.Kp, s = g.s;
-    const int local = bid - g.tile0;
+    return lo;
+}
+
+// Tile geometry shared by the three roles (computed identically by each).
+struct UmTile {
+    int pi, row0, col0, kb0, nkb;
+};
+
+__device__ __forceinline__ UmTile um_tile(const SplitGemmDesc* G, const int* t0, int ng, int t)
+{
+    UmTile u;
+    u.pi = um_problem(t0, ng, t);
+    const SplitGemmDesc& g = G[u.pi];
+    const int local = t - t0[u.pi];
     const int tm = local % g.tiles_m, tn = local / g.tiles_m;
-    const int row0 = tm * UM_BM, col0 = tn * UM_BN;
-    if (row0 >= M || col0 >= N) return;   // whole CTA, before any allocation
-    int kb0 = 0, kb1 = Kp;
+    u.row0 = tm * UM_BM;
+    u.col0 = tn * UM_BN;
+    int kb0 = 0, kb1 = g.Kp;
     if (g.rsplit > 0) {
-        if (row0 >= g.rsplit) kb0 = (g.kbot_beg / UM_BK) * UM_BK;
-        if (row0 + UM_BM <= g.rsplit) kb1 = min(Kp, ((g.ktop_end + UM_BK - 1) / UM_BK) * UM_BK);
+        if (u.row0 >= g.rsplit) kb0 = (g.kbot_beg / UM_BK) * UM_BK;
+        if (u.row0 + UM_BM <= g.rsplit) kb1 = min(g.Kp, ((g.ktop_end + UM_BK - 1) / UM_BK) * UM_BK);
     }
-    const int nkb = kb1 > kb0 ? (kb1 - kb0) / UM_BK : 0;
+    u.kb0 = kb0;
+    u.nkb = kb1 > kb0 ? (kb1 - kb0) / UM_BK : 0;
+    return u;
+}
+
+#define UM_T0_SMEM 2048   // problems whose first tiles are kept in shared memory
+
+extern __shared__ __align__(1024) unsigned char um_smem[];
+
+__global__ void __launch_bounds__(UM_NT, 1)
+    k_split_umma(const SplitGemmDesc* __restrict__ G, const int* __restrict__ tile0, int ng,
+                 int tiles, int smax, int nst, int nacc, int* status)
+{
+    __shared__ __align__(8) uint64_t full_b[UM_MAXST], empty_b[UM_MAXST], tfull_b[2], tempty_b[2];
+    __shared__ uint32_t tmem_slot;
+    const unsigned FULL = 0xffffffffu;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t stage_bytes = (uint32_t)smax * (UM_ASLICE + UM_BSLICE);
-    const uint32_t sbase = smem_u32(um_smem);
-
-    if (tid == 0) {
-        for (int i = 0; i < 3; i++)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bar[i])) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    }
-    __syncthreads();
-
-    auto load = [&](int stg, int k0) {
-        const uint32_t sa = sbase + (uint32_t)stg * stage_bytes;
-        const uint32_t sb = sa + (uint32_t)smax * UM_ASLICE;
-        for (int p = 0; p < s; p++) {
-            const __nv_bfloat16* Ap = g.SA + (size_t)p * M * Kp;
-            const __nv_bfloat16* Bp = g.SB + (size_t)p * N * Kp;
-            for (int ch = tid; ch < UM_BM * UM_KCH; ch += UM_NT) {   // A: 128 rows x UM_KCH chunks
-                const int r = ch / UM_KCH, c = ch % UM_KCH;
-                const int gr = row0 + r;
-                const bool v = gr < M;
-                um_cp16(sa + p * UM_ASLICE + (r >> 3) * UM_SBO + c * UM_LBO + (r & 7) * 16,
-                        Ap + (size_t)(v ? gr : 0) * Kp + k0 + c * 8, v);
-            }
-            for (int ch = tid; ch < UM_BN * UM_KCH; ch += UM_NT) {   // B: 64 rows x UM_KCH chunks
-                const int r = ch / UM_KCH, c = ch % UM_KCH;
-                const int gc = col0 + r;
-                const bool v = gc < N;
-                um_cp16(sb + p * UM_BSLICE + (r >> 3) * UM_SBO + c * UM_LBO + (r & 7) * 16,
-                        Bp + (size_t)(v ? gc : 0) * Kp + k0 + c * 8, v);
-            }
-        }
-    };
-
-    long long ihi[UM_CW];   // sum over levels L < hl of I_L 2^(beta (hl - 1 - L))
-    long long ilo[UM_CW];   // sum over levels L >= hl of I_L 2^(beta (s - 1 - L))
-#pragma unroll
-    for (int c = 0; c < UM_CW; c++) { ihi[c] = 0; ilo[c] = 0; }
-    const int quarter = warp, half = 0;
-    const int beta = g.beta;
-    const int hl = min(s, UM_HI);   // levels summed in the int64
-    for (int i = 0; i < nst - 1; i++) {
-        if (i < nkb) load(i, kb0 + i * UM_BK);
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    // ring base aligned to 1024 bytes (swizzled TMA boxes, descriptor base offset 0)
+    const uint32_t sraw = smem_u32(um_smem);
+    const uint32_t sbase = (sraw + 1023u) & ~1023u;
+    const int* t0 = tile0;
+    if (ng <= UM_T0_SMEM) {
+        int* t0s = (int*)(um_smem + (sbase - sraw) + (size_t)nst * stage_bytes);
+        for (int i = tid; i < ng; i += UM_NT) t0s[i] = tile0[i];
+        t0 = t0s;
     }
     if (warp == 0) {
-        // blocks while the other resident CTA holds the columns
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                          smem_u32(&tmem_slot)),
-                     "r"(tcols)
+                     "r"(UM_TCOLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < nst; i++) {
+            mbar_init(smem_u32(&full_b[i]), 1);
+            mbar_init(smem_u32(&empty_b[i]), 1);
+        }
+        for (int i = 0; i < 2; i++) {
+            mbar_init(smem_u32(&tfull_b[i]), 1);
+            mbar_init(smem_u32(&tempty_b[i]), UM_EPI);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    bool held = true;
-    const uint32_t idesc = umma_idesc(UM_BM, UM_BN, g.f16);
-    const int chunk = g.chunk;
-    const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(half * UM_CW);
-    unsigned started = 0;
-    int kchunk = 0;
-    bool fail = false;
-    for (int it = 0; it < nkb; it++) {
-        const int stg = it % nst;
-        if (nst == 3) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-        else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t a0 = sbase + (uint32_t)stg * stage_bytes;
-            const uint32_t b0 = a0 + (uint32_t)smax * UM_ASLICE;
-            for (int kk = 0; kk < UM_BK / 16; kk++)
-                for (int p = 0; p < s; p++)
-                    for (int q = 0; p + q < s; q++) {
-                        const int L = min(p + q, nacc - 1);
-                        umma_f16kind(tmem + L * UM_BN,
-                                  umma_desc(a0 + p * UM_ASLICE + kk * 2 * UM_LBO),
-                                  umma_desc(b0 + q * UM_BSLICE + kk * 2 * UM_LBO), idesc,
-                                  (started >> L) & 1u);
-                        started |= 1u << L;
-                    }
-            umma_commit(smem_u32(&bar[stg]));
-        }
-        const int nxt = it + nst - 1;
-        bool ok = true;
-        if (nxt < nkb && it >= 1) {
-            // the ring slot of stage nxt was read by the MMAs of iteration it - 1
-            const int pv = it - 1;
-            ok = mbar_wait(smem_u32(&bar[pv % nst]), (uint32_t)((pv / nst) & 1));
-        }
-        if (__syncthreads_or(!ok)) { fail = true; break; }
-        if (nxt < nkb) load(nxt % nst, kb0 + nxt * UM_BK);
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-        kchunk += UM_BK;
-        if (kchunk >= chunk || it == nkb - 1) {
-            ok = mbar_wait(smem_u32(&bar[stg]), (uint32_t)((it / nst) & 1));
-            if (__syncthreads_or(!ok)) { fail = true; break; }
-            tc_fence_after();
-#pragma unroll
-            for (int L = 0; L < UM_NACC_MAX; L++)
-#pragma unroll
-                for (int cg = 0; cg < UM_CW / 16; cg++) {
-                    if (L >= s || L >= nacc) continue;   // level L exists only for s > L
-                    float v[16];
-                    tmem_ld16(trow + L * UM_BN + cg * 16, v);
-                    // acc_L = I_L 2^(-beta L) with I_L an integer: exact in int64
-                    const float up = __int_as_float((127 + beta * L) << 23);
-                    if (L < hl) {
-                        const int sh = beta * (hl - 1 - L);
-#pragma unroll
-                        for (int c = 0; c < 16; c++)
-                            ihi[cg * 16 + c] += __float2ll_rn(v[c] * up) << sh;
-                    } else {
-                        const int sh = beta * (s - 1 - L);
-#pragma unroll
-                        for (int c = 0; c < 16; c++)
-                            ilo[cg * 16 + c] += __float2ll_rn(v[c] * up) << sh;
-                    }
-                }
-            tc_fence_before();
-            __syncthreads();   // TMEM read before the next chunk overwrites it
-            started = 0;
-            kchunk = 0;
-            if (it == nkb - 1 && warp == 0) {
-                asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
-                             "r"(tcols)
-                             : "memory");
-            }
-            if (it == nkb - 1) held = false;
-        }
-    }
+    const uint32_t bufcols = (uint32_t)nacc * UM_BN;   // one set of level accumulators
+    bool ok = true;
 
-    if (!fail) {
-        const int row = row0 + 32 * quarter + lane;
-        if (row < M) {
-            const int er = g.ea[row] - 2 * beta;
+    if (warp == 0) {
+        // ---------------- loader (one thread) ----------------
+        if (lane == 0) {
+            uint32_t fill = 0;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+                const UmTile u = um_tile(G, t0, ng, t);
+                const SplitGemmDesc& g = G[u.pi];
+                const int s = g.s;
+                const void* const tmA = g.tmA;
+                const void* const tmB = g.tmB;
+                const uint32_t bytes = (uint32_t)s * (UM_ASLICE + UM_BSLICE);
+                for (int kb = 0; kb < u.nkb; kb++, fill++) {
+                    const uint32_t slot = fill % nst;
+                    if (fill >= (uint32_t)nst) {
+                        ok = mbar_wait(smem_u32(&empty_b[slot]), ((fill / nst) - 1) & 1);
+                        if (!ok) break;
+                    }
+                    const uint32_t sa = sbase + slot * stage_bytes;
+                    const uint32_t sb = sa + (uint32_t)smax * UM_ASLICE;
+                    const uint32_t fb = smem_u32(&full_b[slot]);
+                    const int k0 = u.kb0 + kb * UM_BK;
+                    mbar_expect_tx(fb, bytes);
+                    tma_load_3d(sa, tmA, k0, u.row0, 0, fb);
+                    tma_load_3d(sb, tmB, k0, u.col0, 0, fb);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            uint32_t fill = 0, use = 0;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+                const UmTile u = um_tile(G, t0, ng, t);
+                const SplitGemmDesc& g = G[u.pi];
+                const int s = g.s, ckb = max(1, g.chunk / UM_BK);
+                const uint32_t idesc = umma_idesc(UM_BM, UM_BN, g.f16);
+                for (int kb = 0; kb < u.nkb && ok;) {
+                    const uint32_t ab = use & 1;
+                    if (use >= 2) {
+                        ok = mbar_wait(smem_u32(&tempty_b[ab]), ((use >> 1) - 1) & 1);
+                        if (!ok) break;
+                    }
+                    tc_fence_after();
+                    const uint32_t acc = tmem + ab * bufcols;
+                    unsigned started = 0;
+                    const int kend = min(u.nkb, kb + ckb);
+                    for (; kb < kend; kb++, fill++) {
+                        const uint32_t slot = fill % nst;
+                        ok = mbar_wait(smem_u32(&full_b[slot]), (fill / nst) & 1);
+                        if (!ok) break;
+                        tc_fence_after();
+                        const uint32_t a0 = sbase + slot * stage_bytes;
+                        const uint32_t b0 = a0 + (uint32_t)smax * UM_ASLICE;
+                        for (int kk = 0; kk < UM_BK / 16; kk++)
+                            for (int p = 0; p < s; p++)
+                                for (int q = 0; p + q < s; q++) {
+                                    const int L = min(p + q, nacc - 1);
+                                    umma_f16kind(acc + L * UM_BN,
+                                                 umma_desc(a0 + p * UM_ASLICE + kk * 32),
+                                                 umma_desc(b0 + q * UM_BSLICE + kk * 32), idesc,
+                                                 (started >> L) & 1u);
+                                    started |= 1u << L;
+                                }
+                        umma_commit(smem_u32(&empty_b[slot]));   // frees the stage when done
+                    }
+                    if (!ok) break;
+                    umma_commit(smem_u32(&tfull_b[ab]));          // the chunk's sums are ready
+                    use++;
+                }
+            }
+        }
+    } else {
+        // ---------------- drain / epilogue (warps 2..5) ----------------
+        const int quarter = warp & 3;
+        const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
+        uint32_t use = 0;
+        for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+            const UmTile u = um_tile(G, t0, ng, t);
+            const SplitGemmDesc& g = G[u.pi];
+            const int s = g.s, beta = g.beta, ckb = max(1, g.chunk / UM_BK);
+            const int hl = min(s, UM_HI);
+            const int N = g.N;
+            // column metadata of the tile (lane c holds column c), loaded while the
+            // sums are computed and read below by shuffles: no cross-warp sync
+            const int mcol = u.col0 + lane;
+            const int my_ek = mcol < N ? g.eb[mcol] : 0;
+            const int my_cc = mcol < N ? (g.ccol ? g.ccol[mcol] : mcol) : 0;
+            long long ihi[UM_BN];   // sum over levels L < hl of I_L 2^(beta (hl - 1 - L))
+            long long ilo[UM_BN];   // sum over levels L >= hl of I_L 2^(beta (s - 1 - L))
+#pragma unroll
+            for (int c = 0; c < UM_BN; c++) { ihi[c] = 0; ilo[c] = 0; }
+            const int nch = (u.nkb + ckb - 1) / ckb;
+            for (int ci = 0; ci < nch; ci++) {
+                const uint32_t ab = use & 1;
+                ok = mbar_wait(smem_u32(&tfull_b[ab]), (use >> 1) & 1);
+                ok = __all_sync(FULL, ok);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t tb = trow + ab * bufcols;
+#pragma unroll 1
+                for (int L = 0; L < UM_NACC_MAX; L++)
+#pragma unroll
+                    for (int cg = 0; cg < UM_BN / 16; cg++) {
+                        if (L >= s || L >= nacc) continue;   // level L exists only for s > L
+                        float v[16];
+                        tmem_ld16(tb + L * UM_BN + cg * 16, v);
+                        // acc_L = I_L 2^(-beta L) with I_L an integer, |I_L| < 2^24: a 32-bit
+                        // conversion (a 64-bit one issues on the FP64 pipe here)
+                        const float up = __int_as_float((127 + beta * L) << 23);
+                        if (L < hl) {
+                            const int sh = beta * (hl - 1 - L);
+#pragma unroll
+                            for (int c = 0; c < 16; c++)
+                                ihi[cg * 16 + c] += (long long)__float2int_rn(v[c] * up) << sh;
+                        } else {
+                            const int sh = beta * (s - 1 - L);
+#pragma unroll
+                            for (int c = 0; c < 16; c++)
+                                ilo[cg * 16 + c] += (long long)__float2int_rn(v[c] * up) << sh;
+                        }
+                    }
+                tc_fence_before();
+                mbar_arrive(smem_u32(&tempty_b[ab]));   // the buffer may be overwritten
+                use++;
+            }
+            if (!ok) break;
+            // descriptor fields in registers: the output stores below cannot alias them
+            const int M = g.M, ldc = g.ldc;
+            double* __restrict__ const C = g.C;
             const double alpha = g.alpha, betac = g.betac;
-            // uniform per launch: alpha = +-1 is a sign flip, betac = 0 / 1 a store / add
+            const int row = u.row0 + 32 * quarter + lane;
+            const bool rv = row < M;   // every lane runs the loop (shuffles), only valid rows store
+            const int er = (rv ? g.ea[row] : 0) - 2 * beta;
+            // uniform per problem: alpha = +-1 is a sign flip, betac = 0 / 1 a store / add
             const int amode = alpha == 1.0 ? 0 : alpha == -1.0 ? 1 : 2;
             const int bmode = betac == 0.0 ? 0 : betac == 1.0 ? 1 : 2;
-            // both halves in one int64 when it cannot overflow: (ihi << sh) + ilo
             const int shc = beta * (s - hl);
+            const int ncol = min(UM_BN, N - u.col0);
 #pragma unroll
-            for (int c = 0; c < UM_CW; c++) {
-                const int col = col0 + half * UM_CW + c;
-                if (col < N) {
-                    const int k = er + g.eb[col];
-                    const long long h = ihi[c];
-                    double v;
-                    if ((h < 0 ? -h : h) < (1ll << (61 - shc)))
-                        v = i2d_scaled((h << shc) + ilo[c], k - beta * (s - 1));
-                    else
-                        v = i2d_scaled(h, k - beta * (hl - 1)) + i2d_scaled(ilo[c], k - beta * (s - 1));
-                    if (amode == 1) v = -v;
-                    else if (amode == 2) v *= alpha;
-                    double* out = g.C + (size_t)(g.ccol ? g.ccol[col] : col) * g.ldc + row;
-                    if (bmode == 0) *out = v;
-                    else if (bmode == 1) *out += v;
-                    else *out = fma(betac, *out, v);
+            for (int hh = 0; hh < UM_BN / 16; hh++) {
+                double old[16];
+                if (bmode != 0) {
+                    // the previous values, as 16 independent loads
+#pragma unroll
+                    for (int c = 0; c < 16; c++) {
+                        const int cc = hh * 16 + c;
+                        const int oc = __shfl_sync(FULL, my_cc, cc);
+                        old[c] = (rv && cc < ncol) ? C[(size_t)oc * ldc + row] : 0.0;
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 16; c++) {
+                    const int cc = hh * 16 + c;
+                    const int ekc = __shfl_sync(FULL, my_ek, cc);
+                    const int occ = __shfl_sync(FULL, my_cc, cc);
+                    if (rv && cc < ncol) {
+                        const int k = er + ekc;
+                        const long long h = ihi[cc];
+                        double v;
+                        // both halves in one int64 when it cannot overflow: (ihi << shc) + ilo
+                        if ((h < 0 ? -h : h) < (1ll << (61 - shc)))
+                            v = i2d_scaled((h << shc) + ilo[cc], k - beta * (s - 1));
+                        else
+                            v = i2d_scaled(h, k - beta * (hl - 1)) +
+                                i2d_scaled(ilo[cc], k - beta * (s - 1));
+                        if (amode == 1) v = -v;
+                        else if (amode == 2) v *= alpha;
+                        if (bmode == 1) v += old[c];
+                        else if (bmode == 2) v = fma(betac, old[c], v);
+                        C[(size_t)occ * ldc + row] = v;
+                    }
                 }
             }
         }
-    } else if (tid == 0) {
-        atomicOr(status, TD_STATUS_TIMEOUT);
     }
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
-    if (held) {   // no k-block, or a bounded wait expired
-        tc_fence_before();
-        __syncthreads();
-        if (warp == 0)
-            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
-                         "r"(tcols)
-                         : "memory");
-    }
+    if (!ok) atomicOr(status, TD_STATUS_TIMEOUT);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                     "r"(UM_TCOLS)
+                     : "memory");
 }
 
-size_t umma_smem_bytes(int smax, int* nstages)
+size_t umma_smem_bytes(int smax, int ng, int* nstages)
 {
     const size_t stage = (size_t)smax * (UM_ASLICE + UM_BSLICE);
-    const int n = (3 * stage <= 110 * 1024) ? 3 : 2;   // two CTAs per SM
+    const size_t t0b = ng <= UM_T0_SMEM ? (size_t)ng * sizeof(int) : 0;
+    int n = (int)((216 * 1024 - t0b) / stage);
+    n = n < 2 ? 2 : n > UM_MAXST ? UM_MAXST : n;
     if (nstages) *nstages = n;
-    return n * stage + 1024;   // + alignment slack of the dynamic base
+    // + alignment slack; at least 120 KiB so that one CTA (holding all 512 TMEM
+    // columns) is resident per SM
+    const size_t b = n * stage + t0b + 1024;
+    return b < 120 * 1024 ? 120 * 1024 : b;
 }
 
-void umma_launch(const SplitGemmDesc* dev, int ng, int tiles, int smax, int nacc, int* status,
-                 cudaStream_t st)
+void umma_launch(const SplitGemmDesc* dev, const int* tile0, int ng, int tiles, int smax, int nacc,
+                 int* status, cudaStream_t st)
 {
-    nacc = nacc < 2 ? 2 : nacc > UM_NACC_MAX ? UM_NACC_MAX : nacc;
     if (tiles <= 0) return;
+    nacc = nacc < 1 ? 1 : nacc > UM_NACC_MAX ? UM_NACC_MAX : nacc;
     int nst = 0;
-    const size_t smem = umma_smem_bytes(smax, &nst);
+    const size_t smem = umma_smem_bytes(smax, ng, &nst);
     static size_t attr = 0;
+    static int nsm = 0;
+    if (!nsm) {
+        int dev_id = 0;
+        cudaGetDevice(&dev_id);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_id);
+        if (nsm <= 0) nsm = 1;
+    }
     if (smem > attr) {
         cudaFuncSetAttribute(k_split_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = smem;
     }
+    const int grid = tiles < nsm ? tiles : nsm;
     td_prof_begin(st);
-    k_split_umma<<<tiles, UM_NT, smem, st>>>(dev, ng, smax, nst, nacc, status);
+    k_split_umma<<<grid, UM_NT, smem, st>>>(dev, tile0, ng, tiles, smax, nst, nacc, status);
     td_prof_end(st, "k_split_umma");
 }

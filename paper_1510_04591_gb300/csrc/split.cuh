@@ -50,23 +50,28 @@ struct SplitGemmDesc {
     int rsplit, ktop_end, kbot_beg;   // block-structured update: k ranges of the row halves
     int chunk, f16;                   // k-range summed exactly before a drain; FP16 slices
     int tile0, tiles_m;
+    // TMA tensor maps (device CUtensorMap) of the slices: dims (Kp, rows, s),
+    // box (32, 128 | 32, s), 64-byte swizzle
+    const void *tmA, *tmB;
 };
 
 // Tensor-core (tcgen05) slice-pair products: tile 128 x 32 per CTA, one TMEM
 // accumulator per level p + q (at most 8).
 #define UM_BM 128
 #define UM_BN 32
-#define UM_BK 16
+#define UM_BK 32
 
 enum { SPLIT_OZAKI = 0, SPLIT_BF16X2 = 1, SPLIT_FP16X2 = 2 };
 struct SplitPrec {
     int beta, s, chunk, f16, nacc;
 };
 SplitPrec split_prec(int kind, int bits);
-// nacc: TMEM accumulators, one per level p + q (s of them)
-void umma_launch(const SplitGemmDesc* dev, int ng, int tiles, int smax, int nacc, int* status,
-                 cudaStream_t st);
-size_t umma_smem_bytes(int smax, int* nstages);
+// Persistent tcgen05 launch over `tiles` output tiles of ng problems; tile0[i]
+// (device) is the first tile of problem i; nacc: TMEM accumulators, one per
+// level p + q (s of them).
+void umma_launch(const SplitGemmDesc* dev, const int* tile0, int ng, int tiles, int smax, int nacc,
+                 int* status, cudaStream_t st);
+size_t umma_smem_bytes(int smax, int ng, int* nstages);
 
 struct SplitWS {
     char* base = nullptr;

@@ -820,6 +820,16 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
                 kj += kb;
             }
             kj += "}";
+            // launches with a shape note: [ms, note...]
+            std::string lj;
+            for (size_t i = 1; i < g_td_prof.n; i++) {
+                if (!g_td_prof.name[i] || g_td_prof.name[i - 1] || g_td_prof.note[i].empty()) continue;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, g_td_prof.ev[i - 1], g_td_prof.ev[i]);
+                snprintf(kb, sizeof(kb), "%s[\"%s\",%.6f,", lj.empty() ? "" : ",", g_td_prof.name[i], ms);
+                lj += kb + g_td_prof.note[i].substr(1);
+            }
+            if (!lj.empty()) kj += ",\"launch_shapes\":[" + lj + "]";
         }
         snprintf(kb, sizeof(kb), ",\"split_tensor_flops\":%.6e", g_split_tensor_flops - split_flops0);
         kj += kb;

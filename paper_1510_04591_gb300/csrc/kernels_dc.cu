@@ -530,6 +530,21 @@ void td_launch_merge_level(const MergeDesc* M, int nmerge, int nmax, int rows, i
 // when the model step leaves the bracket.  The K-term sums are lane-strided
 // and reduced with warp shuffles.
 // ---------------------------------------------------------------------------
+// 1 / x by Newton-Raphson iteration for the reciprocal (r <- r + r (1 - x r),
+// each step squaring the relative error) from the hardware's approximate FP64
+// reciprocal: two steps take its ~2^-22 seed below 2^-53.  Within a few ulp,
+// not correctly rounded; FP64 divides issue as long instruction sequences on
+// the 1/64-rate FP64 pipe, this is five FP64 instructions.
+__device__ __forceinline__ double td_recip(double x)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+
 __device__ void secular_root_warp(const double* __restrict__ d, const double* __restrict__ w, int K,
                                   int i, int lane, double* lam, double* gam, double* mu, int* iters)
 {
@@ -559,12 +574,12 @@ __device__ void secular_root_warp(const double* __restrict__ d, const double* __
     for (it = 1; it <= TD_SECULAR_MAXIT; it++) {
         double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
         for (int j = lane; j <= i; j += 32) {
-            double q = 1.0 / ((d[j] - dorg) - tau);
+            double q = td_recip((d[j] - dorg) - tau);
             double t = w[j] * q;
             s1 += t; s2 += t * q;
         }
         for (int j = i + 1 + lane; j < K; j += 32) {
-            double q = 1.0 / ((d[j] - dorg) - tau);
+            double q = td_recip((d[j] - dorg) - tau);
             double t = w[j] * q;
             s3 += t; s4 += t * q;
         }

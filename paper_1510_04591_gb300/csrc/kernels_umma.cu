@@ -225,6 +225,53 @@ __device__ __forceinline__ UmTile um_tile(const SplitGemmDesc* G, const int* t0,
 
 #define UM_T0_SMEM 2048   // problems whose first tiles are kept in shared memory
 
+// MMAs of one k-block for S slices: every pair p + q <= S - 1, both k-steps,
+// into the accumulator of its level (levels >= nacc share the last one).
+// Descriptors differ only in their start-address field (the low 14 bits,
+// address >> 4), so they are formed by adding offsets to a base descriptor.
+// `first` (uniform): the k-block starts a chunk, so each level's first MMA
+// overwrites its accumulator.
+template <int S>
+__device__ __forceinline__ void um_issue(uint32_t acc, uint64_t da, uint64_t db, uint32_t idesc,
+                                         int nacc, bool first)
+{
+#pragma unroll
+    for (int kk = 0; kk < UM_BK / 16; kk++)
+#pragma unroll
+        for (int p = 0; p < S; p++)
+#pragma unroll
+            for (int q = 0; p + q < S; q++) {
+                const int L = p + q < nacc ? p + q : nacc - 1;
+                // the level's first pair (p = 0 for levels below nacc) at k-step 0
+                const bool lead = kk == 0 && (p + q < nacc ? p == 0 : (p == 0 && q == nacc - 1));
+                umma_f16kind(acc + L * UM_BN, da + (uint64_t)((p * UM_ASLICE + kk * 32) >> 4),
+                             db + (uint64_t)((q * UM_BSLICE + kk * 32) >> 4), idesc,
+                             (lead && first) ? 0u : 1u);
+            }
+}
+
+__device__ __noinline__ void um_issue_any(int s, uint32_t acc, uint64_t da, uint64_t db,
+                                          uint32_t idesc, int nacc, bool first)
+{
+    switch (s) {
+    case 2: um_issue<2>(acc, da, db, idesc, nacc, first); break;
+    case 6: um_issue<6>(acc, da, db, idesc, nacc, first); break;
+    case 8: um_issue<8>(acc, da, db, idesc, nacc, first); break;
+    default: {
+        // other slice counts (rare): same order, loops not unrolled
+        for (int kk = 0; kk < UM_BK / 16; kk++)
+            for (int p = 0; p < s; p++)
+                for (int q = 0; p + q < s; q++) {
+                    const int L = min(p + q, nacc - 1);
+                    const bool lead = kk == 0 && (p + q < nacc ? p == 0 : (p == 0 && q == nacc - 1));
+                    umma_f16kind(acc + L * UM_BN, da + (uint64_t)((p * UM_ASLICE + kk * 32) >> 4),
+                                 db + (uint64_t)((q * UM_BSLICE + kk * 32) >> 4), idesc,
+                                 (lead && first) ? 0u : 1u);
+                }
+    }
+    }
+}
+
 extern __shared__ __align__(1024) unsigned char um_smem[];
 
 __global__ void __launch_bounds__(UM_NT, 1)
@@ -314,7 +361,7 @@ __global__ void __launch_bounds__(UM_NT, 1)
                     }
                     tc_fence_after();
                     const uint32_t acc = tmem + ab * bufcols;
-                    unsigned started = 0;
+                    const int kstart = kb;
                     const int kend = min(u.nkb, kb + ckb);
                     for (; kb < kend; kb++, fill++) {
                         const uint32_t slot = fill % nst;
@@ -323,16 +370,7 @@ __global__ void __launch_bounds__(UM_NT, 1)
                         tc_fence_after();
                         const uint32_t a0 = sbase + slot * stage_bytes;
                         const uint32_t b0 = a0 + (uint32_t)smax * UM_ASLICE;
-                        for (int kk = 0; kk < UM_BK / 16; kk++)
-                            for (int p = 0; p < s; p++)
-                                for (int q = 0; p + q < s; q++) {
-                                    const int L = min(p + q, nacc - 1);
-                                    umma_f16kind(acc + L * UM_BN,
-                                                 umma_desc(a0 + p * UM_ASLICE + kk * 32),
-                                                 umma_desc(b0 + q * UM_BSLICE + kk * 32), idesc,
-                                                 (started >> L) & 1u);
-                                    started |= 1u << L;
-                                }
+                        um_issue_any(s, acc, umma_desc(a0), umma_desc(b0), idesc, nacc, kb == kstart);
                         umma_commit(smem_u32(&empty_b[slot]));   // frees the stage when done
                     }
                     if (!ok) break;

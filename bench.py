@@ -34,7 +34,6 @@ METRIC = "full eigendecomp time at N=16384: ADC vs plain DC on GB300, orth/resid
 N_SMS = 152
 SM_MHZ = 2070.0
 FP64_FMA_PER_SM_CLK = 2          # measured: FP64 FMA chain throughput 1.19-1.20 TFLOP/s
-MMA_SYNC_BF16_TFLOPS = 600.0     # measured: mma.sync m16n8k16 BF16, register operands
 
 
 def parse():
@@ -152,16 +151,46 @@ def dense_update_flops(st):
 
 
 def grouped_flops(st):
-    """FP64 flops of the grouped products (HSS sampling and construction, and
-    Algorithm 3 when it is not split)."""
+    """FP64 flops of the grouped products (dense fallbacks, FP64 sampling, HSS
+    construction, and Algorithm 3 when it is not split)."""
     fl = 0.0
+    split = st.get("split_tensor_flops", 0.0) > 0.0
     for h in st.get("hss", []):
         f = h.get("flops")
         if f:
-            fl += f["dense"] + f["sample"] + f["build"]
-            if st.get("split_tensor_flops", 0.0) == 0.0:
-                fl += f["mult"]
+            fl += f["build"] + f["sample"]   # "sample" counts FP64 sampling only
+            if not split:
+                fl += f["dense"] + f["mult"]
     return fl
+
+
+FP64_INSTR_PER_SECULAR_TERM = 10   # 2 subtractions, reciprocal (approximation + 4 FMA), mul, add, FMA
+
+
+def kernel_work(name, stats_list, pk):
+    """Algorithmic work of one kernel over the profiled solves: (amount, peak,
+    bound, unit, note), or None."""
+    fp64_peak = N_SMS * SM_MHZ * 1e6 * 2 * FP64_FMA_PER_SM_CLK / 1e12
+    if name == "k_gemm_f64":
+        return (sum(dense_update_flops(s) for s in stats_list) / 1e12, fp64_peak, "alu", "TFLOP/s",
+                "FP64 FMA issue: 152 SMs x 2070 MHz x 2 FMA/clk/SM (measured FMA-chain probe "
+                "1.20 TFLOP/s; cuBLAS DGEMM 1.10)")
+    if name == "k_gemm_grouped":
+        return (sum(grouped_flops(s) for s in stats_list) / 1e12, fp64_peak, "alu", "TFLOP/s",
+                "FP64 FMA issue peak, as for k_gemm_f64")
+    if name == "k_split_umma":
+        peak = pk.get("bf16_tflops", 1900.0)
+        return (sum(s.get("split_tensor_flops", 0.0) for s in stats_list) / 1e12, peak, "tensor",
+                "TFLOP/s", "tensor work issued (2 M N K per slice pair) against the measured bf16 "
+                "peak (cuBLAS burst) %.0f TFLOP/s" % peak)
+    if name == "k_secular":
+        terms = sum(s.get("secular_terms", 0) for s in stats_list)
+        peak = N_SMS * SM_MHZ * 1e6 * 2 / 1e12   # FP64 instructions: 2 lanes/clk/SM
+        return (terms * FP64_INSTR_PER_SECULAR_TERM / 1e12, peak, "alu", "Tinstr/s",
+                "FP64 instruction issue, 152 SMs x 2070 MHz x 2 lanes/clk/SM; %d FP64 "
+                "instructions per secular term evaluated (terms counted on the device)"
+                % FP64_INSTR_PER_SECULAR_TERM)
+    return None
 
 
 def roofline(stats_list, pk):
@@ -174,33 +203,28 @@ def roofline(stats_list, pk):
     if not kern:
         return None
     total = sum(v[0] for v in kern.values())
-    dom = max(kern, key=lambda k: kern[k][0])
+    order = sorted(kern, key=lambda k: -kern[k][0])
+    dom = order[0]
     ms, launches = kern[dom]
-    fp64_peak = N_SMS * SM_MHZ * 1e6 * 2 * FP64_FMA_PER_SM_CLK / 1e12
     res = {"kernel": dom, "share": ms / total, "launches": launches,
            "avg_launch_ms": ms / max(launches, 1),
-           "kernel_share": {k: round(v[0] / total, 4) for k, v in
-                            sorted(kern.items(), key=lambda x: -x[1][0])},
+           "kernel_share": {k: round(kern[k][0] / total, 4) for k in order},
            "traffic": None}
-    fl = None
-    if dom == "k_gemm_f64":
-        fl = sum(dense_update_flops(s) for s in stats_list)
-        peak, bound, note = fp64_peak, "alu", (
-            "FP64 FMA issue: 152 SMs x 2070 MHz x 2 FMA/clk/SM (measured FMA-chain probe "
-            "1.20 TFLOP/s; cuBLAS DGEMM 1.10)")
-    elif dom == "k_gemm_grouped":
-        fl = sum(grouped_flops(s) for s in stats_list)
-        peak, bound, note = fp64_peak, "alu", "FP64 FMA issue peak, as for k_gemm_f64"
-    elif dom == "k_split_gemm":
-        fl = sum(s.get("split_tensor_flops", 0.0) for s in stats_list)
-        peak = pk.get("bf16_tflops", 1900.0)
-        bound, note = "tensor", (
-            "measured bf16 (cuBLAS burst) %.0f TFLOP/s; mma.sync m16n8k16 measured ceiling "
-            "%.0f TFLOP/s" % (peak, MMA_SYNC_BF16_TFLOPS))
-    if fl:
-        ach = fl / (ms / 1e3) / 1e12
-        res.update({"bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "peak_note": note + " (of measured)"})
+    per = []
+    for k in order:
+        w = kernel_work(k, stats_list, pk)
+        if not w or not w[0]:
+            continue
+        amount, peak, bound, unit, note = w
+        ach = amount / (kern[k][0] / 1e3)
+        ent = {"kernel": k, "share": round(kern[k][0] / total, 4), "bound": bound,
+               "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+               "peak_note": note + " (of measured)"}
+        per.append(ent)
+        if k == dom:
+            res.update({kk: ent[kk] for kk in ("bound", "achieved", "peak", "unit", "frac",
+                                               "peak_note")})
+    res["kernels"] = per
     return res
 
 

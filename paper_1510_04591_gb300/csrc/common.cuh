@@ -14,6 +14,8 @@
 #define TD_STATUS_LEAF 2
 #define TD_STATUS_TIMEOUT 4
 #define TD_STATUS_BADRANK 8
+// status[TD_STATUS_SECULAR_TERMS .. +1]: 64-bit count of secular terms evaluated
+#define TD_STATUS_SECULAR_TERMS 2
 
 // One merge of the DC tree (Algorithm 1): the node covers global rows
 // [g0, g0 + n); child 1 is [g0, g0 + n1), child 2 the rest.

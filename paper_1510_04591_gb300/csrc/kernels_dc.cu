@@ -637,6 +637,9 @@ __global__ void k_secular(const MergeDesc* M, int nmerge, int rows, LevelWS ws, 
         ws.gamK[g0 + i] = gam;
         ws.muK[g0 + i] = mu;
         if (it > TD_SECULAR_MAXIT) atomicOr(status, TD_STATUS_NOTCONV);
+        // work count: K terms per evaluation (the start plus every iteration)
+        atomicAdd((unsigned long long*)(status + TD_STATUS_SECULAR_TERMS),
+                  (unsigned long long)(min(it, TD_SECULAR_MAXIT) + 1) * (unsigned long long)K);
     }
 }
 

@@ -761,7 +761,7 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
         if (r && !prc) prc = r;
         return f;
     };
-    double fl_dense = 0.0, fl_sample = 0.0, fl_build = 0.0, fl_mult = 0.0;
+    double fl_dense = 0.0, fl_sample = 0.0, fl_sample_split = 0.0, fl_build = 0.0, fl_mult = 0.0;
     (void)dev_merges;
     const int p_over = opt.oversample;
     std::vector<HMerge> H;
@@ -1039,7 +1039,7 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
     // two-slice variants sample in FP64.
     if (masked) {
         int r = TDEIG_OK;
-        fl_sample += split_launch_gemm(gl, *split, st, &r, status, SPLIT_OZAKI, TD_SAMPLE_BITS);
+        fl_sample_split += split_launch_gemm(gl, *split, st, &r, status, SPLIT_OZAKI, TD_SAMPLE_BITS);
         if (r) return r;
     } else {
         fl_sample += hss_launch_gemm(gl, dgemm, st);
@@ -1369,8 +1369,10 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
 
     // statistics
     char buf[256];
-    snprintf(buf, sizeof(buf), "%s{\"flops\":{\"dense\":%.6e,\"sample\":%.6e,\"build\":%.6e,\"mult\":%.6e}}",
-             js.empty() ? "" : ",", fl_dense, fl_sample, fl_build, fl_mult);
+    snprintf(buf, sizeof(buf),
+             "%s{\"flops\":{\"dense\":%.6e,\"sample\":%.6e,\"sample_split\":%.6e,\"build\":%.6e,"
+             "\"mult\":%.6e}}",
+             js.empty() ? "" : ",", fl_dense, fl_sample, fl_sample_split, fl_build, fl_mult);
     js += buf;
     for (auto& h : H) {
         int kmax = 0;

@@ -765,8 +765,8 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     if (!l_dev) CU(cudaMemcpyAsync(lam_out, B.Lfinal, R * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (Q_out && !q_dev)
         CU(cudaMemcpyAsync(Q_out, B.Qfinal, Qsz * sizeof(double), cudaMemcpyDeviceToHost, st));
-    int hstat[2] = {0, 0};
-    CU(cudaMemcpyAsync(hstat, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    int hstat[4] = {0, 0, 0, 0};
+    CU(cudaMemcpyAsync(hstat, status, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     std::vector<int> kh(std::max<size_t>(ndesc, 1)), gh(2 * std::max<size_t>(ndesc, 1));
     if (ndesc) {
         CU(cudaMemcpyAsync(kh.data(), kstat, ndesc * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -793,6 +793,14 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     h->mlp_fallbacks = learn.fallbacks;
     h->stats = stats_json(h, P, kh, gh, hss_js, secs, hstat[0]);
+    {
+        unsigned long long terms = 0;
+        memcpy(&terms, hstat + TD_STATUS_SECULAR_TERMS, sizeof(terms));
+        char tb[64];
+        snprintf(tb, sizeof(tb), ",\"secular_terms\":%llu}", terms);
+        h->stats.pop_back();
+        h->stats += tb;
+    }
     if (graph) h->stats.insert(1, "\"graph\":\"captured\",");
     {
         // per-kernel device time of a profiled solve: "after" event minus "before"

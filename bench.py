@@ -46,7 +46,7 @@ def parse():
     p.add_argument("--n", type=int, default=16384)
     p.add_argument("--matrix", default="toeplitz", choices=["toeplitz", "random"])
     p.add_argument("--mode", default="adc2", choices=["adc1", "adc2", "dense"])
-    p.add_argument("--prec", default="split", choices=["fp64", "split"])
+    p.add_argument("--prec", default="split", choices=["fp64", "split", "bf16x2", "fp16x2"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-dense-compare", action="store_true")
     p.add_argument("--no-e2e", action="store_true")

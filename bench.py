@@ -428,6 +428,12 @@ def run_batched(args, torch, dist, world, rank, local, dev, stream, solver, flus
         ms.append(e0.elapsed_time(e1))
     ck = clocks.stop()
     v = float(np.mean(ms)) / 1e3
+    stats = None
+    if prof:
+        stats = one(mode | prof)   # one extra, untimed solve with per-kernel events
+        if args.stats_out and rank == 0:
+            with open(args.stats_out, "w") as f:
+                json.dump(stats, f)
     out = {"metric": "batched eigendecomposition time, 4096 uneven tridiagonals", "value": v,
            "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
@@ -435,6 +441,15 @@ def run_batched(args, torch, dist, world, rank, local, dev, stream, solver, flus
            "config": {"workload": workload_name(args), "members": len(sizes),
                       "rows": int(sum(sizes)), "q_entries": int(sum(n * n for n in sizes))},
            "clocks": ck, "matrices_per_s": len(sizes) / v}
+    if stats is not None:
+        ch = stats.get("chunks", [stats])
+        kern = {}
+        for c in ch:
+            for k, kv in c.get("kernels", {}).items():
+                kern[k] = kern.get(k, 0.0) + kv["ms"]
+        tot = sum(kern.values()) or 1.0
+        out["kernel_share_untimed_solve"] = {k: round(t / tot, 4) for k, t in
+                                             sorted(kern.items(), key=lambda x: -x[1])[:10]}
     if rank == 0:
         print(json.dumps(out), flush=True)
     solver.close()

@@ -25,8 +25,8 @@ __device__ __forceinline__ double slice_load(const SliceDesc& d, int r, int k)
 
 __global__ void k_slice_exp(const SliceDesc* D)
 {
-    const SliceDesc d = D[blockIdx.y];
-    const int r0 = blockIdx.x * 32;
+    const SliceDesc d = D[blockIdx.x];   // grid: (operand, 32-row tile)
+    const int r0 = blockIdx.y * 32;
     if (r0 >= d.rows) return;
     __shared__ double red[8][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -75,7 +75,8 @@ __device__ __forceinline__ long long slice_mag(double x, int e, int bs)
     return mant >> (-sh);
 }
 
-// Grid: (64-wide k tile, 64-row tile, operand).  The tile passes through shared
+// Grid: (operand, 64-wide k tile, 64-row tile): the operand count (two per
+// product, one product per merge) may exceed the 65535 limit of y and z.  The tile passes through shared
 // memory (coalesced along whichever dimension of X is contiguous); then each
 // thread turns 8 consecutive k of one row into digits and writes each slice's
 // 8 values with one 16-byte store.  Shared rows hold 8 groups of 8 doubles,
@@ -87,8 +88,8 @@ __device__ __forceinline__ long long slice_mag(double x, int e, int bs)
 #define SL_G 10   // padded group length (doubles)
 __global__ void __launch_bounds__(256) k_slice(const SliceDesc* D)
 {
-    const SliceDesc d = D[blockIdx.z];
-    const int k0 = blockIdx.x * SL_T, r0 = blockIdx.y * SL_T;
+    const SliceDesc d = D[blockIdx.x];   // grid: (operand, 64-wide k tile, 64-row tile)
+    const int k0 = blockIdx.y * SL_T, r0 = blockIdx.z * SL_T;
     if (k0 >= d.Kp || r0 >= d.rows) return;
     __shared__ __align__(16) double T[SL_T][8 * SL_G + 2];   // +2: row stride 164 words
     const int tid = threadIdx.x;
@@ -129,10 +130,13 @@ __global__ void __launch_bounds__(256) k_slice(const SliceDesc* D)
             for (int j = 0; j < 8; j++) {
                 // bits [sh, sh + beta) of the 64-bit magnitude
                 const unsigned w = sh >= 32 ? (mhi[j] >> (sh - 32)) : __funnelshift_r(mlo[j], mhi[j], sh);
+                // the digit as a float without a conversion instruction: 2^23 + t - 2^23
+                const float t = __uint_as_float(0x4B000000u | (w & mask)) - 8388608.0f;
                 // t_p 2^(-beta p): exact in the slice type (beta <= 8 BF16, <= 11 FP16)
-                const float val = sg[j] * (float)(int)(w & mask) * sc;
+                const float val = t * (sg[j] * sc);
+                // at most 8 significant bits: the BF16 pattern is the top half of the FP32 one
                 h[j] = d.f16 ? __half_as_ushort(__float2half_rn(val))
-                             : __bfloat16_as_ushort(__float2bfloat16_rn(val));
+                             : (unsigned short)(__float_as_uint(val) >> 16);
             }
             uint4 w4;
             w4.x = (unsigned)h[0] | ((unsigned)h[1] << 16);
@@ -309,11 +313,11 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
     }
     const unsigned ry = (unsigned)td_cdiv(maxrows, 32);
     td_prof_begin(st);
-    k_slice_exp<<<dim3(ry, (unsigned)sl.size()), 256, 0, st>>>(dsl);
+    k_slice_exp<<<dim3((unsigned)sl.size(), ry), 256, 0, st>>>(dsl);
     td_prof_end(st, "k_slice_exp");
     td_prof_begin(st);
-    k_slice<<<dim3((unsigned)td_cdiv(maxkp, SL_T), (unsigned)td_cdiv(maxrows, SL_T),
-                   (unsigned)sl.size()), 256, 0, st>>>(dsl);
+    k_slice<<<dim3((unsigned)sl.size(), (unsigned)td_cdiv(maxkp, SL_T),
+                   (unsigned)td_cdiv(maxrows, SL_T)), 256, 0, st>>>(dsl);
     td_prof_end(st, "k_slice");
     umma_launch(dsg, dt0, (int)sg.size(), tiles, pr.s, pr.nacc, status, st);
     if (g_td_prof.on) {

@@ -42,6 +42,15 @@ struct LeafDesc {
     const double* scale_ptr;  // the matrix scale if the leaf is the whole matrix, else NULL
     int g0, n;
     int first, last;   // 1 if the leaf starts / ends its matrix (no split correction there)
+    int64_t rot_off;   // first slot of the leaf's rotation buffer
+    int rot_cap;       // its capacity (2 n^2 + 64 rotations)
+};
+
+// Rotations of the leaf QR iterations (phase one -> phase two).
+struct LeafRot {
+    double *c, *s;
+    unsigned char* k;
+    int* n;            // per leaf: rotations recorded (> rot_cap: overflowed)
 };
 
 // Per-level vectors indexed by global row (one entry per row of the level's
@@ -88,7 +97,7 @@ void td_launch_scale_input(const double* d, const double* e, const int64_t* mrow
                            int members, double* A, double* Bc, double* scale, int64_t R,
                            cudaStream_t st);
 void td_launch_leaf(const LeafDesc* leaves, int nleaves, const double* A, const double* Bc,
-                    int* status, cudaStream_t st);
+                    const LeafRot& R, int* status, cudaStream_t st);
 void td_launch_merge_level(const MergeDesc* M, int nmerge, int nmax, int rows, int total_tiles,
                            const LevelWS& ws, int* status, int use_hss_mask, cudaStream_t st);
 void td_launch_secular(const MergeDesc* M, int nmerge, int rows, const LevelWS& ws, int* status,

@@ -3,7 +3,8 @@
 // arithmetic is IEEE FP64.
 //
 //   k_scale_input   scale each matrix by max(|a|, |b|)
-//   k_leaf          QR algorithm with Wilkinson shift on each leaf (warp per leaf)
+//   k_leaf_qr       QR algorithm with Wilkinson shift on each leaf (thread per leaf), rotations recorded
+//   k_leaf_apply    the rotations applied to Q (warp per leaf), eigenpairs sorted
 //   k_prep          eq. T3: u from the children's Q rows; sort; deflation
 //                   (tiny z and close-pole Givens tests); compaction
 //   k_build_w       sorted diag(Q1, Q2) columns
@@ -136,26 +137,34 @@ void td_launch_scale_input(const double* d, const double* e, const int64_t* mrow
 // lane r owns row r of Q, kept in shared memory.
 // ---------------------------------------------------------------------------
 #define LEAF_WARPS 4
-__global__ void __launch_bounds__(32 * LEAF_WARPS) k_leaf(const LeafDesc* L, int nleaves,
-                                                          const double* A, const double* Bc,
-                                                          int* status)
+
+// Implicit symmetric tridiagonal QR with Wilkinson shift on one leaf (Algorithm
+// 1's leaf solver; Golub & Van Loan Sec. 8.3), done in two phases so that the
+// scalar bulge chase is not repeated by every lane of a warp (on this part a
+// warp-wide FP64 instruction costs the FP64 pipe 16 cycles whatever it does):
+//   k_leaf_qr     one thread per leaf: the QR iterations on (a, b), recording
+//                 every Givens rotation (k, c, s) and the unsorted eigenvalues;
+//   k_leaf_apply  one warp per leaf: Q = I, the rotations applied in order (lane
+//                 = row of Q), then the eigenpairs sorted ascending and written.
+// Both take the same operations in the same order as a single-warp solver; a
+// leaf whose rotations exceed its buffer runs the single-warp solver
+// (leaf_solve_warp) in phase two.
+__device__ __forceinline__ void leaf_load(const LeafDesc& lf, const double* A, const double* Bc,
+                                          double* a, double* b)
 {
-    __shared__ double Qs[LEAF_WARPS][32][33];
-    int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int leaf = blockIdx.x * LEAF_WARPS + wib;
-    if (leaf >= nleaves) return;
-    LeafDesc lf = L[leaf];
-    int n = lf.n, g0 = lf.g0;
-    double a[32], b[32];
+    const int n = lf.n, g0 = lf.g0;
     for (int i = 0; i < n; i++) a[i] = A[g0 + i];
     for (int i = 0; i < n - 1; i++) b[i] = Bc[g0 + i];
     if (!lf.first) a[0] -= fabs(Bc[g0 - 1]);
     if (!lf.last) a[n - 1] -= fabs(Bc[g0 + n - 1]);
-    double (*Q)[33] = Qs[wib];
-    for (int c = 0; c < 32; c++) Q[lane][c] = (lane == c) ? 1.0 : 0.0;
-    __syncwarp();
+}
 
-    int sweeps = 0, fail = 0;
+// The QR iterations on (a, b); rot(k, c, s) is called for every rotation in
+// order.  Returns false when the sweep cap is reached.
+template <class Rot>
+__device__ __forceinline__ bool leaf_qr(int n, double* a, double* b, Rot rot)
+{
+    int sweeps = 0;
     int h = n - 1;
     while (h > 0) {
         for (int i = 0; i < h; i++)
@@ -164,7 +173,7 @@ __global__ void __launch_bounds__(32 * LEAF_WARPS) k_leaf(const LeafDesc* L, int
         if (h == 0) break;
         int l = h - 1;
         while (l > 0 && b[l - 1] != 0.0) l--;
-        if (++sweeps > 30 * n) { fail = 1; break; }
+        if (++sweeps > 30 * n) return false;
         double dd = 0.5 * (a[h - 1] - a[h]);
         double bh = b[h - 1];
         double sg = (dd >= 0.0) ? 1.0 : -1.0;
@@ -185,13 +194,17 @@ __global__ void __launch_bounds__(32 * LEAF_WARPS) k_leaf(const LeafDesc* L, int
                 b[k + 1] = c * e;
                 x = b[k];
             }
-            double qk = Q[lane][k], qk1 = Q[lane][k + 1];
-            Q[lane][k] = c * qk - s * qk1;
-            Q[lane][k + 1] = s * qk + c * qk1;
+            rot(k, c, s);
         }
     }
-    if (fail && lane == 0) atomicOr(status, TD_STATUS_LEAF);
-    // selection sort, ascending
+    return true;
+}
+
+// Selection sort of the eigenvalues (ascending) with the matching columns of
+// Q, then the leaf's outputs.  a: eigenvalues (every lane holds a copy).
+__device__ __forceinline__ void leaf_finish(const LeafDesc& lf, double* a, double (*Q)[33], int lane)
+{
+    const int n = lf.n;
     for (int i = 0; i < n - 1; i++) {
         int m = i;
         for (int j = i + 1; j < n; j++) if (a[j] < a[m]) m = j;
@@ -209,11 +222,98 @@ __global__ void __launch_bounds__(32 * LEAF_WARPS) k_leaf(const LeafDesc* L, int
     }
 }
 
+// One leaf by one warp: every lane runs the chase, lane = row of Q.
+__device__ void leaf_solve_warp(const LeafDesc& lf, const double* A, const double* Bc,
+                                double (*Q)[33], int lane, int* status)
+{
+    double a[32], b[32];
+    leaf_load(lf, A, Bc, a, b);
+    for (int c = 0; c < 32; c++) Q[lane][c] = (lane == c) ? 1.0 : 0.0;
+    __syncwarp();
+    const bool ok = leaf_qr(lf.n, a, b, [&](int k, double c, double s) {
+        double qk = Q[lane][k], qk1 = Q[lane][k + 1];
+        Q[lane][k] = c * qk - s * qk1;
+        Q[lane][k + 1] = s * qk + c * qk1;
+    });
+    if (!ok && lane == 0) atomicOr(status, TD_STATUS_LEAF);
+    leaf_finish(lf, a, Q, lane);
+}
+
+__global__ void __launch_bounds__(128) k_leaf_qr(const LeafDesc* L, int nleaves, const double* A,
+                                                 const double* Bc, LeafRot R, int* status)
+{
+    const int leaf = blockIdx.x * blockDim.x + threadIdx.x;
+    if (leaf >= nleaves) return;
+    const LeafDesc lf = L[leaf];
+    double a[32], b[32];
+    leaf_load(lf, A, Bc, a, b);
+    const int64_t off = lf.rot_off;
+    const int cap = lf.rot_cap;
+    int nr = 0;
+    const bool ok = leaf_qr(lf.n, a, b, [&](int k, double c, double s) {
+        if (nr < cap) {
+            R.c[off + nr] = c;
+            R.s[off + nr] = s;
+            R.k[off + nr] = (unsigned char)k;
+        }
+        nr++;
+    });
+    if (!ok) atomicOr(status, TD_STATUS_LEAF);
+    R.n[leaf] = nr;
+    for (int i = 0; i < lf.n; i++) lf.lam_out[i] = a[i];   // unsorted, unscaled
+}
+
+__global__ void __launch_bounds__(32 * LEAF_WARPS) k_leaf_apply(const LeafDesc* L, int nleaves,
+                                                                const double* A, const double* Bc,
+                                                                LeafRot R, int* status)
+{
+    __shared__ double Qs[LEAF_WARPS][32][33];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int leaf = blockIdx.x * LEAF_WARPS + wib;
+    if (leaf >= nleaves) return;
+    const LeafDesc lf = L[leaf];
+    double (*Q)[33] = Qs[wib];
+    const int nr = R.n[leaf];
+    if (nr > lf.rot_cap) {   // rotations did not fit: the single-warp solver
+        leaf_solve_warp(lf, A, Bc, Q, lane, status);
+        return;
+    }
+    for (int c = 0; c < 32; c++) Q[lane][c] = (lane == c) ? 1.0 : 0.0;
+    __syncwarp();
+    // Rotations in chunks of 32, one per lane (coalesced), the next chunk
+    // loaded while the current one is broadcast by shuffles and applied.
+    const int64_t off = lf.rot_off;
+    double cn = 0.0, sn = 0.0;
+    int kn = 0;
+    if (lane < nr) { cn = R.c[off + lane]; sn = R.s[off + lane]; kn = R.k[off + lane]; }
+    for (int r0 = 0; r0 < nr; r0 += 32) {
+        const double cl = cn, sl = sn;
+        const int kl = kn;
+        const int m = min(32, nr - r0);
+        if (r0 + 32 + lane < nr) {
+            cn = R.c[off + r0 + 32 + lane]; sn = R.s[off + r0 + 32 + lane]; kn = R.k[off + r0 + 32 + lane];
+        }
+        for (int j = 0; j < m; j++) {
+            const int k = __shfl_sync(0xffffffffu, kl, j);
+            const double c = __shfl_sync(0xffffffffu, cl, j);
+            const double s = __shfl_sync(0xffffffffu, sl, j);
+            double qk = Q[lane][k], qk1 = Q[lane][k + 1];
+            Q[lane][k] = c * qk - s * qk1;
+            Q[lane][k + 1] = s * qk + c * qk1;
+        }
+    }
+    double a[32];
+    for (int i = 0; i < lf.n; i++) a[i] = lf.lam_out[i];
+    __syncwarp();   // every lane has read the unsorted eigenvalues before they are overwritten
+    leaf_finish(lf, a, Q, lane);
+}
+
 void td_launch_leaf(const LeafDesc* leaves, int nleaves, const double* A, const double* Bc,
-                    int* status, cudaStream_t st)
+                    const LeafRot& R, int* status, cudaStream_t st)
 {
     if (nleaves <= 0) return;
-    td_prof_begin(st); k_leaf<<<td_cdiv(nleaves, LEAF_WARPS), 32 * LEAF_WARPS, 0, st>>>(leaves, nleaves, A, Bc, status); td_prof_end(st, "k_leaf");
+    td_prof_begin(st); k_leaf_qr<<<td_cdiv(nleaves, 128), 128, 0, st>>>(leaves, nleaves, A, Bc, R, status); td_prof_end(st, "k_leaf_qr");
+    td_prof_begin(st); k_leaf_apply<<<td_cdiv(nleaves, LEAF_WARPS), 32 * LEAF_WARPS, 0, st>>>(leaves, nleaves, A, Bc, R, status); td_prof_end(st, "k_leaf_apply");
 }
 
 // ---------------------------------------------------------------------------

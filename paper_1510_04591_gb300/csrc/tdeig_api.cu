@@ -551,6 +551,9 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     bytes += (size_t)batch * (3 * sizeof(int64_t) + sizeof(double));
     bytes += (size_t)(Mmax * 64) * (sizeof(MergeDesc) + (3 + TD_GEMM_VARIANTS) * sizeof(int)) +
              (size_t)leaves_max * sizeof(LeafDesc);
+    // Leaf rotation buffers: 2 n^2 + 64 rotations of 17 bytes per leaf of n <= leaf rows.
+    const int64_t rot_max = 2 * (int64_t)leaf * R + 64 * leaves_max;
+    bytes += (size_t)rot_max * (2 * sizeof(double) + 1) + (size_t)leaves_max * sizeof(int) + 256;
     bytes += 64 * 1024;
     int rc = ensure_ws(h, bytes);
     if (rc) return rc;
@@ -577,6 +580,17 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     carve_level_ws(ar, lws, R, Mmax);
 
     build_plan(P, B, leaf);
+    int64_t rot_total = 0;
+    for (auto& lf : P.leaves) {
+        lf.rot_off = rot_total;
+        lf.rot_cap = 2 * lf.n * lf.n + 64;
+        rot_total += lf.rot_cap;
+    }
+    LeafRot lrot;
+    lrot.c = ar.take<double>(std::max<int64_t>(rot_total, 1));
+    lrot.s = ar.take<double>(std::max<int64_t>(rot_total, 1));
+    lrot.n = ar.take<int>(std::max<size_t>(P.leaves.size(), 1));
+    lrot.k = ar.take<unsigned char>(std::max<int64_t>(rot_total, 1));
     size_t ndesc = 0;
     for (auto& L : P.levels) ndesc += L.merges.size();
     MergeDesc* dev_desc = ar.take<MergeDesc>(std::max<size_t>(ndesc, 1));
@@ -646,7 +660,7 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     td_launch_scale_input(d_st, Esz > 0 ? e_st : nullptr, dev_row0, dev_N, (int)batch, B.A, B.Bc,
                           B.scale, R, st);
     MARK("leaf", -1);
-    td_launch_leaf(dev_leaf, (int)P.leaves.size(), B.A, B.Bc, status, st);
+    td_launch_leaf(dev_leaf, (int)P.leaves.size(), B.A, B.Bc, lrot, status, st);
     CU(cudaGetLastError());
 
     std::string hss_js;

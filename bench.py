@@ -183,6 +183,15 @@ def kernel_work(name, stats_list, pk):
         return (sum(s.get("split_tensor_flops", 0.0) for s in stats_list) / 1e12, peak, "tensor",
                 "TFLOP/s", "tensor work issued (2 M N K per slice pair) against the measured bf16 "
                 "peak (cuBLAS burst) %.0f TFLOP/s" % peak)
+    if name in ("k_slice", "k_slice_exp"):
+        key = "split_slice_bytes" if name == "k_slice" else "split_exp_bytes"
+        peak = pk.get("hbm_gbs", 6800.0)
+        what = ("reads each operand element once (8 B) and writes its s 16-bit slices "
+                "(2 s B per element, k padded to 32)" if name == "k_slice" else
+                "reads each operand element once (8 B) for the row exponents")
+        return (sum(s.get(key, 0.0) for s in stats_list) / 1e9, peak, "hbm", "GB/s",
+                "algorithmic bytes: %s; masked sampling entries counted as read; against the "
+                "measured HBM copy bandwidth %.0f GB/s" % (what, peak))
     if name == "k_secular":
         terms = sum(s.get("secular_terms", 0) for s in stats_list)
         peak = N_SMS * SM_MHZ * 1e6 * 2 / 1e12   # FP64 instructions: 2 lanes/clk/SM

@@ -35,6 +35,12 @@ struct GemmDesc {
     // optional (split products only): entry (r, k) of op(A) is taken as zero when
     // amask[r] == amask[k] (ADC2 sampling of the off-diagonal part of Qhat)
     const int* amask;
+    // optional (split products only): a second term along k, C = alpha (op(A) op(B) +
+    // op(A2) op(B2)) + beta C, op(A2) M x Kd2, op(B2) Kd2 x N (no column gather);
+    // Kd2 = 0: none
+    const double* A2;
+    const double* B2;
+    int Kd2, lda2, ldb2, transA2, transB2;
 };
 
 // out[a + b ld] = uhat[row] v[col] / (d[row] - lambda[col]) (Remark 1), for

@@ -627,8 +627,10 @@ void td_launch_merge_level(const MergeDesc* M, int nmerge, int nmax, int rows, i
 // oracle: origin at the nearer pole (sign of f at the midpoint), unknown
 // tau = lambda - d_origin, two-pole rational model of psi (poles <= i) and phi
 // (poles > i) fitted in value and slope (Bunch, Nielsen & Sorensen), bisection
-// when the model step leaves the bracket.  The K-term sums are lane-strided
-// and reduced with warp shuffles.
+// when the model step leaves the bracket; it starts from the root of a
+// two-pole model built from the midpoint value (the oracle starts at the
+// middle of the bracket).  The K-term sums are lane-strided and reduced with
+// warp shuffles.
 // ---------------------------------------------------------------------------
 // 1 / x by Newton-Raphson iteration for the reciprocal (r <- r + r (1 - x r),
 // each step squaring the relative error) from the hardware's approximate FP64
@@ -645,20 +647,31 @@ __device__ __forceinline__ double td_recip(double x)
     return fma(r, e, r);
 }
 
+// x = m 2^e with m in [1, 2) (sign kept): returns m and adds sgn * e to *ex.
+// Zero (and subnormal) x is returned unchanged.
+__device__ __forceinline__ double td_renorm(double x, int* ex, int sgn)
+{
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0) return x;
+    *ex += sgn * (e - 1023);
+    return __longlong_as_double((b & ~(0x7ffLL << 52)) | (1023LL << 52));
+}
+
 __device__ void secular_root_warp(const double* __restrict__ d, const double* __restrict__ w, int K,
                                   int i, int lane, double* lam, double* gam, double* mu, int* iters)
 {
     if (K == 1) { *lam = d[0] + w[0]; *gam = w[0]; *mu = 0.0; *iters = 0; return; }
     const bool last = (i == K - 1);
     int org;
-    double lo, hi;
+    double lo, hi, fmid = 0.0;
     if (!last) {
         const double di = d[i];
         const double half = 0.5 * (d[i + 1] - di);
         double f = 0.0;
         for (int j = lane; j < K; j += 32) f += w[j] / ((d[j] - di) - half);
-        f = 1.0 + td_warp_sum(f);
-        if (f >= 0.0) { org = i; lo = 0.0; hi = half; }
+        fmid = 1.0 + td_warp_sum(f);
+        if (fmid >= 0.0) { org = i; lo = 0.0; hi = half; }
         else { org = i + 1; lo = -half; hi = 0.0; }
     } else {
         double zz = 0.0;
@@ -670,6 +683,33 @@ __device__ void secular_root_warp(const double* __restrict__ d, const double* __
     const double deli = d[i] - dorg;
     const double deli1 = last ? 0.0 : d[i + 1] - dorg;
     double tau = 0.5 * (lo + hi);
+    if (!last) {
+        // Starting point: the two nearest poles kept exactly and the other terms
+        // frozen at their midpoint value, 1 + c + w_i/(deli - t) + w_i1/(deli1 - t)
+        // = 0, a quadratic a t^2 - b t + c0 = 0 solved for its root in the bracket
+        // (the midpoint is the fallback).  Only the start differs from a midpoint
+        // start; the iteration and its stopping test are unchanged.
+        const double mid = 0.5 * (d[i + 1] - d[i]);   // midpoint offset from d_i
+        const double wi = w[i], wi1 = w[i + 1];
+        const double a = fmid - wi / (-mid) - wi1 / (mid);   // 1 + c
+        const double b = a * (deli + deli1) + wi + wi1;
+        const double c0 = a * deli * deli1 + wi * deli1 + wi1 * deli;
+        const double disc = b * b - 4.0 * a * c0;
+        if (disc >= 0.0) {
+            const double qq = 0.5 * (b + (b >= 0.0 ? sqrt(disc) : -sqrt(disc)));
+            double t0 = 0.5 * (lo + hi);
+            bool got = false;
+            if (qq != 0.0) {
+                const double r1 = c0 / qq;
+                if (r1 > lo && r1 < hi) { t0 = r1; got = true; }
+            }
+            if (!got && a != 0.0) {
+                const double r2 = qq / a;
+                if (r2 > lo && r2 < hi) t0 = r2;
+            }
+            tau = t0;
+        }
+    }
     int it;
     for (it = 1; it <= TD_SECULAR_MAXIT; it++) {
         double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
@@ -770,15 +810,35 @@ __global__ void k_lowner(const MergeDesc* M, int nmerge, int rows, LevelWS ws)
     const double* gam = ws.gamK + g0;
     const double* mu = ws.muK + g0;
     const double di = d[i];
-    double p = 1.0;
+    // Numerators and denominators multiplied separately (one divide per lane
+    // instead of one per term), each brought back to [1, 2) every 4 factors with
+    // its power of two kept in an integer: a factor of the scaled matrix is at
+    // most 8 in magnitude, and 4 of them stay inside the FP64 range unless pole
+    // gaps fall below 1e-75.
+    double pn = 1.0, pd = 1.0;
+    int ex = 0, cnt = 0;
     for (int j = lane; j < K; j += 32) {
         if (j == i) continue;
-        p *= (-td_dminus(d, gam, mu, i, j)) / (d[j] - di);
+        pn *= -td_dminus(d, gam, mu, i, j);   // lambda_j - d_i
+        pd *= d[j] - di;
+        if (++cnt == 4) {
+            cnt = 0;
+            pn = td_renorm(pn, &ex, 1);
+            pd = td_renorm(pd, &ex, -1);
+        }
     }
+    pn = td_renorm(pn, &ex, 1);
+    pd = td_renorm(pd, &ex, -1);
+    double p = pn / pd;   // in (1/2, 2)
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) p *= __shfl_xor_sync(0xffffffffu, p, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        const double q = __shfl_xor_sync(0xffffffffu, p, o);
+        const int eq = __shfl_xor_sync(0xffffffffu, ex, o);
+        p = td_renorm(p * q, &ex, 1);
+        ex += eq;
+    }
     if (lane == 0) {
-        double u = sqrt(gam[i] / ws.rho[m] * p);
+        double u = sqrt(scalbn(gam[i] / ws.rho[m] * p, ex));
         ws.uhat[g0 + i] = copysign(u, ws.zK[g0 + i]);
     }
 }
@@ -814,7 +874,7 @@ __global__ void __launch_bounds__(CAUCHY_NT) k_cauchy(const MergeDesc* M, int nm
     double acc = 0.0;
     for (int p = threadIdx.x; p < K; p += blockDim.x) {
         const int k = perm ? perm[p] : p;
-        double t = uh[k] / td_dminus(d, gam, mu, k, j);
+        double t = uh[k] * td_recip(td_dminus(d, gam, mu, k, j));
         if (SMEM) col[p] = t;
         acc += t * t;
     }
@@ -825,7 +885,7 @@ __global__ void __launch_bounds__(CAUCHY_NT) k_cauchy(const MergeDesc* M, int nm
     double* out = md.qhat + (int64_t)j * K;
     for (int p = threadIdx.x; p < K; p += blockDim.x) {
         const int k = perm ? perm[p] : p;
-        double t = SMEM ? col[p] : uh[k] / td_dminus(d, gam, mu, k, j);
+        double t = SMEM ? col[p] : uh[k] * td_recip(td_dminus(d, gam, mu, k, j));
         out[p] = t * vj;
     }
 }

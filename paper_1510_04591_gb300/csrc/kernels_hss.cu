@@ -1340,7 +1340,13 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
             fl_mult += run(gf, dgemm);
             fl_mult += run(gv, dgemm);
         }
-        // leaves: out[:, t_i] = X_i D_i + F_i V_i^T (columns scattered to their final positions)
+        // leaves: out[:, t_i] = X_i D_i + F_i V_i^T (columns scattered to their final
+        // positions).  Split products take both terms in one product with two terms
+        // along k (one pass over the output; X_i and F_i rows, D_i columns and V_i
+        // rows are of like magnitude, so a shared exponent per row / column costs
+        // little).  The same fusion in the downsweep, F_c = F_p V_p^T + G_j B_j, was
+        // measured (CPU emulation of the digit products) to lose an order of
+        // magnitude: there the two terms' scales differ by up to 2^14.
         std::vector<GemmDesc> gd, gvv;
         for (auto& h : H) {
             for (int q = 0; q < (1 << h.L); q++) {
@@ -1352,18 +1358,25 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
                 g.B = nd.D; g.ldb = h.mcap;
                 g.C = h.qout; g.ldc = h.n; g.ccol = h.posNew + nd.r0;
                 g.M = h.n; g.N = m; g.Kd = m; g.alpha = 1.0;
-                gd.push_back(g);
                 GemmDesc v;
                 memset(&v, 0, sizeof(v));
                 v.A = h.F[h.L] + (size_t)colV(h, h.L, q) * h.n; v.lda = h.n;
                 v.B = nd.V; v.ldb = nd.ldU; v.transB = 1;
                 v.C = h.qout; v.ldc = h.n; v.ccol = h.posNew + nd.r0;
                 v.M = h.n; v.N = m; v.Kd = nd.kV; v.alpha = 1.0; v.beta = 1.0;
-                gvv.push_back(v);
+                if (split) {
+                    g.A2 = v.A; g.lda2 = v.lda;
+                    g.B2 = v.B; g.ldb2 = v.ldb; g.transB2 = 1;
+                    g.Kd2 = v.Kd;
+                    gd.push_back(g);
+                } else {
+                    gd.push_back(g);
+                    gvv.push_back(v);
+                }
             }
         }
         fl_mult += run(gd, dgemm);
-        fl_mult += run(gvv, dgemm);
+        if (!gvv.empty()) fl_mult += run(gvv, dgemm);
     }
     HCU(cudaGetLastError());
 

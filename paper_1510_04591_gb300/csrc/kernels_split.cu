@@ -18,6 +18,7 @@
 
 __device__ __forceinline__ double slice_load(const SliceDesc& d, int r, int k)
 {
+    if (k >= d.K1) return d.X2[r * d.sr2 + (long long)(k - d.K1) * d.sk2];
     if (d.mask && d.mask[r] == d.mask[k]) return 0.0;
     const long long c = d.gk ? d.gk[k] : k;
     return d.X[r * d.sr + c * d.sk];
@@ -152,6 +153,8 @@ __global__ void __launch_bounds__(256) k_slice(const SliceDesc* D)
 // Host side
 // ---------------------------------------------------------------------------
 double g_split_tensor_flops = 0.0;
+double g_split_slice_bytes = 0.0;
+double g_split_exp_bytes = 0.0;
 
 void split_free(SplitWS& w)
 {
@@ -226,15 +229,21 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
     size_t bytes = al256(g.size() * 2 * sizeof(SliceDesc)) + al256(g.size() * sizeof(SplitGemmDesc)) +
                    al256(g.size() * sizeof(int)) + al256(g.size() * 2 * sizeof(CUtensorMap));
     std::vector<int> betas(g.size()), ss(g.size()), kps(g.size());
-    double flops = 0.0, tflops = 0.0;
+    double flops = 0.0, tflops = 0.0, sbytes = 0.0, ebytes = 0.0;
     for (size_t i = 0; i < g.size(); i++) {
         betas[i] = pr.beta;
         ss[i] = pr.s;
-        kps[i] = std::max(32, ((g[i].Kd + 31) / 32) * 32);
+        const int Kt = g[i].Kd + g[i].Kd2;
+        kps[i] = std::max(32, ((Kt + 31) / 32) * 32);
         bytes += al256((size_t)ss[i] * g[i].M * kps[i] * 2) + al256((size_t)ss[i] * g[i].N * kps[i] * 2);
         bytes += al256((size_t)g[i].M * 4) + al256((size_t)g[i].N * 4);
-        flops += 2.0 * g[i].M * g[i].N * g[i].Kd;
-        tflops += 2.0 * g[i].M * g[i].N * g[i].Kd * (ss[i] * (ss[i] + 1) / 2);
+        flops += 2.0 * g[i].M * g[i].N * Kt;
+        tflops += 2.0 * g[i].M * g[i].N * Kt * (ss[i] * (ss[i] + 1) / 2);
+        // algorithmic traffic: every operand element read once by each slicing kernel,
+        // 2 s bytes of slices written per padded element
+        const double elems = (double)(g[i].M + g[i].N) * Kt;
+        sbytes += 8.0 * elems + 2.0 * ss[i] * (double)(g[i].M + g[i].N) * kps[i];
+        ebytes += 8.0 * elems;
     }
     if (bytes > ws.cap) {
         cudaStreamSynchronize(st);
@@ -265,14 +274,24 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
         a.mask = d.amask;
         if (!d.transA) { a.sr = 1; a.sk = d.lda; a.gk = d.acol; }
         else { a.sr = d.lda; a.sk = 1; a.gk = nullptr; }
-        a.rows = d.M; a.K = d.Kd; a.Kp = kps[i]; a.s = ss[i]; a.beta = betas[i]; a.f16 = pr.f16;
+        a.K1 = d.Kd;
+        if (d.Kd2 > 0) {
+            a.X2 = d.A2;
+            if (!d.transA2) { a.sr2 = 1; a.sk2 = d.lda2; } else { a.sr2 = d.lda2; a.sk2 = 1; }
+        }
+        a.rows = d.M; a.K = d.Kd + d.Kd2; a.Kp = kps[i]; a.s = ss[i]; a.beta = betas[i]; a.f16 = pr.f16;
         a.S = (__nv_bfloat16*)take((size_t)ss[i] * d.M * kps[i] * 2);
         a.e = (int*)take((size_t)d.M * 4);
         SliceDesc b;
         memset(&b, 0, sizeof(b));
         b.X = d.B;
         if (!d.transB) { b.sr = d.ldb; b.sk = 1; } else { b.sr = 1; b.sk = d.ldb; }
-        b.rows = d.N; b.K = d.Kd; b.Kp = kps[i]; b.s = ss[i]; b.beta = betas[i]; b.f16 = pr.f16;
+        b.K1 = d.Kd;
+        if (d.Kd2 > 0) {
+            b.X2 = d.B2;
+            if (!d.transB2) { b.sr2 = d.ldb2; b.sk2 = 1; } else { b.sr2 = 1; b.sk2 = d.ldb2; }
+        }
+        b.rows = d.N; b.K = d.Kd + d.Kd2; b.Kp = kps[i]; b.s = ss[i]; b.beta = betas[i]; b.f16 = pr.f16;
         b.S = (__nv_bfloat16*)take((size_t)ss[i] * d.N * kps[i] * 2);
         b.e = (int*)take((size_t)d.N * 4);
         sl.push_back(a);
@@ -330,6 +349,8 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
         td_prof_note(nb);
     }
     g_split_tensor_flops += tflops;
+    g_split_slice_bytes += sbytes;
+    g_split_exp_bytes += ebytes;
     if (cudaGetLastError() != cudaSuccess) *rc = TDEIG_ECUDA;
     return flops;
 }

@@ -24,11 +24,15 @@
 
 #include "hss.cuh"
 
-// element (r, k) of the operand being sliced: X[r*sr + col(k)*sk], col(k) = gk ? gk[k] : k
+// element (r, k) of the operand being sliced: X[r*sr + col(k)*sk], col(k) = gk ? gk[k] : k,
+// for k < K1; X2[r*sr2 + (k - K1)*sk2] for K1 <= k < K (a second term along k)
 struct SliceDesc {
     const double* X;
     const int* gk;
     long long sr, sk;
+    const double* X2;
+    long long sr2, sk2;
+    int K1;
     int rows, K, Kp, s, beta;
     const int* mask;    // optional: entry (r, k) is zero when mask[r] == mask[k]
     int f16;            // slices are FP16 (else BF16)
@@ -88,4 +92,6 @@ double split_launch_gemm(const std::vector<GemmDesc>& g, SplitWS& ws, cudaStream
                          int* status, int kind, int bits);
 // Tensor-core work issued by split products so far: 2 M N K per slice pair.
 extern double g_split_tensor_flops;
+extern double g_split_slice_bytes;   // algorithmic bytes of k_slice (read 8 B, write 2 s B per element)
+extern double g_split_exp_bytes;     // algorithmic bytes of k_slice_exp (read 8 B per element)
 void split_free(SplitWS& ws);

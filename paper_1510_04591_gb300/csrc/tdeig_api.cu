@@ -461,6 +461,7 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     auto t_start = std::chrono::steady_clock::now();
     const long long launches0 = g_td_launches;
     const double split_flops0 = g_split_tensor_flops;
+    const double slice_bytes0 = g_split_slice_bytes, exp_bytes0 = g_split_exp_bytes;
     // per-kernel events only for this solve (see TDEIG_FLAG_PROFILE)
     struct ProfOff {
         ~ProfOff() { g_td_prof.on = false; }
@@ -853,7 +854,9 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
             }
             if (!lj.empty()) kj += ",\"launch_shapes\":[" + lj + "]";
         }
-        snprintf(kb, sizeof(kb), ",\"split_tensor_flops\":%.6e", g_split_tensor_flops - split_flops0);
+        snprintf(kb, sizeof(kb), ",\"split_tensor_flops\":%.6e,\"split_slice_bytes\":%.6e,\"split_exp_bytes\":%.6e",
+                 g_split_tensor_flops - split_flops0, g_split_slice_bytes - slice_bytes0,
+                 g_split_exp_bytes - exp_bytes0);
         kj += kb;
         h->stats.pop_back();
         h->stats += kj + "}";

@@ -594,21 +594,67 @@ __global__ void k_build_w(const MergeDesc* M, LevelWS ws)
 }
 
 // Deflation rotations, in sweep order, one row per thread.
-// Grid: (merge, 128-row tile).
-__global__ void k_rotate(const MergeDesc* M, LevelWS ws)
+// Grid: (merge, 64-row tile).  The sweep visits i in ascending order and
+// rotates it against the last survivor j, so the column i of a rotation has
+// not been touched before and its j is either the previous rotation's i or a
+// column not touched before.  The kernel keeps the latest rotated i column of
+// its row in a register (stored when the chain breaks and at the end), and
+// loads the untouched columns of 16 rotations at a time before applying them:
+// a sequential load/store chain per rotation left it latency-bound.  A column
+// that turns out to have been touched (checked against the running maximum of
+// the columns seen) is read when its rotation is applied instead, so the
+// result does not depend on the sweep's structure.
+#define ROT_B 16
+__global__ void __launch_bounds__(64) k_rotate(const MergeDesc* M, LevelWS ws)
 {
     MergeDesc md = M[blockIdx.x];
     const int nrot = ws.nrot[blockIdx.x];
     const int n = md.n, g0 = md.g0;
     const int r = blockIdx.y * blockDim.x + threadIdx.x;
     if (nrot == 0 || r >= n) return;
-    for (int t = 0; t < nrot; t++) {
-        int j = ws.rot_j[g0 + t], i = ws.rot_i[g0 + t];
-        double c = ws.rot_c[g0 + t], s = ws.rot_s[g0 + t];
-        double qj = md.W[(int64_t)j * n + r], qi = md.W[(int64_t)i * n + r];
-        md.W[(int64_t)j * n + r] = c * qj - s * qi;
-        md.W[(int64_t)i * n + r] = s * qj + c * qi;
+    double* const W = md.W;
+    int cur = -1;          // column whose latest value is held in cv (not yet stored)
+    double cv = 0.0;
+    int mx = -1;           // largest column touched by the rotations seen so far
+    for (int t0 = 0; t0 < nrot; t0 += ROT_B) {
+        int jj[ROT_B], ii[ROT_B];
+        double cc[ROT_B], ss[ROT_B], vj[ROT_B], vi[ROT_B];
+        bool fj[ROT_B], fi[ROT_B];
+#pragma unroll
+        for (int u = 0; u < ROT_B; u++) {
+            const int t = t0 + u;
+            const bool ok = t < nrot;
+            jj[u] = ok ? ws.rot_j[g0 + t] : -1;
+            ii[u] = ok ? ws.rot_i[g0 + t] : -1;
+            cc[u] = ok ? ws.rot_c[g0 + t] : 1.0;
+            ss[u] = ok ? ws.rot_s[g0 + t] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < ROT_B; u++) {
+            // untouched before this rotation: no store to it can precede the load
+            fj[u] = jj[u] > mx;
+            fi[u] = ii[u] > mx && ii[u] != jj[u];
+            mx = max(mx, max(jj[u], ii[u]));
+        }
+#pragma unroll
+        for (int u = 0; u < ROT_B; u++) {
+            vj[u] = (jj[u] >= 0 && fj[u]) ? W[(int64_t)jj[u] * n + r] : 0.0;
+            vi[u] = (ii[u] >= 0 && fi[u]) ? W[(int64_t)ii[u] * n + r] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < ROT_B; u++) {
+            const int j = jj[u], i = ii[u];
+            if (j < 0) continue;
+            if (cur >= 0 && cur != j && cur != i) { W[(int64_t)cur * n + r] = cv; cur = -1; }
+            const double qj = (j == cur) ? cv : fj[u] ? vj[u] : W[(int64_t)j * n + r];
+            const double qi = (i == cur) ? cv : fi[u] ? vi[u] : W[(int64_t)i * n + r];
+            const double c = cc[u], sn = ss[u];
+            W[(int64_t)j * n + r] = c * qj - sn * qi;
+            cur = i;
+            cv = sn * qj + c * qi;
+        }
     }
+    if (cur >= 0) W[(int64_t)cur * n + r] = cv;
 }
 
 void td_launch_merge_level(const MergeDesc* M, int nmerge, int nmax, int rows, int total_tiles,
@@ -618,8 +664,8 @@ void td_launch_merge_level(const MergeDesc* M, int nmerge, int nmax, int rows, i
     td_prof_begin(st); k_prep<<<nmerge, PREP_NT, 0, st>>>(M, ws); td_prof_end(st, "k_prep");
     dim3 gw(nmerge, td_cdiv(nmax, 256), td_cdiv(nmax, 32));
     td_prof_begin(st); k_build_w<<<gw, 256, 0, st>>>(M, ws); td_prof_end(st, "k_build_w");
-    dim3 gr(nmerge, td_cdiv(nmax, 128));
-    td_prof_begin(st); k_rotate<<<gr, 128, 0, st>>>(M, ws); td_prof_end(st, "k_rotate");
+    dim3 gr(nmerge, td_cdiv(nmax, 64));
+    td_prof_begin(st); k_rotate<<<gr, 64, 0, st>>>(M, ws); td_prof_end(st, "k_rotate");
 }
 
 // ---------------------------------------------------------------------------

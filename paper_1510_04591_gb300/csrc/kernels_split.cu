@@ -24,41 +24,63 @@ __device__ __forceinline__ double slice_load(const SliceDesc& d, int r, int k)
     return d.X[r * d.sr + c * d.sk];
 }
 
+// Grid: (operand, 32-row tile, k chunk of SE_K).  Each CTA takes the largest
+// biased exponent field of its rows over its k chunk (integer maxima: FP64
+// max/abs instructions would bind the kernel to the 1/64-rate FP64 pipe) and
+// raises the rows' exponent bounds e (max |x| < 2^e, the field minus 1022) with
+// atomicMax.  The bounds start at a large negative value; a row with no
+// normal entry keeps it, which is harmless: every digit of that row is zero
+// (subnormal entries are sliced as zero).  Eight independent loads per thread
+// are in flight.
+#define SE_K 1024
+__device__ __forceinline__ int exp_field(double x)
+{
+    return (__double2hiint(x) >> 20) & 0x7ff;
+}
+
 __global__ void k_slice_exp(const SliceDesc* D)
 {
-    const SliceDesc d = D[blockIdx.x];   // grid: (operand, 32-row tile)
+    const SliceDesc d = D[blockIdx.x];
     const int r0 = blockIdx.y * 32;
-    if (r0 >= d.rows) return;
-    __shared__ double red[8][33];
+    const int kb = blockIdx.z * SE_K;
+    if (r0 >= d.rows || kb >= d.K) return;
+    const int ke = min(d.K, kb + SE_K);
+    __shared__ int red[8][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    double mx[4] = {0.0, 0.0, 0.0, 0.0};
     if (d.sr == 1) {
         // rows contiguous: lane = row, warps stride over k
         const int r = r0 + tx;
+        int mx = 0;
         if (r < d.rows)
-            for (int k = ty; k < d.K; k += 8) mx[0] = fmax(mx[0], fabs(slice_load(d, r, k)));
-        red[ty][tx] = mx[0];
+            for (int k = kb + ty; k < ke; k += 64) {
+                double v[8];
+#pragma unroll
+                for (int j = 0; j < 8; j++) v[j] = (k + 8 * j < ke) ? slice_load(d, r, k + 8 * j) : 0.0;
+#pragma unroll
+                for (int j = 0; j < 8; j++) mx = max(mx, exp_field(v[j]));
+            }
+        red[ty][tx] = mx;
         __syncthreads();
         if (ty == 0 && r < d.rows) {
-            double m = 0.0;
-            for (int w = 0; w < 8; w++) m = fmax(m, red[w][tx]);
-            int ex = 0;
-            if (m > 0.0) frexp(m, &ex);
-            d.e[r] = ex;
+            int m = 0;
+            for (int w = 0; w < 8; w++) m = max(m, red[w][tx]);
+            if (m > 0) atomicMax(d.e + r, m - 1022);
         }
     } else {
         // k contiguous: lane = k, warp ty handles rows ty, ty+8, ty+16, ty+24
         for (int q = 0; q < 4; q++) {
             const int r = r0 + ty + 8 * q;
-            double m = 0.0;
+            int m = 0;
             if (r < d.rows)
-                for (int k = tx; k < d.K; k += 32) m = fmax(m, fabs(slice_load(d, r, k)));
-            m = td_warp_max(m);
-            if (tx == 0 && r < d.rows) {
-                int ex = 0;
-                if (m > 0.0) frexp(m, &ex);
-                d.e[r] = ex;
-            }
+                for (int k = kb + tx; k < ke; k += 256) {
+                    double v[8];
+#pragma unroll
+                    for (int j = 0; j < 8; j++) v[j] = (k + 32 * j < ke) ? slice_load(d, r, k + 32 * j) : 0.0;
+#pragma unroll
+                    for (int j = 0; j < 8; j++) m = max(m, exp_field(v[j]));
+                }
+            m = __reduce_max_sync(0xffffffffu, m);
+            if (tx == 0 && r < d.rows && m > 0) atomicMax(d.e + r, m - 1022);
         }
     }
 }
@@ -87,20 +109,49 @@ __device__ __forceinline__ long long slice_mag(double x, int e, int bs)
 // magnitude by 32-bit funnel shifts (beta s <= 56 < 64).
 #define SL_T 64
 #define SL_G 10   // padded group length (doubles)
+#define SL_ROW (8 * SL_G + 2)   // +2: row stride 164 words
+
+// The 64 x 64 tile of the operand at (r0, k0) into shared memory, rows of 8
+// padded groups of 8 doubles; all 16 loads of a thread are issued before any
+// shared-memory store.
+__device__ __forceinline__ void slice_tile_load(const SliceDesc& d, double (*T)[SL_ROW], int r0, int k0)
+{
+    const int tid = threadIdx.x;
+    double v[SL_T * SL_T / 256];
+#pragma unroll
+    for (int t = 0; t < SL_T * SL_T / 256; t++) {
+        const int idx = tid + 256 * t;
+        int r, k;
+        if (d.sr == 1) { r = idx % SL_T; k = idx / SL_T; } else { k = idx % SL_T; r = idx / SL_T; }
+        v[t] = (r0 + r < d.rows && k0 + k < d.K) ? slice_load(d, r0 + r, k0 + k) : 0.0;
+    }
+#pragma unroll
+    for (int t = 0; t < SL_T * SL_T / 256; t++) {
+        const int idx = tid + 256 * t;
+        int r, k;
+        if (d.sr == 1) { r = idx % SL_T; k = idx / SL_T; } else { k = idx % SL_T; r = idx / SL_T; }
+        T[r][(k >> 3) * SL_G + (k & 7)] = v[t];
+    }
+}
+
+// Grid: (operand, 64-wide k tile, 64-row tile): the operand count (two per
+// product, one product per merge) may exceed the 65535 limit of y and z.  The
+// tile passes through shared memory (coalesced along whichever dimension of X
+// is contiguous); then each thread turns 8 consecutive k of one row into digits
+// and writes each slice's 8 values with one 16-byte store.  Shared rows hold 8
+// groups of 8 doubles, each group padded to 10 doubles, so a quarter-warp's
+// 16-byte reads of the 8 groups of a row fall in distinct banks (and the row
+// stride of 82 doubles keeps the transposing stores at most 2-way).  Digits
+// come from the 64-bit magnitude by 32-bit funnel shifts (beta s <= 56 < 64).
+// General form (any beta, BF16 or FP16 slices).
 __global__ void __launch_bounds__(256) k_slice(const SliceDesc* D)
 {
     const SliceDesc d = D[blockIdx.x];   // grid: (operand, 64-wide k tile, 64-row tile)
     const int k0 = blockIdx.y * SL_T, r0 = blockIdx.z * SL_T;
     if (k0 >= d.Kp || r0 >= d.rows) return;
-    __shared__ __align__(16) double T[SL_T][8 * SL_G + 2];   // +2: row stride 164 words
+    __shared__ __align__(16) double T[SL_T][SL_ROW];
     const int tid = threadIdx.x;
-    for (int idx = tid; idx < SL_T * SL_T; idx += 256) {
-        int r, k;
-        if (d.sr == 1) { r = idx % SL_T; k = idx / SL_T; } else { k = idx % SL_T; r = idx / SL_T; }
-        double v = 0.0;
-        if (r0 + r < d.rows && k0 + k < d.K) v = slice_load(d, r0 + r, k0 + k);
-        T[r][(k >> 3) * SL_G + (k & 7)] = v;
-    }
+    slice_tile_load(d, T, r0, k0);
     __syncthreads();
     const int bs = d.beta * d.s;
     const unsigned mask = (1u << d.beta) - 1u;
@@ -120,8 +171,9 @@ __global__ void __launch_bounds__(256) k_slice(const SliceDesc* D)
             const long long m0 = slice_mag(x2.x, e, bs), m1 = slice_mag(x2.y, e, bs);
             mlo[2 * j] = (unsigned)m0; mhi[2 * j] = (unsigned)(m0 >> 32);
             mlo[2 * j + 1] = (unsigned)m1; mhi[2 * j + 1] = (unsigned)(m1 >> 32);
-            sg[2 * j] = (x2.x < 0.0) ? -1.0f : 1.0f;
-            sg[2 * j + 1] = (x2.y < 0.0) ? -1.0f : 1.0f;
+            // signs from the bit patterns (an FP64 compare issues on the slow FP64 pipe)
+            sg[2 * j] = (__double2hiint(x2.x) < 0) ? -1.0f : 1.0f;
+            sg[2 * j + 1] = (__double2hiint(x2.y) < 0) ? -1.0f : 1.0f;
         }
         for (int p = 0; p < d.s; p++) {
             const float sc = __int_as_float((127 - d.beta * p) << 23);   // 2^(-beta p), exact
@@ -145,6 +197,65 @@ __global__ void __launch_bounds__(256) k_slice(const SliceDesc* D)
             w4.z = (unsigned)h[4] | ((unsigned)h[5] << 16);
             w4.w = (unsigned)h[6] | ((unsigned)h[7] << 16);
             *(uint4*)(d.S + ((size_t)p * d.rows + row) * d.Kp + kk) = w4;
+        }
+    }
+}
+
+// The 7-bit-digit BF16 form with the slice count fixed at compile time.  Two
+// digits t0, t1 < 128 of neighbouring entries are packed as the BF16 pair
+// (128 + t0, 128 + t1) (bit patterns 0x4300 | t) and turned into
+// (t0, t1) 2^(-7p) by one fma.rn.bf16x2 with the exact constants 2^(-7p) and
+// -128 2^(-7p); the entries' signs are then set by an XOR of the sign bits.
+// Every value is exact, and the slices are bit-identical to the general form's
+// except that a negative zero keeps its sign.
+template <int S>
+__global__ void __launch_bounds__(256, 4) k_slice7(const SliceDesc* D)
+{
+    const SliceDesc d = D[blockIdx.x];
+    const int k0 = blockIdx.y * SL_T, r0 = blockIdx.z * SL_T;
+    if (k0 >= d.Kp || r0 >= d.rows) return;
+    __shared__ __align__(16) double T[SL_T][SL_ROW];
+    const int tid = threadIdx.x;
+    slice_tile_load(d, T, r0, k0);
+    __syncthreads();
+    constexpr int BS = 7 * S;
+#pragma unroll
+    for (int i = 0; i < (SL_T * SL_T / 8) / 256; i++) {
+        const int u = tid + 256 * i;
+        const int r = u / (SL_T / 8), kg = u % (SL_T / 8);
+        const int row = r0 + r, kk = k0 + kg * 8;
+        if (row >= d.rows || kk >= d.Kp) continue;
+        const int e = d.e[row];
+        unsigned long long m[8];
+        unsigned sgn[4];   // sign bits of the pairs at bits 15 and 31
+        const double2* src = (const double2*)&T[r][kg * SL_G];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const double2 x2 = src[j];
+            m[2 * j] = (unsigned long long)slice_mag(x2.x, e, BS);
+            m[2 * j + 1] = (unsigned long long)slice_mag(x2.y, e, BS);
+            sgn[j] = (((unsigned)__double2hiint(x2.x) >> 31) << 15) | ((unsigned)__double2hiint(x2.y) & 0x80000000u);
+        }
+#pragma unroll
+        for (int p = 0; p < S; p++) {
+            const int sh = 7 * (S - 1 - p);
+            const unsigned sc = (unsigned)(127 - 7 * p) << 7;             // BF16 2^(-7p)
+            const unsigned nc = ((unsigned)(134 - 7 * p) << 7) | 0x8000u;  // BF16 -128 2^(-7p)
+            const __nv_bfloat162 sc2 = __halves2bfloat162(__ushort_as_bfloat16((unsigned short)sc),
+                                                          __ushort_as_bfloat16((unsigned short)sc));
+            const __nv_bfloat162 nc2 = __halves2bfloat162(__ushort_as_bfloat16((unsigned short)nc),
+                                                          __ushort_as_bfloat16((unsigned short)nc));
+            unsigned w[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const unsigned d0 = (unsigned)(m[2 * j] >> sh) & 127u;
+                const unsigned d1 = (unsigned)(m[2 * j + 1] >> sh) & 127u;
+                const unsigned pk = d0 | (d1 << 16) | 0x43004300u;
+                __nv_bfloat162 x = *reinterpret_cast<const __nv_bfloat162*>(&pk);
+                x = __hfma2(x, sc2, nc2);
+                w[j] = *reinterpret_cast<const unsigned*>(&x) ^ sgn[j];
+            }
+            *(uint4*)(d.S + ((size_t)p * d.rows + row) * d.Kp + kk) = make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
 }
@@ -236,7 +347,7 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
         const int Kt = g[i].Kd + g[i].Kd2;
         kps[i] = std::max(32, ((Kt + 31) / 32) * 32);
         bytes += al256((size_t)ss[i] * g[i].M * kps[i] * 2) + al256((size_t)ss[i] * g[i].N * kps[i] * 2);
-        bytes += al256((size_t)g[i].M * 4) + al256((size_t)g[i].N * 4);
+        bytes += ((size_t)g[i].M + g[i].N) * 4;
         flops += 2.0 * g[i].M * g[i].N * Kt;
         tflops += 2.0 * g[i].M * g[i].N * Kt * (ss[i] * (ss[i] + 1) / 2);
         // algorithmic traffic: every operand element read once by each slicing kernel,
@@ -258,6 +369,13 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
     }
     char* p = ws.base;
     auto take = [&](size_t n) { char* r = p; p += al256(n); return r; };
+    // exponents of every operand row in one region, filled with 0xC0 bytes
+    // (-1061109568: far below any exponent, and two of them still add without
+    // overflow) before k_slice_exp raises them
+    size_t erows = 0;
+    for (size_t i = 0; i < g.size(); i++) erows += (size_t)g[i].M + g[i].N;
+    int* ebase = (int*)take(erows * 4);
+    size_t eoff = 0;
     SliceDesc* dsl = (SliceDesc*)take(g.size() * 2 * sizeof(SliceDesc));
     SplitGemmDesc* dsg = (SplitGemmDesc*)take(g.size() * sizeof(SplitGemmDesc));
     int* dt0 = (int*)take(g.size() * sizeof(int));
@@ -281,7 +399,8 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
         }
         a.rows = d.M; a.K = d.Kd + d.Kd2; a.Kp = kps[i]; a.s = ss[i]; a.beta = betas[i]; a.f16 = pr.f16;
         a.S = (__nv_bfloat16*)take((size_t)ss[i] * d.M * kps[i] * 2);
-        a.e = (int*)take((size_t)d.M * 4);
+        a.e = ebase + eoff;
+        eoff += d.M;
         SliceDesc b;
         memset(&b, 0, sizeof(b));
         b.X = d.B;
@@ -293,7 +412,8 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
         }
         b.rows = d.N; b.K = d.Kd + d.Kd2; b.Kp = kps[i]; b.s = ss[i]; b.beta = betas[i]; b.f16 = pr.f16;
         b.S = (__nv_bfloat16*)take((size_t)ss[i] * d.N * kps[i] * 2);
-        b.e = (int*)take((size_t)d.N * 4);
+        b.e = ebase + eoff;
+        eoff += d.N;
         sl.push_back(a);
         sl.push_back(b);
         maxrows = std::max(maxrows, std::max(d.M, d.N));
@@ -330,13 +450,30 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
         *rc = TDEIG_ECUDA;
         return 0.0;
     }
+    if (cudaMemsetAsync(ebase, 0xC0, erows * 4, st) != cudaSuccess) {
+        *rc = TDEIG_ECUDA;
+        return 0.0;
+    }
     const unsigned ry = (unsigned)td_cdiv(maxrows, 32);
     td_prof_begin(st);
-    k_slice_exp<<<dim3((unsigned)sl.size(), ry), 256, 0, st>>>(dsl);
+    k_slice_exp<<<dim3((unsigned)sl.size(), ry, (unsigned)td_cdiv(maxkp, SE_K)), 256, 0, st>>>(dsl);
     td_prof_end(st, "k_slice_exp");
+    const dim3 gs((unsigned)sl.size(), (unsigned)td_cdiv(maxkp, SL_T), (unsigned)td_cdiv(maxrows, SL_T));
     td_prof_begin(st);
-    k_slice<<<dim3((unsigned)sl.size(), (unsigned)td_cdiv(maxkp, SL_T),
-                   (unsigned)td_cdiv(maxrows, SL_T)), 256, 0, st>>>(dsl);
+    if (pr.beta == 7 && !pr.f16) {
+        switch (pr.s) {
+        case 1: k_slice7<1><<<gs, 256, 0, st>>>(dsl); break;
+        case 2: k_slice7<2><<<gs, 256, 0, st>>>(dsl); break;
+        case 3: k_slice7<3><<<gs, 256, 0, st>>>(dsl); break;
+        case 4: k_slice7<4><<<gs, 256, 0, st>>>(dsl); break;
+        case 5: k_slice7<5><<<gs, 256, 0, st>>>(dsl); break;
+        case 6: k_slice7<6><<<gs, 256, 0, st>>>(dsl); break;
+        case 7: k_slice7<7><<<gs, 256, 0, st>>>(dsl); break;
+        default: k_slice7<8><<<gs, 256, 0, st>>>(dsl); break;
+        }
+    } else {
+        k_slice<<<gs, 256, 0, st>>>(dsl);
+    }
     td_prof_end(st, "k_slice");
     umma_launch(dsg, dt0, (int)sg.size(), tiles, pr.s, pr.nacc, status, st);
     if (g_td_prof.on) {

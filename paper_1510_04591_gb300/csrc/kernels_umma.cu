@@ -28,7 +28,9 @@
 //     one rounding per add.  Accumulators are double-buffered (two sets of
 //     levels in 512 TMEM columns), so one chunk is drained while the next is
 //     computed;
-//   * warps 2-5 (drain / epilogue, TMEM lane = tile row): after every chunk
+//   * warps 2-9 (drain / epilogue, TMEM lane = tile row, two warps per lane
+//     quarter, 16 columns each: two warps per SM sub-partition hide each
+//     other's latencies in this instruction-bound part): after every chunk
 //     they read the levels with tcgen05.ld and sum them per output entry
 //     exactly as integers (the first UM_HI levels in one int64, the finer ones
 //     in a second, each level shifted by beta relative to the next; a rounded
@@ -45,8 +47,9 @@
 #include "split.cuh"
 
 
-#define UM_NT 192                        // warp 0 loads, warp 1 issues MMAs, warps 2-5 drain and write
-#define UM_EPI 128                       // drain / epilogue threads (one TMEM lane = tile row each)
+#define UM_NT 320                        // warp 0 loads, warp 1 issues MMAs, warps 2-9 drain and write
+#define UM_EPI 256                       // drain / epilogue threads (TMEM lane = tile row, two column halves)
+#define UM_EH 16                         // columns of the tile per epilogue warp
 #define UM_HI 4                          // levels in the first int64 sum (the rest in the second)
 #define UM_MAXST 8                       // shared-memory ring stages
 #define UM_TCOLS 512                     // two accumulator buffers of up to 8 levels x 32 columns
@@ -381,7 +384,10 @@ __global__ void __launch_bounds__(UM_NT, 1)
         }
     } else {
         // ---------------- drain / epilogue (warps 2..5) ----------------
+        // warp w reaches TMEM lanes 32 (w % 4) ... + 31: warps 2..9 cover each
+        // lane quarter twice, the two warps of a quarter taking 16 columns each
         const int quarter = warp & 3;
+        const int cb = UM_EH * ((warp - 2) >> 2);
         const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
         uint32_t use = 0;
         for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
@@ -395,10 +401,10 @@ __global__ void __launch_bounds__(UM_NT, 1)
             const int mcol = u.col0 + lane;
             const int my_ek = mcol < N ? g.eb[mcol] : 0;
             const int my_cc = mcol < N ? (g.ccol ? g.ccol[mcol] : mcol) : 0;
-            long long ihi[UM_BN];   // sum over levels L < hl of I_L 2^(beta (hl - 1 - L))
-            long long ilo[UM_BN];   // sum over levels L >= hl of I_L 2^(beta (s - 1 - L))
+            long long ihi[UM_EH];   // sum over levels L < hl of I_L 2^(beta (hl - 1 - L))
+            long long ilo[UM_EH];   // sum over levels L >= hl of I_L 2^(beta (s - 1 - L))
 #pragma unroll
-            for (int c = 0; c < UM_BN; c++) { ihi[c] = 0; ilo[c] = 0; }
+            for (int c = 0; c < UM_EH; c++) { ihi[c] = 0; ilo[c] = 0; }
             const int nch = (u.nkb + ckb - 1) / ckb;
             for (int ci = 0; ci < nch; ci++) {
                 const uint32_t ab = use & 1;
@@ -408,27 +414,25 @@ __global__ void __launch_bounds__(UM_NT, 1)
                 tc_fence_after();
                 const uint32_t tb = trow + ab * bufcols;
 #pragma unroll 1
-                for (int L = 0; L < UM_NACC_MAX; L++)
+                for (int L = 0; L < UM_NACC_MAX; L++) {
+                    if (L >= s || L >= nacc) break;   // level L exists only for s > L
+                    float v[UM_EH];
+                    tmem_ld16(tb + L * UM_BN + cb, v);
+                    // acc_L = I_L 2^(-beta L) with I_L an integer, |I_L| < 2^24: a 32-bit
+                    // conversion (a 64-bit one issues on the FP64 pipe here)
+                    const float up = __int_as_float((127 + beta * L) << 23);
+                    if (L < hl) {
+                        const int sh = beta * (hl - 1 - L);
 #pragma unroll
-                    for (int cg = 0; cg < UM_BN / 16; cg++) {
-                        if (L >= s || L >= nacc) continue;   // level L exists only for s > L
-                        float v[16];
-                        tmem_ld16(tb + L * UM_BN + cg * 16, v);
-                        // acc_L = I_L 2^(-beta L) with I_L an integer, |I_L| < 2^24: a 32-bit
-                        // conversion (a 64-bit one issues on the FP64 pipe here)
-                        const float up = __int_as_float((127 + beta * L) << 23);
-                        if (L < hl) {
-                            const int sh = beta * (hl - 1 - L);
+                        for (int c = 0; c < UM_EH; c++)
+                            ihi[c] += (long long)__float2int_rn(v[c] * up) << sh;
+                    } else {
+                        const int sh = beta * (s - 1 - L);
 #pragma unroll
-                            for (int c = 0; c < 16; c++)
-                                ihi[cg * 16 + c] += (long long)__float2int_rn(v[c] * up) << sh;
-                        } else {
-                            const int sh = beta * (s - 1 - L);
-#pragma unroll
-                            for (int c = 0; c < 16; c++)
-                                ilo[cg * 16 + c] += (long long)__float2int_rn(v[c] * up) << sh;
-                        }
+                        for (int c = 0; c < UM_EH; c++)
+                            ilo[c] += (long long)__float2int_rn(v[c] * up) << sh;
                     }
+                }
                 tc_fence_before();
                 mbar_arrive(smem_u32(&tempty_b[ab]));   // the buffer may be overwritten
                 use++;
@@ -446,33 +450,32 @@ __global__ void __launch_bounds__(UM_NT, 1)
             const int bmode = betac == 0.0 ? 0 : betac == 1.0 ? 1 : 2;
             const int shc = beta * (s - hl);
             const int ncol = min(UM_BN, N - u.col0);
-#pragma unroll
-            for (int hh = 0; hh < UM_BN / 16; hh++) {
-                double old[16];
+            {
+                double old[UM_EH];
                 if (bmode != 0) {
                     // the previous values, as 16 independent loads
 #pragma unroll
-                    for (int c = 0; c < 16; c++) {
-                        const int cc = hh * 16 + c;
+                    for (int c = 0; c < UM_EH; c++) {
+                        const int cc = cb + c;
                         const int oc = __shfl_sync(FULL, my_cc, cc);
                         old[c] = (rv && cc < ncol) ? C[(size_t)oc * ldc + row] : 0.0;
                     }
                 }
 #pragma unroll
-                for (int c = 0; c < 16; c++) {
-                    const int cc = hh * 16 + c;
+                for (int c = 0; c < UM_EH; c++) {
+                    const int cc = cb + c;
                     const int ekc = __shfl_sync(FULL, my_ek, cc);
                     const int occ = __shfl_sync(FULL, my_cc, cc);
                     if (rv && cc < ncol) {
                         const int k = er + ekc;
-                        const long long h = ihi[cc];
+                        const long long h = ihi[c];
                         double v;
                         // both halves in one int64 when it cannot overflow: (ihi << shc) + ilo
                         if ((h < 0 ? -h : h) < (1ll << (61 - shc)))
-                            v = i2d_scaled((h << shc) + ilo[cc], k - beta * (s - 1));
+                            v = i2d_scaled((h << shc) + ilo[c], k - beta * (s - 1));
                         else
                             v = i2d_scaled(h, k - beta * (hl - 1)) +
-                                i2d_scaled(ilo[cc], k - beta * (s - 1));
+                                i2d_scaled(ilo[c], k - beta * (s - 1));
                         if (amode == 1) v = -v;
                         else if (amode == 2) v *= alpha;
                         if (bmode == 1) v += old[c];

@@ -71,6 +71,8 @@ struct LevelWS {
     int* ordr;         // final ordering of an unsorted merge: rank of each value
     int* unsorted;     // per merge: 1 when the deflated poles are not ascending
     double* rho;       // per merge, after normalisation of z
+    float *dhK, *dlK;  // FP32 pair of dK (dK ~ dhK + dlK, 48 bits) for the FP32 midpoint test
+    float* wfK;        // wK in FP32
 };
 
 // Number of kernels launched by this library (host counter, read per solve).

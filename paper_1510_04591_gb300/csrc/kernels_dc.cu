@@ -522,9 +522,14 @@ __global__ void __launch_bounds__(PREP_NT) k_prep(const MergeDesc* M, LevelWS ws
                 int k = run_k + pre;
                 double zi = ws.zsort[g0 + i];
                 ws.survIdx[g0 + k] = i;
-                ws.dK[g0 + k] = ws.dsort[g0 + i];
+                const double di = ws.dsort[g0 + i], wi = s_rho * zi * zi;
+                ws.dK[g0 + k] = di;
                 ws.zK[g0 + k] = zi;
-                ws.wK[g0 + k] = s_rho * zi * zi;
+                ws.wK[g0 + k] = wi;
+                const float dh = __double2float_rn(di);
+                ws.dhK[g0 + k] = dh;
+                ws.dlK[g0 + k] = __double2float_rn(di - (double)dh);
+                ws.wfK[g0 + k] = __double2float_rn(wi);
             } else {
                 int l = run_d + ((int)threadIdx.x - pre);
                 ws.deflIdx[g0 + l] = i;
@@ -704,14 +709,44 @@ __device__ __forceinline__ double td_renorm(double x, int* ex, int sgn)
     return __longlong_as_double((b & ~(0x7ffLL << 52)) | (1023LL << 52));
 }
 
+__device__ __forceinline__ float td_rcp_f32(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// dh, dl, wf (optional): d as an FP32 pair and w in FP32; with them the
+// midpoint value that picks the origin and seeds the start is taken in FP32
+// (about 1/50 of the cost of an FP64 evaluation here) and the bracket is the
+// whole interval on the origin's side, (0, d_i+1 - d_i) or (-(d_i+1 - d_i), 0):
+// a wrong sign from FP32 rounding can then only choose the farther pole as
+// origin for a root near the midpoint, where either origin is accurate.
 __device__ void secular_root_warp(const double* __restrict__ d, const double* __restrict__ w, int K,
-                                  int i, int lane, double* lam, double* gam, double* mu, int* iters)
+                                  int i, int lane, double* lam, double* gam, double* mu, int* iters,
+                                  const float* __restrict__ dh = nullptr,
+                                  const float* __restrict__ dl = nullptr,
+                                  const float* __restrict__ wf = nullptr)
 {
     if (K == 1) { *lam = d[0] + w[0]; *gam = w[0]; *mu = 0.0; *iters = 0; return; }
     const bool last = (i == K - 1);
     int org;
     double lo, hi, fmid = 0.0;
-    if (!last) {
+    if (!last && dh) {
+        const double gap = d[i + 1] - d[i];
+        const float hf = __double2float_rn(0.5 * gap);
+        const float ohi = dh[i], olo = dl[i];
+        float f = 0.0f;
+        for (int j = lane; j < K; j += 32) {
+            const float del = (dh[j] - ohi) + (dl[j] - olo);   // d_j - d_i
+            f = fmaf(wf[j], td_rcp_f32(del - hf), f);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+        fmid = 1.0 + (double)f;
+        if (fmid >= 0.0) { org = i; lo = 0.0; hi = gap; }
+        else { org = i + 1; lo = -gap; hi = 0.0; }
+    } else if (!last) {
         const double di = d[i];
         const double half = 0.5 * (d[i + 1] - di);
         double f = 0.0;
@@ -817,15 +852,18 @@ __global__ void k_secular(const MergeDesc* M, int nmerge, int rows, LevelWS ws, 
     if (i >= K) return;
     double lam, gam, mu;
     int it;
-    secular_root_warp(ws.dK + g0, ws.wK + g0, K, i, lane, &lam, &gam, &mu, &it);
+    secular_root_warp(ws.dK + g0, ws.wK + g0, K, i, lane, &lam, &gam, &mu, &it, ws.dhK + g0,
+                      ws.dlK + g0, ws.wfK + g0);
     if (lane == 0) {
         ws.lamK[g0 + i] = lam;
         ws.gamK[g0 + i] = gam;
         ws.muK[g0 + i] = mu;
         if (it > TD_SECULAR_MAXIT) atomicOr(status, TD_STATUS_NOTCONV);
-        // work count: K terms per evaluation (the start plus every iteration)
+        // work count: K FP64 terms per evaluation of the iteration (the FP32
+        // midpoint value is not counted; the last root's FP64 start is)
         atomicAdd((unsigned long long*)(status + TD_STATUS_SECULAR_TERMS),
-                  (unsigned long long)(min(it, TD_SECULAR_MAXIT) + 1) * (unsigned long long)K);
+                  (unsigned long long)(min(it, TD_SECULAR_MAXIT) + (i == K - 1 ? 1 : 0)) *
+                      (unsigned long long)K);
     }
 }
 
@@ -1203,7 +1241,12 @@ __global__ void k_stage_init(LevelWS ws, int K, double rho)
     if (i == 0) { ws.K[0] = K; ws.rho[0] = rho; ws.nrot[0] = 0; }
     if (i < K) {
         double z = ws.zK[i];
-        ws.wK[i] = rho * z * z;
+        const double w = rho * z * z, di = ws.dK[i];
+        ws.wK[i] = w;
+        const float dh = __double2float_rn(di);
+        ws.dhK[i] = dh;
+        ws.dlK[i] = __double2float_rn(di - (double)dh);
+        ws.wfK[i] = __double2float_rn(w);
     }
 }
 

@@ -336,8 +336,8 @@ static void build_plan(Plan& P, const Bufs& B, int leaf)
 
 static size_t level_ws_bytes(int64_t R, int64_t Mmax)
 {
-    return (size_t)R * (12 * sizeof(double) + 11 * sizeof(int)) + Mmax * (5 * sizeof(int) + 8) +
-           34 * 256;
+    return (size_t)R * (12 * sizeof(double) + 11 * sizeof(int) + 3 * sizeof(float)) +
+           Mmax * (5 * sizeof(int) + 8) + 37 * 256;
 }
 
 static void carve_level_ws(Arena& a, LevelWS& w, int64_t R, int64_t Mmax)
@@ -370,6 +370,9 @@ static void carve_level_ws(Arena& a, LevelWS& w, int64_t R, int64_t Mmax)
     w.ordr = a.take<int>(R);
     w.unsorted = a.take<int>(Mmax);
     w.rho = a.take<double>(Mmax);
+    w.dhK = a.take<float>(R);
+    w.dlK = a.take<float>(R);
+    w.wfK = a.take<float>(R);
 }
 
 // Statistics of the last solve: per level the merge sizes n, n1, deflated sizes

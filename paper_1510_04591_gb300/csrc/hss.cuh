@@ -60,7 +60,10 @@ struct FillDesc {
 struct IdDesc {
     const double* Phi;
     int ldphi, m, s;
-    const int* rowmap;  // global index of local row a: rowmap ? rowmap[a] : rowbase + a
+    // global index of local row a: rowmap ? (a < n1 ? rowmap[a] : rowmap2[a - n1]) : rowbase + a
+    const int* rowmap;
+    const int* rowmap2;
+    int n1;
     int rowbase;
     double* U;          // m x rank, leading dimension ldu
     int ldu;

@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(HSS_NT) k_id(const IdDesc* D, int nd, double t
     for (int c = tid; c < rank; c += HSS_NT) {
         const int pr = perm[c];
         g.out_piv[c] = pr;
-        g.out_idx[c] = g.rowmap ? g.rowmap[pr] : g.rowbase + pr;
+        g.out_idx[c] = g.rowmap ? (pr < g.n1 ? g.rowmap[pr] : g.rowmap2[pr - g.n1]) : g.rowbase + pr;
     }
     if (tid == 0) *g.out_rank = rank;
 }
@@ -638,6 +638,34 @@ static int grow(HssWS& w, size_t bytes, cudaStream_t st)
 
 // ADC1: HSS generators U, V (and the skeleton indices) level by level by SRRSC;
 // D and B come from the generators as in Algorithm 2.
+// The ranks of tree level l of every merge, one copy (the level's nodes hold
+// consecutive rank pairs), then a synchronisation.
+static int read_level_ranks(std::vector<HMerge>& H, int l, cudaStream_t st)
+{
+    const int* base = nullptr;
+    size_t cnt = 0;
+    for (auto& h : H) {
+        if (l > h.L) continue;
+        if (!base) base = h.nodes[hidx(l, 0)].rk;
+        cnt += (size_t)1 << l;
+    }
+    if (!base) return TDEIG_OK;
+    static thread_local std::vector<int> buf;
+    buf.resize(2 * cnt);
+    HCU(cudaMemcpyAsync(buf.data(), base, 2 * cnt * sizeof(int), cudaMemcpyDeviceToHost, st));
+    HCU(cudaStreamSynchronize(st));
+    size_t i = 0;
+    for (auto& h : H) {
+        if (l > h.L) continue;
+        for (int q = 0; q < (1 << l); q++, i++) {
+            HNode& nd = h.nodes[hidx(l, q)];
+            nd.kU = buf[2 * i];
+            nd.kV = buf[2 * i + 1];
+        }
+    }
+    return TDEIG_OK;
+}
+
 static int srrsc_levels(const tdeig_options& opt, std::vector<HMerge>& H, int Lmax, FillDesc* dfill,
                         SrrscDesc* dsr, char* sr_base, size_t sr_bytes, int* status, cudaStream_t st)
 {
@@ -707,15 +735,8 @@ static int srrsc_levels(const tdeig_options& opt, std::vector<HMerge>& H, int Lm
         k_srrsc<<<(unsigned)sd.size(), SR_NT, 0, st>>>(dsr, opt.tol, status);
         td_prof_end(st, "k_srrsc");
         HCU(cudaGetLastError());
-        for (auto& h : H) {
-            if (l > h.L) continue;
-            for (int q = 0; q < (1 << l); q++) {
-                HNode& nd = h.nodes[hidx(l, q)];
-                HCU(cudaMemcpyAsync(&nd.kU, nd.rk, sizeof(int), cudaMemcpyDeviceToHost, st));
-                HCU(cudaMemcpyAsync(&nd.kV, nd.rk + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-            }
-        }
-        HCU(cudaStreamSynchronize(st));
+        const int rr = read_level_ranks(H, l, st);
+        if (rr) return rr;
     }
     return TDEIG_OK;
 }
@@ -956,7 +977,6 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
                 HNode& nd = h.nodes[hidx(l, q)];
                 nd.I = B.take<int>(s); nd.J = B.take<int>(s);
                 nd.pivI = B.take<int>(s); nd.pivJ = B.take<int>(s);
-                nd.rk = B.take<int>(2);
                 nd.B = B.take<double>((size_t)s * s);
                 if (l == h.L) {
                     nd.r0 = h.bounds[q]; nd.r1 = h.bounds[q + 1];
@@ -983,6 +1003,23 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
             h.G[l] = B.take<double>((size_t)nn * ((size_t)1 << l) * s);
             h.F[l] = B.take<double>((size_t)nn * ((size_t)1 << l) * s);
         }
+    }
+    {
+        // ranks (kU, kV) of every node, level by level, so that one copy per
+        // tree level brings a level's ranks to the host
+        size_t total = 0;
+        int lm = 0;
+        for (auto& h : H) {
+            lm = std::max(lm, h.L);
+            for (int l = 1; l <= h.L; l++) total += (size_t)1 << l;
+        }
+        int* rk_all = B.take<int>(2 * std::max<size_t>(total, 1));
+        size_t idx = 0;
+        for (int l = 1; l <= lm; l++)
+            for (auto& h : H) {
+                if (l > h.L) continue;
+                for (int q = 0; q < (1 << l); q++) h.nodes[hidx(l, q)].rk = rk_all + 2 * idx++;
+            }
     }
     SrrscDesc* dsr = nullptr;
     char* sr_base = nullptr;
@@ -1121,10 +1158,12 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
                     memset(&a, 0, sizeof(a));
                     a.Phi = nd.Phi; a.ldphi = 2 * s; a.m = c1.kU + c2.kU; a.s = s;
                     a.U = nd.U; a.ldu = 2 * s; a.out_idx = nd.I; a.out_piv = nd.pivI; a.out_rank = nd.rk;
-                    a.rowmap = nullptr;
+                    // stacked rows: the children's skeleton rows, c1's then c2's
+                    a.rowmap = c1.I; a.rowmap2 = c2.I; a.n1 = c1.kU;
                     ids.push_back(a);
                     a.Phi = nd.Theta; a.m = c1.kV + c2.kV; a.U = nd.V; a.out_idx = nd.J;
                     a.out_piv = nd.pivJ; a.out_rank = nd.rk + 1;
+                    a.rowmap = c1.J; a.rowmap2 = c2.J; a.n1 = c1.kV;
                     ids.push_back(a);
                 }
             }
@@ -1132,31 +1171,6 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
         launch_fill(fills, dfill, st);
         launch_gather(gathers, dgat, st);
         fl_build += hss_launch_gemm(upd, dgemm, st);
-        // global row maps of the parents' stacked rows: children skeletons
-        {
-            size_t ii = 0;
-            std::vector<int*> maps;
-            for (auto& h : H) {
-                if (l > h.L) continue;
-                for (int q = 0; q < (1 << l); q++) {
-                    if (l == h.L) { ii += 2; continue; }
-                    HNode& nd = h.nodes[hidx(l, q)];
-                    HNode& c1 = h.nodes[hidx(l + 1, 2 * q)];
-                    HNode& c2 = h.nodes[hidx(l + 1, 2 * q + 1)];
-                    int* mi = B.take<int>(2 * h.s);
-                    int* mj = B.take<int>(2 * h.s);
-                    if (B.off > B.cap) return TDEIG_ENOMEM;
-                    HCU(cudaMemcpyAsync(mi, c1.I, c1.kU * sizeof(int), cudaMemcpyDeviceToDevice, st));
-                    HCU(cudaMemcpyAsync(mi + c1.kU, c2.I, c2.kU * sizeof(int), cudaMemcpyDeviceToDevice, st));
-                    HCU(cudaMemcpyAsync(mj, c1.J, c1.kV * sizeof(int), cudaMemcpyDeviceToDevice, st));
-                    HCU(cudaMemcpyAsync(mj + c1.kV, c2.J, c2.kV * sizeof(int), cudaMemcpyDeviceToDevice, st));
-                    ids[ii].rowmap = mi;
-                    ids[ii + 1].rowmap = mj;
-                    (void)nd;
-                    ii += 2;
-                }
-            }
-        }
         if (!ids.empty()) {
             HCU(cudaMemcpyAsync(did, ids.data(), ids.size() * sizeof(IdDesc), cudaMemcpyHostToDevice, st));
             int mmax = 0, smax = 0;
@@ -1173,15 +1187,7 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
             HCU(cudaGetLastError());
         }
         // ranks back to the host
-        for (auto& h : H) {
-            if (l > h.L) continue;
-            for (int q = 0; q < (1 << l); q++) {
-                HNode& nd = h.nodes[hidx(l, q)];
-                HCU(cudaMemcpyAsync(&nd.kU, nd.rk, sizeof(int), cudaMemcpyDeviceToHost, st));
-                HCU(cudaMemcpyAsync(&nd.kV, nd.rk + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-            }
-        }
-        HCU(cudaStreamSynchronize(st));
+        if ((rc = read_level_ranks(H, l, st))) return rc;
         // Yhat_i = V_i^T (Omega_i or stacked children Yhat), Zhat_i = U_i^T (...),
         // stacked into the parent (levels >= 2 only: the root needs no Phi).
         if (l >= 2) {

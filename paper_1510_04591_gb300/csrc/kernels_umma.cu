@@ -213,7 +213,11 @@ __device__ __forceinline__ UmTile um_tile(const SplitGemmDesc* G, const int* t0,
     u.pi = um_problem(t0, ng, t);
     const SplitGemmDesc& g = G[u.pi];
     const int local = t - t0[u.pi];
-    const int tm = local % g.tiles_m, tn = local / g.tiles_m;
+    // column tiles fastest: the CTAs that run at the same time share the row
+    // block of op(A), the larger operand here (M >= N), so it is read from
+    // memory about once and from L2 by the others
+    const int tiles_n = (g.N + UM_BN - 1) / UM_BN;
+    const int tn = local % tiles_n, tm = local / tiles_n;
     u.row0 = tm * UM_BM;
     u.col0 = tn * UM_BN;
     int kb0 = 0, kb1 = g.Kp;

@@ -180,9 +180,20 @@ __device__ __forceinline__ bool leaf_qr(int n, double* a, double* b, Rot rot)
         double mu = a[h] - bh * bh / (dd + sg * hypot(dd, bh));
         double x = a[l] - mu, z = b[l];
         for (int k = l; k < h; k++) {
-            double r = hypot(x, z);
-            double c = 1.0, s = 0.0;
-            if (r != 0.0) { c = x / r; s = -z / r; }
+            // the rotation by one reciprocal square root (a few ulp, like hypot and
+            // two divides, at a third of their FP64 instructions); hypot when the
+            // squares would underflow
+            double r, c = 1.0, s = 0.0;
+            const double r2 = x * x + z * z;
+            if (r2 > 1e-290) {
+                const double inv = rsqrt(r2);
+                r = r2 * inv;
+                c = x * inv;
+                s = -z * inv;
+            } else {
+                r = hypot(x, z);
+                if (r != 0.0) { c = x / r; s = -z / r; }
+            }
             if (k > l) b[k - 1] = r;
             double p = a[k], q = b[k], w = a[k + 1];
             a[k] = c * c * p - 2.0 * c * s * q + s * s * w;
@@ -604,12 +615,65 @@ __global__ void k_build_w(const MergeDesc* M, LevelWS ws)
 // not been touched before and its j is either the previous rotation's i or a
 // column not touched before.  The kernel keeps the latest rotated i column of
 // its row in a register (stored when the chain breaks and at the end), and
-// loads the untouched columns of 16 rotations at a time before applying them:
-// a sequential load/store chain per rotation left it latency-bound.  A column
-// that turns out to have been touched (checked against the running maximum of
-// the columns seen) is read when its rotation is applied instead, so the
-// result does not depend on the sweep's structure.
-#define ROT_B 16
+// loads the untouched columns of the next 8 rotations while it applies the
+// current 8: a sequential load/store chain per rotation left it
+// latency-bound.  A column that turns out to have been touched (checked
+// against the running maximum of the columns seen) is read when its rotation
+// is applied instead.
+// The same structure makes the chains (maximal runs whose j is the previous
+// rotation's i) touch disjoint sets of columns, so they are independent: the
+// rotations are split into ROT_G groups of whole chains (a group starts at the
+// first chain start at or after its even share), each applied by its own CTAs.
+#define ROT_B 8
+#define ROT_G 32
+struct RotBlk {
+    int j[ROT_B], i[ROT_B];
+    double c[ROT_B], s[ROT_B], vj[ROT_B], vi[ROT_B];
+    bool fj[ROT_B], fi[ROT_B];
+};
+
+__device__ __forceinline__ void rot_fetch(RotBlk& b, const LevelWS& ws, int g0, int t0, int nrot,
+                                          int& mx, const double* W, int n, int r)
+{
+#pragma unroll
+    for (int u = 0; u < ROT_B; u++) {
+        const int t = t0 + u;
+        const bool ok = t < nrot;
+        b.j[u] = ok ? ws.rot_j[g0 + t] : -1;
+        b.i[u] = ok ? ws.rot_i[g0 + t] : -1;
+        b.c[u] = ok ? ws.rot_c[g0 + t] : 1.0;
+        b.s[u] = ok ? ws.rot_s[g0 + t] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < ROT_B; u++) {
+        // untouched by every earlier rotation: no store to it can precede the load
+        b.fj[u] = b.j[u] > mx;
+        b.fi[u] = b.i[u] > mx && b.i[u] != b.j[u];
+        mx = max(mx, max(b.j[u], b.i[u]));
+    }
+#pragma unroll
+    for (int u = 0; u < ROT_B; u++) {
+        b.vj[u] = (b.j[u] >= 0 && b.fj[u]) ? W[(int64_t)b.j[u] * n + r] : 0.0;
+        b.vi[u] = (b.i[u] >= 0 && b.fi[u]) ? W[(int64_t)b.i[u] * n + r] : 0.0;
+    }
+}
+
+__device__ __forceinline__ void rot_apply(const RotBlk& b, double* W, int n, int r, int& cur, double& cv)
+{
+#pragma unroll
+    for (int u = 0; u < ROT_B; u++) {
+        const int j = b.j[u], i = b.i[u];
+        if (j < 0) continue;
+        if (cur >= 0 && cur != j && cur != i) { W[(int64_t)cur * n + r] = cv; cur = -1; }
+        const double qj = (j == cur) ? cv : b.fj[u] ? b.vj[u] : W[(int64_t)j * n + r];
+        const double qi = (i == cur) ? cv : b.fi[u] ? b.vi[u] : W[(int64_t)i * n + r];
+        const double c = b.c[u], sn = b.s[u];
+        W[(int64_t)j * n + r] = c * qj - sn * qi;
+        cur = i;
+        cv = sn * qj + c * qi;
+    }
+}
+
 __global__ void __launch_bounds__(64) k_rotate(const MergeDesc* M, LevelWS ws)
 {
     MergeDesc md = M[blockIdx.x];
@@ -617,47 +681,25 @@ __global__ void __launch_bounds__(64) k_rotate(const MergeDesc* M, LevelWS ws)
     const int n = md.n, g0 = md.g0;
     const int r = blockIdx.y * blockDim.x + threadIdx.x;
     if (nrot == 0 || r >= n) return;
+    // this group's whole chains: [tb, te)
+    auto chain_start = [&](int t) { return t == 0 || ws.rot_j[g0 + t] != ws.rot_i[g0 + t - 1]; };
+    int tb = (int)(((int64_t)blockIdx.z * nrot) / ROT_G);
+    int te = (int)(((int64_t)(blockIdx.z + 1) * nrot) / ROT_G);
+    while (tb < nrot && !chain_start(tb)) tb++;
+    while (te < nrot && !chain_start(te)) te++;
+    if (tb >= te) return;
     double* const W = md.W;
     int cur = -1;          // column whose latest value is held in cv (not yet stored)
     double cv = 0.0;
-    int mx = -1;           // largest column touched by the rotations seen so far
-    for (int t0 = 0; t0 < nrot; t0 += ROT_B) {
-        int jj[ROT_B], ii[ROT_B];
-        double cc[ROT_B], ss[ROT_B], vj[ROT_B], vi[ROT_B];
-        bool fj[ROT_B], fi[ROT_B];
-#pragma unroll
-        for (int u = 0; u < ROT_B; u++) {
-            const int t = t0 + u;
-            const bool ok = t < nrot;
-            jj[u] = ok ? ws.rot_j[g0 + t] : -1;
-            ii[u] = ok ? ws.rot_i[g0 + t] : -1;
-            cc[u] = ok ? ws.rot_c[g0 + t] : 1.0;
-            ss[u] = ok ? ws.rot_s[g0 + t] : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < ROT_B; u++) {
-            // untouched before this rotation: no store to it can precede the load
-            fj[u] = jj[u] > mx;
-            fi[u] = ii[u] > mx && ii[u] != jj[u];
-            mx = max(mx, max(jj[u], ii[u]));
-        }
-#pragma unroll
-        for (int u = 0; u < ROT_B; u++) {
-            vj[u] = (jj[u] >= 0 && fj[u]) ? W[(int64_t)jj[u] * n + r] : 0.0;
-            vi[u] = (ii[u] >= 0 && fi[u]) ? W[(int64_t)ii[u] * n + r] : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < ROT_B; u++) {
-            const int j = jj[u], i = ii[u];
-            if (j < 0) continue;
-            if (cur >= 0 && cur != j && cur != i) { W[(int64_t)cur * n + r] = cv; cur = -1; }
-            const double qj = (j == cur) ? cv : fj[u] ? vj[u] : W[(int64_t)j * n + r];
-            const double qi = (i == cur) ? cv : fi[u] ? vi[u] : W[(int64_t)i * n + r];
-            const double c = cc[u], sn = ss[u];
-            W[(int64_t)j * n + r] = c * qj - sn * qi;
-            cur = i;
-            cv = sn * qj + c * qi;
-        }
+    int mx = -1;           // largest column touched by the rotations fetched so far
+    RotBlk A, B;
+    rot_fetch(A, ws, g0, tb, te, mx, W, n, r);
+    for (int t0 = tb; t0 < te; t0 += 2 * ROT_B) {
+        if (t0 + ROT_B < te) rot_fetch(B, ws, g0, t0 + ROT_B, te, mx, W, n, r);
+        rot_apply(A, W, n, r, cur, cv);
+        if (t0 + ROT_B >= te) break;
+        if (t0 + 2 * ROT_B < te) rot_fetch(A, ws, g0, t0 + 2 * ROT_B, te, mx, W, n, r);
+        rot_apply(B, W, n, r, cur, cv);
     }
     if (cur >= 0) W[(int64_t)cur * n + r] = cv;
 }
@@ -669,7 +711,7 @@ void td_launch_merge_level(const MergeDesc* M, int nmerge, int nmax, int rows, i
     td_prof_begin(st); k_prep<<<nmerge, PREP_NT, 0, st>>>(M, ws); td_prof_end(st, "k_prep");
     dim3 gw(nmerge, td_cdiv(nmax, 256), td_cdiv(nmax, 32));
     td_prof_begin(st); k_build_w<<<gw, 256, 0, st>>>(M, ws); td_prof_end(st, "k_build_w");
-    dim3 gr(nmerge, td_cdiv(nmax, 64));
+    dim3 gr(nmerge, td_cdiv(nmax, 64), ROT_G);
     td_prof_begin(st); k_rotate<<<gr, 64, 0, st>>>(M, ws); td_prof_end(st, "k_rotate");
 }
 

@@ -206,15 +206,13 @@ __global__ void __launch_bounds__(HSS_NT) k_id(const IdDesc* D, int nd, double t
     extern __shared__ double sm[];
     __shared__ double redv[HSS_NT / 32];
     __shared__ int redi[HSS_NT / 32];
-    __shared__ double s_norm;
-    __shared__ int s_piv;
     const IdDesc g = D[blockIdx.x];
     const int m = g.m, s = g.s;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     double* A = sm;                       // s x m
-    double* nrm = A + (size_t)s * m;      // m
-    double* vec = nrm + m;                // s
-    int* perm = (int*)(vec + s);          // m
+    double* nrm = A + (size_t)s * m;      // m: squared norm of the rows below the current step
+    double* ref = nrm + m;                // m: that norm when last computed exactly
+    int* perm = (int*)(ref + m);          // m
     for (int t = tid; t < s * m; t += HSS_NT) {
         const int j = t % m, i = t / m;
         A[i * m + j] = g.Phi[j + (int64_t)i * g.ldphi];
@@ -224,9 +222,16 @@ __global__ void __launch_bounds__(HSS_NT) k_id(const IdDesc* D, int nd, double t
         double a = 0.0;
         for (int i = 0; i < s; i++) a += A[i * m + j] * A[i * m + j];
         nrm[j] = a;
+        ref[j] = a;
         perm[j] = j;
     }
     __syncthreads();
+    // Three barriers per step: after the pivot's partial maxima, after the
+    // column swap, after the update.  The remaining column norms are downdated
+    // and, as in LAPACK's xGEQP3, recomputed only when the downdate has fallen
+    // below sqrt(eps) of the last exact value (norms serve the pivot choice
+    // only); the pivot column's norm is always computed exactly, by every warp
+    // in the same order.
     const int kmax = min(s, m);
     double r00 = 0.0;
     int rank = kmax;
@@ -244,17 +249,12 @@ __global__ void __launch_bounds__(HSS_NT) k_id(const IdDesc* D, int nd, double t
         }
         if (lane == 0) { redv[wid] = best; redi[wid] = bi; }
         __syncthreads();
-        if (tid == 0) {
-            double b = -1.0;
-            int ib = k;
-            for (int w = 0; w < HSS_NT / 32; w++)
-                if (redv[w] > b || (redv[w] == b && redi[w] < ib)) { b = redv[w]; ib = redi[w]; }
-            s_piv = ib;
-        }
-        __syncthreads();
-        const int p = s_piv;
-        if (k == 0) r00 = sqrt(nrm[p]);
-        __syncthreads();
+        best = redv[0];
+        bi = redi[0];
+        for (int w = 1; w < HSS_NT / 32; w++)
+            if (redv[w] > best || (redv[w] == best && redi[w] < bi)) { best = redv[w]; bi = redi[w]; }
+        const int p = bi;
+        if (k == 0) r00 = sqrt(best);   // the exact norm of the first pivot column
         if (r00 == 0.0) { rank = 0; break; }
         if (p != k) {
             for (int i = tid; i < s; i += HSS_NT) {
@@ -262,40 +262,38 @@ __global__ void __launch_bounds__(HSS_NT) k_id(const IdDesc* D, int nd, double t
             }
             if (tid == 0) {
                 double t = nrm[k]; nrm[k] = nrm[p]; nrm[p] = t;
+                t = ref[k]; ref[k] = ref[p]; ref[p] = t;
                 int u = perm[k]; perm[k] = perm[p]; perm[p] = u;
             }
         }
         __syncthreads();
-        if (wid == 0) {
-            double a = 0.0;
-            for (int i = k + lane; i < s; i += 32) a += A[i * m + k] * A[i * m + k];
-            a = td_warp_sum(a);
-            if (lane == 0) s_norm = sqrt(a);
-        }
-        __syncthreads();
-        const double xn = s_norm;
+        double a = 0.0;
+        for (int i = k + lane; i < s; i += 32) a += A[i * m + k] * A[i * m + k];
+        const double xn = sqrt(td_warp_sum(a));
         if (xn <= tol * r00) { rank = k; break; }
         const double x0 = A[k * m + k];
         const double alpha = (x0 >= 0.0) ? -xn : xn;
         const double beta = 1.0 / (alpha * (alpha - x0));
-        for (int i = k + tid; i < s; i += HSS_NT) vec[i] = (i == k) ? x0 - alpha : A[i * m + k];
-        __syncthreads();
+        const double v0 = x0 - alpha;   // Householder vector: (v0, A[k+1.., k])
         for (int j = k + 1 + tid; j < m; j += HSS_NT) {
-            double dot = 0.0;
-            for (int i = k; i < s; i++) dot += vec[i] * A[i * m + j];
+            double dot = v0 * A[k * m + j];
+            for (int i = k + 1; i < s; i++) dot += A[i * m + k] * A[i * m + j];
             const double f = beta * dot;
-            double nn = 0.0;
-            for (int i = k; i < s; i++) {
-                double a = A[i * m + j] - f * vec[i];
-                A[i * m + j] = a;
-                if (i > k) nn += a * a;
+            const double akj = A[k * m + j] - f * v0;
+            A[k * m + j] = akj;
+            for (int i = k + 1; i < s; i++) A[i * m + j] -= f * A[i * m + k];
+            double nn = nrm[j] - akj * akj;
+            if (!(nn > 1.4901161193847656e-8 * ref[j])) {   // sqrt(2^-52)
+                nn = 0.0;
+                for (int i = k + 1; i < s; i++) nn += A[i * m + j] * A[i * m + j];
+                ref[j] = nn;
             }
             nrm[j] = nn;
         }
         __syncthreads();
-        if (tid == 0) A[k * m + k] = alpha;
-        __syncthreads();
+        if (tid == 0) A[k * m + k] = alpha;   // column k is read by no one until the end
     }
+    __syncthreads();
     // T = R11^{-1} R12 in place (columns rank..m-1), back substitution
     for (int j = rank + tid; j < m; j += HSS_NT) {
         for (int i = rank - 1; i >= 0; i--) {
@@ -318,7 +316,7 @@ __global__ void __launch_bounds__(HSS_NT) k_id(const IdDesc* D, int nd, double t
     if (tid == 0) *g.out_rank = rank;
 }
 
-static size_t id_smem(int s, int m) { return (size_t)s * m * 8 + (size_t)m * 12 + (size_t)s * 8 + 64; }
+static size_t id_smem(int s, int m) { return (size_t)s * m * 8 + (size_t)m * 20 + (size_t)s * 8 + 64; }
 
 // ---------------------------------------------------------------------------
 // Gaussian sampling matrix: Omega[i, j] from Philox4x32-10 (Salmon, Moraes,

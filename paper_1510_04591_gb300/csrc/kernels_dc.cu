@@ -805,8 +805,11 @@ __device__ void secular_root_warp(const double* __restrict__ d, const double* __
     const double dorg = d[org];
     const double deli = d[i] - dorg;
     const double deli1 = last ? 0.0 : d[i + 1] - dorg;
+    // The scalar work of the iteration (start, stopping tests, model step) is
+    // done by lane 0 alone and the new tau and the decision broadcast: repeated
+    // by 32 lanes it cost as much FP64 issue as the sums of a small merge.
     double tau = 0.5 * (lo + hi);
-    if (!last) {
+    if (!last && lane == 0) {
         // Starting point: the two nearest poles kept exactly and the other terms
         // frozen at their midpoint value, 1 + c + w_i/(deli - t) + w_i1/(deli1 - t)
         // = 0, a quadratic a t^2 - b t + c0 = 0 solved for its root in the bracket
@@ -833,6 +836,7 @@ __device__ void secular_root_warp(const double* __restrict__ d, const double* __
             tau = t0;
         }
     }
+    tau = __shfl_sync(0xffffffffu, tau, 0);
     int it;
     for (it = 1; it <= TD_SECULAR_MAXIT; it++) {
         double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
@@ -848,31 +852,42 @@ __device__ void secular_root_warp(const double* __restrict__ d, const double* __
         }
         const double psi = td_warp_sum(s1), dpsi = td_warp_sum(s2);
         const double phi = td_warp_sum(s3), dphi = td_warp_sum(s4);
-        const double f = 1.0 + psi + phi;
-        const double err = 8.0 * TD_EPS * (1.0 + fabs(psi) + fabs(phi) + fabs(tau) * (dpsi + dphi));
-        if (fabs(f) <= err) break;
-        if (f > 0.0) hi = tau; else lo = tau;
-        if (hi - lo <= 4.0 * TD_EPS * fmax(fabs(lo), fabs(hi))) break;
-        const double a1 = deli - tau;
-        double step = 0.0;
-        bool ok = true;
-        if (!last) {
-            const double a2 = deli1 - tau;
-            const double E = f - dpsi * a1 - dphi * a2;
-            const double beta = E * (a1 + a2) + dpsi * a1 * a1 + dphi * a2 * a2;
-            const double c0 = a1 * a2 * f;
-            double disc = beta * beta - 4.0 * E * c0;
-            if (disc < 0.0) disc = 0.0;
-            const double den = beta + (beta >= 0.0 ? sqrt(disc) : -sqrt(disc));
-            if (den == 0.0) ok = false; else step = 2.0 * c0 / den;
-        } else {
-            const double E = f - dpsi * a1;
-            if (E == 0.0) ok = false; else step = a1 * f / E;
+        int stop = 0;
+        double nt = tau;
+        if (lane == 0) {
+            const double f = 1.0 + psi + phi;
+            const double err = 8.0 * TD_EPS * (1.0 + fabs(psi) + fabs(phi) + fabs(tau) * (dpsi + dphi));
+            if (fabs(f) <= err) {
+                stop = 1;
+            } else {
+                if (f > 0.0) hi = tau; else lo = tau;
+                if (hi - lo <= 4.0 * TD_EPS * fmax(fabs(lo), fabs(hi))) {
+                    stop = 1;
+                } else {
+                    const double a1 = deli - tau;
+                    double step = 0.0;
+                    bool ok = true;
+                    if (!last) {
+                        const double a2 = deli1 - tau;
+                        const double E = f - dpsi * a1 - dphi * a2;
+                        const double beta = E * (a1 + a2) + dpsi * a1 * a1 + dphi * a2 * a2;
+                        const double c0 = a1 * a2 * f;
+                        double disc = beta * beta - 4.0 * E * c0;
+                        if (disc < 0.0) disc = 0.0;
+                        const double den = beta + (beta >= 0.0 ? sqrt(disc) : -sqrt(disc));
+                        if (den == 0.0) ok = false; else step = 2.0 * c0 / den;
+                    } else {
+                        const double E = f - dpsi * a1;
+                        if (E == 0.0) ok = false; else step = a1 * f / E;
+                    }
+                    nt = ok ? tau + step : 0.5 * (lo + hi);
+                    if (!(nt > lo && nt < hi)) nt = 0.5 * (lo + hi);
+                    if (nt == tau) stop = 1;
+                }
+            }
         }
-        double nt = ok ? tau + step : 0.5 * (lo + hi);
-        if (!(nt > lo && nt < hi)) nt = 0.5 * (lo + hi);
-        if (nt == tau) break;
-        tau = nt;
+        if (__shfl_sync(0xffffffffu, stop, 0)) break;
+        tau = __shfl_sync(0xffffffffu, nt, 0);
     }
     *lam = dorg + tau;
     if (last) { *gam = tau; *mu = 0.0; }
@@ -1005,8 +1020,15 @@ __global__ void __launch_bounds__(CAUCHY_NT) k_cauchy(const MergeDesc* M, int nm
         acc += t * t;
     }
     acc = blk_sum(acc, red);
-    const double vj = 1.0 / sqrt(acc);
-    if (threadIdx.x == 0) ws.vv[g0 + j] = vj;
+    // one thread takes the FP64 square root and divide (all 256 repeating it
+    // cost the 1/64-rate FP64 pipe a sizeable share of a small column)
+    __shared__ double s_vj;
+    if (threadIdx.x == 0) {
+        s_vj = 1.0 / sqrt(acc);
+        ws.vv[g0 + j] = s_vj;
+    }
+    __syncthreads();
+    const double vj = s_vj;
     if (!write_qhat) return;
     double* out = md.qhat + (int64_t)j * K;
     for (int p = threadIdx.x; p < K; p += blockDim.x) {

@@ -204,7 +204,7 @@ static void launch_gather(const std::vector<GatherDesc>& G, GatherDesc* dev, cud
 __global__ void __launch_bounds__(HSS_NT) k_id(const IdDesc* D, int nd, double tol)
 {
     extern __shared__ double sm[];
-    __shared__ double redv[HSS_NT / 32];
+    __shared__ long long redb[HSS_NT / 32];
     __shared__ int redi[HSS_NT / 32];
     const IdDesc g = D[blockIdx.x];
     const int m = g.m, s = g.s;
@@ -226,36 +226,46 @@ __global__ void __launch_bounds__(HSS_NT) k_id(const IdDesc* D, int nd, double t
         perm[j] = j;
     }
     __syncthreads();
-    // Three barriers per step: after the pivot's partial maxima, after the
-    // column swap, after the update.  The remaining column norms are downdated
-    // and, as in LAPACK's xGEQP3, recomputed only when the downdate has fallen
-    // below sqrt(eps) of the last exact value (norms serve the pivot choice
-    // only); the pivot column's norm is always computed exactly, by every warp
-    // in the same order.
+    // Four barriers per step: after the pivot's partial maxima, after the
+    // column swap, after the Householder scalars, after the update.  Scalar
+    // FP64 work (the pivot column's norm, square root, divide) is done by one
+    // warp and shared through shared memory: repeated by all 256 threads it
+    // cost several times the update itself on the 1/64-rate FP64 pipe, and the
+    // pivot search compares the non-negative norms as integers for the same
+    // reason.  The remaining column norms are downdated and, as in LAPACK's
+    // xGEQP3, recomputed only when the downdate has fallen below sqrt(eps) of
+    // the last exact value (norms serve the pivot choice only); the pivot
+    // column's norm is always computed exactly.
+    __shared__ double s_par[3];
+    __shared__ int s_stop;
     const int kmax = min(s, m);
     double r00 = 0.0;
     int rank = kmax;
     for (int k = 0; k < kmax; k++) {
         // pivot: largest remaining column norm, lowest index on ties
-        double best = -1.0;
+        long long best = -1;
         int bi = k;
-        for (int j = k + tid; j < m; j += HSS_NT)
-            if (nrm[j] > best) { best = nrm[j]; bi = j; }
+        for (int j = k + tid; j < m; j += HSS_NT) {
+            const long long v = __double_as_longlong(nrm[j]);
+            if (v > best) { best = v; bi = j; }
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            double ob = __shfl_xor_sync(0xffffffffu, best, o);
-            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
             if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
-        if (lane == 0) { redv[wid] = best; redi[wid] = bi; }
+        if (lane == 0) { redb[wid] = best; redi[wid] = bi; }
         __syncthreads();
-        best = redv[0];
+        best = redb[0];
         bi = redi[0];
         for (int w = 1; w < HSS_NT / 32; w++)
-            if (redv[w] > best || (redv[w] == best && redi[w] < bi)) { best = redv[w]; bi = redi[w]; }
+            if (redb[w] > best || (redb[w] == best && redi[w] < bi)) { best = redb[w]; bi = redi[w]; }
         const int p = bi;
-        if (k == 0) r00 = sqrt(best);   // the exact norm of the first pivot column
-        if (r00 == 0.0) { rank = 0; break; }
+        if (k == 0) {
+            if (best <= 0) { rank = 0; break; }   // zero matrix
+            if (tid == 0) r00 = sqrt(__longlong_as_double(best));   // exact first pivot norm
+        }
         if (p != k) {
             for (int i = tid; i < s; i += HSS_NT) {
                 double t = A[i * m + k]; A[i * m + k] = A[i * m + p]; A[i * m + p] = t;
@@ -267,14 +277,23 @@ __global__ void __launch_bounds__(HSS_NT) k_id(const IdDesc* D, int nd, double t
             }
         }
         __syncthreads();
-        double a = 0.0;
-        for (int i = k + lane; i < s; i += 32) a += A[i * m + k] * A[i * m + k];
-        const double xn = sqrt(td_warp_sum(a));
-        if (xn <= tol * r00) { rank = k; break; }
-        const double x0 = A[k * m + k];
-        const double alpha = (x0 >= 0.0) ? -xn : xn;
-        const double beta = 1.0 / (alpha * (alpha - x0));
-        const double v0 = x0 - alpha;   // Householder vector: (v0, A[k+1.., k])
+        if (wid == 0) {
+            double a = 0.0;
+            for (int i = k + lane; i < s; i += 32) a += A[i * m + k] * A[i * m + k];
+            a = td_warp_sum(a);
+            if (lane == 0) {
+                const double xn = sqrt(a);
+                const double x0 = A[k * m + k];
+                const double alpha = (x0 >= 0.0) ? -xn : xn;
+                s_stop = xn <= tol * r00;
+                s_par[0] = 1.0 / (alpha * (alpha - x0));   // beta
+                s_par[1] = x0 - alpha;                     // first entry of the Householder vector
+                s_par[2] = alpha;
+            }
+        }
+        __syncthreads();
+        if (s_stop) { rank = k; break; }
+        const double beta = s_par[0], v0 = s_par[1];
         for (int j = k + 1 + tid; j < m; j += HSS_NT) {
             double dot = v0 * A[k * m + j];
             for (int i = k + 1; i < s; i++) dot += A[i * m + k] * A[i * m + j];
@@ -291,7 +310,7 @@ __global__ void __launch_bounds__(HSS_NT) k_id(const IdDesc* D, int nd, double t
             nrm[j] = nn;
         }
         __syncthreads();
-        if (tid == 0) A[k * m + k] = alpha;   // column k is read by no one until the end
+        if (tid == 0) A[k * m + k] = s_par[2];   // column k is read by no one until the end
     }
     __syncthreads();
     // T = R11^{-1} R12 in place (columns rank..m-1), back substitution

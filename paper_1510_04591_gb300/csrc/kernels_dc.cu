@@ -722,8 +722,9 @@ void td_launch_merge_level(const MergeDesc* M, int nmerge, int nmax, int rows, i
 // (poles > i) fitted in value and slope (Bunch, Nielsen & Sorensen), bisection
 // when the model step leaves the bracket; it starts from the root of a
 // two-pole model built from the midpoint value (the oracle starts at the
-// middle of the bracket).  The K-term sums are lane-strided and reduced with
-// warp shuffles.
+// middle of the bracket) and takes a model step below 1e-9 of tau as the
+// converged value without evaluating there (the oracle evaluates once more).
+// The K-term sums are lane-strided and reduced with warp shuffles.
 // ---------------------------------------------------------------------------
 // 1 / x by Newton-Raphson iteration for the reciprocal (r <- r + r (1 - x r),
 // each step squaring the relative error) from the hardware's approximate FP64
@@ -880,14 +881,20 @@ __device__ void secular_root_warp(const double* __restrict__ d, const double* __
                         const double E = f - dpsi * a1;
                         if (E == 0.0) ok = false; else step = a1 * f / E;
                     }
-                    nt = ok ? tau + step : 0.5 * (lo + hi);
-                    if (!(nt > lo && nt < hi)) nt = 0.5 * (lo + hi);
+                    const bool model = ok && tau + step > lo && tau + step < hi;
+                    nt = model ? tau + step : 0.5 * (lo + hi);
                     if (nt == tau) stop = 1;
+                    // a model step below 1e-9 of tau: tau is within about that of the
+                    // root and the step (second order in that error) lands within
+                    // rounding of it, so nt is taken without another evaluation
+                    else if (model && fabs(step) <= 1e-9 * fabs(tau)) stop = 2;
                 }
             }
         }
-        if (__shfl_sync(0xffffffffu, stop, 0)) break;
+        stop = __shfl_sync(0xffffffffu, stop, 0);
+        if (stop == 1) break;
         tau = __shfl_sync(0xffffffffu, nt, 0);
+        if (stop == 2) break;
     }
     *lam = dorg + tau;
     if (last) { *gam = tau; *mu = 0.0; }

@@ -967,8 +967,11 @@ __global__ void k_lowner(const MergeDesc* M, int nmerge, int rows, LevelWS ws)
     int ex = 0, cnt = 0;
     for (int j = lane; j < K; j += 32) {
         if (j == i) continue;
-        pn *= -td_dminus(d, gam, mu, i, j);   // lambda_j - d_i
-        pd *= d[j] - di;
+        const double den = d[j] - di;
+        // lambda_j - d_i by Remark 1: (d_j - d_i) + gamma_j for j > i (the same
+        // value as -td_dminus, reusing the denominator), (d_j+1 - d_i) - mu_j below
+        pn *= (j > i) ? den + gam[j] : -td_dminus(d, gam, mu, i, j);
+        pd *= den;
         if (++cnt == 4) {
             cnt = 0;
             pn = td_renorm(pn, &ex, 1);

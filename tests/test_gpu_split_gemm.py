@@ -109,3 +109,23 @@ def test_split_gemm_rejects_bad_arguments():
             with pytest.raises(tdeig.TdeigError) as e:
                 s.split_gemm(A, A, **kw)
             assert e.value.status == tdeig.EINVAL
+
+
+def test_zero_rows_and_columns():
+    """Rows of op(A) and columns of op(B) with no nonzero entry (their exponent
+    bound keeps its initial value) give exact zeros; the other entries keep the
+    40-bit bound."""
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((150, 90))
+    B = rng.standard_normal((90, 40))
+    A[[0, 77, 149], :] = 0.0
+    B[:, [5, 39]] = 0.0
+    with solver() as s:
+        C = s.split_gemm(A, B, "split", 40)
+    assert np.all(C[[0, 77, 149], :] == 0.0)
+    assert np.all(C[:, [5, 39]] == 0.0)
+    rows = np.setdiff1d(np.arange(150), [0, 77, 149])
+    cols = np.setdiff1d(np.arange(40), [5, 39])
+    e = rel_err(C[np.ix_(rows, cols)], A[rows], B[:, cols])
+    print("zero rows/cols", e)
+    assert e <= 2.0 ** -36

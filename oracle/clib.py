@@ -39,7 +39,7 @@ def lib():
             L.orc_leaf_qr.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp]
             L.orc_leaf_qr.restype = ctypes.c_int
             L.orc_deflate.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, ctypes.c_int,
-                                      ctypes.c_int, _ip]
+                                      ctypes.c_int, _ip, _ip, _ip, _dp, _dp, _ip]
             L.orc_deflate.restype = ctypes.c_int
             L.orc_secular_root.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_int,
                                            _dp, _dp, _dp, _dp]

@@ -45,15 +45,61 @@ def leaf_qr(a, b):
     return lam, Q
 
 
-def deflate(d, z, rho, W):
-    """In-place deflation; returns keep mask (bool).  W is Fortran-ordered."""
+def deflate(d, z, rho, W, rotations=False):
+    """In-place deflation (Sec. 4.3 reading in tdeig_oracle.c); returns the keep
+    mask (bool), and with rotations=True also the rotation list in sweep order
+    (j, i, c, s arrays).  W is Fortran-ordered."""
     n = len(d)
     keep = np.zeros(n, dtype=np.int32)
     assert W.flags["F_CONTIGUOUS"]
+    rj = np.zeros(max(n, 1), dtype=np.int32)
+    ri = np.zeros(max(n, 1), dtype=np.int32)
+    rc = np.zeros(max(n, 1))
+    rs = np.zeros(max(n, 1))
+    nr = np.zeros(1, dtype=np.int32)
     K = lib().orc_deflate(n, dptr(d), dptr(z), float(rho), dptr(W), W.shape[0], W.shape[0],
-                          iptr(keep))
+                          iptr(keep), iptr(rj), iptr(ri), dptr(rc), dptr(rs), iptr(nr))
     assert K == int(keep.sum())
+    if rotations:
+        m = int(nr[0])
+        return keep.astype(bool), (rj[:m].copy(), ri[:m].copy(), rc[:m].copy(), rs[:m].copy())
     return keep.astype(bool)
+
+
+def merge_prep(lam1, Q1, lam2, Q2, beta, rotations=False):
+    """Steps 3-4 of a merge (eq. T3, then the sort and the deflation of Sec. 4.3).
+
+    Q1, Q2 may be full eigenvector matrices or just the rows the merge uses
+    (Q1's last row and Q2's first row, given as 1 x n arrays); W is then built
+    from identity blocks.  Returns a dict with perm (sorted position -> index
+    into [lam1, lam2]), d and z after deflation, rho, keep (bool), W (the
+    sorted, rotated diag(Q1, Q2)) and, with rotations=True, the rotation list.
+    """
+    n1, n2 = len(lam1), len(lam2)
+    n = n1 + n2
+    rho = abs(beta)
+    s = -1.0 if beta < 0 else 1.0
+    z = np.concatenate([Q1[-1, :], s * Q2[0, :]])
+    dcat = np.concatenate([lam1, lam2])
+    perm = np.argsort(dcat, kind="stable")
+    d = np.ascontiguousarray(dcat[perm])
+    z = np.ascontiguousarray(z[perm])
+    W = np.zeros((n, n), order="F")
+    W[:n1, :n1] = Q1 if Q1.shape[0] == n1 else np.eye(n1)
+    W[n1:, n1:] = Q2 if Q2.shape[0] == n2 else np.eye(n2)
+    W = np.asfortranarray(W[:, perm])
+    nrm = np.sqrt(np.dot(z, z))
+    if nrm > 0:
+        z /= nrm
+        rho *= nrm * nrm
+    out = {"perm": perm, "rho": rho, "W": W}
+    if rotations:
+        keep, rot = deflate(d, z, rho, W, rotations=True)
+        out["rot"] = rot
+    else:
+        keep = deflate(d, z, rho, W)
+    out.update(d=d, z=z, keep=keep)
+    return out
 
 
 def secular(d, z, rho, nthreads=None):
@@ -128,24 +174,9 @@ class Options:
 
 def merge(lam1, Q1, lam2, Q2, beta, opt, merge_id=0, stats=None):
     """One merge of Algorithm 1: returns (lam, Q) of the n x n subproblem."""
-    n1, n2 = len(lam1), len(lam2)
-    n = n1 + n2
-    rho = abs(beta)
-    s = -1.0 if beta < 0 else 1.0
-    z = np.concatenate([Q1[n1 - 1, :], s * Q2[0, :]])
-    dcat = np.concatenate([lam1, lam2])
-    perm = np.argsort(dcat, kind="stable")
-    d = np.ascontiguousarray(dcat[perm])
-    z = np.ascontiguousarray(z[perm])
-    W = np.zeros((n, n), order="F")
-    W[:n1, :n1] = Q1
-    W[n1:, n1:] = Q2
-    W = np.asfortranarray(W[:, perm])
-    nrm = np.sqrt(np.dot(z, z))
-    if nrm > 0:
-        z /= nrm
-        rho *= nrm * nrm
-    keep = deflate(d, z, rho, W)
+    n = len(lam1) + len(lam2)
+    pr = merge_prep(lam1, Q1, lam2, Q2, beta)
+    d, z, rho, keep, W = pr["d"], pr["z"], pr["rho"], pr["keep"], pr["W"]
     K = int(keep.sum())
     rec = {"n": n, "K": K, "hss": False, "rank": 0}
     if K == 0:

@@ -117,9 +117,12 @@ int orc_leaf_qr(int n, const double* a_in, const double* b_in, double* lam, doub
 /*       the diagonal of G^T diag(d_j, d_i) G, and j deflates.              */
 /* W (n x n, column-major, leading dim ldw) holds the columns that go with  */
 /* d; rotated columns are updated in place.  keep[i] = 1 for survivors.     */
+/* rot (optional, NULL to skip): the rotations in sweep order, rot_j[t],    */
+/* rot_i[t], rot_c[t], rot_s[t] (up to n of them), *nrot their count.       */
 /* Returns the number of survivors K.                                       */
 /* ------------------------------------------------------------------------ */
-int orc_deflate(int n, double* d, double* z, double rho, double* W, int nrow, int ldw, int* keep)
+int orc_deflate(int n, double* d, double* z, double rho, double* W, int nrow, int ldw, int* keep,
+                int* rot_j, int* rot_i, double* rot_c, double* rot_s, int* nrot)
 {
     double dmax = 0.0, zmax = 0.0;
     for (int i = 0; i < n; i++) {
@@ -127,7 +130,7 @@ int orc_deflate(int n, double* d, double* z, double rho, double* W, int nrow, in
         if (fabs(z[i]) > zmax) zmax = fabs(z[i]);
     }
     double tau = 8.0 * ORC_EPS * fmax(dmax, rho * zmax);
-    int j = -1, K = 0;
+    int j = -1, K = 0, nr = 0;
     for (int i = 0; i < n; i++) {
         keep[i] = 0;
         if (rho * fabs(z[i]) <= tau) { z[i] = 0.0; continue; }
@@ -147,11 +150,19 @@ int orc_deflate(int n, double* d, double* z, double rho, double* W, int nrow, in
                 W[row + (size_t)i * ldw] = s * qj + c * qi;
             }
             keep[j] = 0;
+            if (rot_j) {
+                rot_j[nr] = j;
+                rot_i[nr] = i;
+                rot_c[nr] = c;
+                rot_s[nr] = s;
+            }
+            nr++;
         }
         keep[i] = 1;
         j = i;
     }
     for (int i = 0; i < n; i++) K += keep[i];
+    if (nrot) *nrot = nr;
     return K;
 }
 

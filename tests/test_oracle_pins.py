@@ -216,6 +216,37 @@ def test_deflation_types():
     assert np.all(np.diff(dd[keep]) > 0)
 
 
+def test_deflation_rotation_record():
+    """The recorded rotation list (sweep order) reproduces the rotated columns:
+    applying each (j, i, c, s) to the identity in order gives W; i ascends, j < i,
+    and every rotated j ends deflated with z_j = 0 (Sec. 4.3 reading)."""
+    n = 40
+    rng = np.random.default_rng(11)
+    d = np.sort(rng.uniform(-1, 1, n))
+    for k in (3, 10, 11, 25):
+        d[k + 1] = d[k]          # exact ties: rotations, one of them chained (10, 11, 12)
+    z = rng.standard_normal(n)
+    z[30] = 1e-19                # tiny weight: deflates without a rotation
+    z /= np.linalg.norm(z)
+    W = np.asfortranarray(np.eye(n))
+    dd, zz = d.copy(), z.copy()
+    keep, (rj, ri, rc, rs) = dc.deflate(dd, zz, 1.3, W, rotations=True)
+    assert len(rj) >= 4 and not keep[30]
+    assert np.all(rj < ri) and np.all(np.diff(ri) > 0)
+    assert any(rj[t + 1] == ri[t] for t in range(len(rj) - 1))   # a chain
+    V = np.eye(n)
+    for j, i, c, s in zip(rj, ri, rc, rs):
+        qj, qi = V[:, j].copy(), V[:, i].copy()
+        V[:, j] = c * qj - s * qi
+        V[:, i] = s * qj + c * qi
+        assert np.isclose(c * c + s * s, 1.0, rtol=0, atol=4e-16)
+    assert np.array_equal(V, W)
+    assert np.all(zz[rj] == 0.0) and not np.any(keep[rj])
+    pr = dc.merge_prep(d[:20], np.eye(20), d[20:], np.eye(20), -0.5, rotations=True)
+    assert np.array_equal(pr["perm"], np.argsort(d, kind="stable"))
+    assert abs(pr["rho"] - 1.0) <= 4e-16   # |b| times |u|^2 = 2 (two unit rows)
+
+
 @pytest.mark.parametrize("n,seed", [(1, 0), (2, 1), (17, 2), (32, 3)])
 def test_leaf_qr(n, seed):
     a, b = inputs.uniform(n, seed)
@@ -279,6 +310,31 @@ def test_rank_estimate_boundary_move_and_cap():
     assert b2[2] != 32 and abs(int(b2[2]) - 32) <= 5
     r2, _ = hss.rank_estimate(gen, np.array([0, 32, 64]), eps=1e-16, cap=100, shift=0)
     assert r2 == 100
+
+
+def test_philox_known_answer_vectors():
+    """Philox4x32-10 against the published known-answer vectors (golden file):
+    a wrong multiplier, Weyl constant, round count or word shuffle fails here."""
+    rows = golden("philox4x32_10_kat.txt")
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        ctr = np.array([v[0:4]], dtype=np.uint64)
+        out = hss.philox4x32_10(ctr, (v[4], v[5]))
+        assert [int(x) for x in out[0]] == v[6:10]
+
+
+def test_philox_gaussian_uses_the_counter_layout():
+    """Omega[i, j] is Box-Muller on the first two words of Philox at counter
+    (i, j, stream, 0) with key (seed lo, seed hi), u = (x + 0.5) 2^-32."""
+    seed = 0x1234567890ABCDEF
+    Om = hss.philox_gaussian(5, 3, seed, 9)
+    for i, j in [(0, 0), (4, 2), (3, 1)]:
+        w = hss.philox4x32_10(np.array([[i, j, 9, 0]], dtype=np.uint64),
+                              (seed & 0xFFFFFFFF, seed >> 32))[0]
+        u1 = (float(w[0]) + 0.5) / 2.0 ** 32
+        u2 = (float(w[1]) + 0.5) / 2.0 ** 32
+        assert Om[i, j] == np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
 
 
 def test_philox_gaussian_moments():

@@ -66,6 +66,21 @@ def deflate(d, z, rho, W, rotations=False):
     return keep.astype(bool)
 
 
+def sum_squares(z):
+    """sum_i z_i^2 correctly rounded: each square split exactly into p + e
+    (Dekker's product with Veltkamp's split), then math.fsum of all the parts.
+    The norm that normalises u is then a function of u alone, whatever the
+    summation order of an implementation."""
+    import math
+    z = np.asarray(z, dtype=np.float64)
+    p = z * z
+    sp = 134217729.0 * z                  # 2^27 + 1
+    zh = sp - (sp - z)
+    zl = z - zh
+    e = ((zh * zh - p) + 2.0 * zh * zl) + zl * zl
+    return math.fsum(np.concatenate([p, e]).tolist())
+
+
 def merge_prep(lam1, Q1, lam2, Q2, beta, rotations=False):
     """Steps 3-4 of a merge (eq. T3, then the sort and the deflation of Sec. 4.3).
 
@@ -88,7 +103,7 @@ def merge_prep(lam1, Q1, lam2, Q2, beta, rotations=False):
     W[:n1, :n1] = Q1 if Q1.shape[0] == n1 else np.eye(n1)
     W[n1:, n1:] = Q2 if Q2.shape[0] == n2 else np.eye(n2)
     W = np.asfortranarray(W[:, perm])
-    nrm = np.sqrt(np.dot(z, z))
+    nrm = np.sqrt(sum_squares(z))
     if nrm > 0:
         z /= nrm
         rho *= nrm * nrm
@@ -178,7 +193,7 @@ def merge(lam1, Q1, lam2, Q2, beta, opt, merge_id=0, stats=None):
     pr = merge_prep(lam1, Q1, lam2, Q2, beta)
     d, z, rho, keep, W = pr["d"], pr["z"], pr["rho"], pr["keep"], pr["W"]
     K = int(keep.sum())
-    rec = {"n": n, "K": K, "hss": False, "rank": 0}
+    rec = {"n": n, "K": K, "hss": False, "rank": 0, "node": merge_id}
     if K == 0:
         lam_new = np.empty(0)
         Qk = np.empty((n, 0), order="F")
@@ -193,7 +208,8 @@ def merge(lam1, Q1, lam2, Q2, beta, opt, merge_id=0, stats=None):
             gen = hss.generators(dk, gam, mu, uhat)
             H, info = hss.build(gen, opt, merge_id)
             Qk = hss.matmul_right(X, H)
-            rec.update(hss=True, rank=info["rank"], max_block_rank=info["max_block_rank"])
+            rec.update(hss=True, rank=info["rank"], max_block_rank=info["max_block_rank"],
+                       bounds=info["bounds"], node_ranks=info["node_ranks"])
         else:
             Qh, _ = cauchy(dk, gam, mu, uhat)
             Qk = X @ Qh

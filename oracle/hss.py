@@ -324,6 +324,11 @@ def build(gen, opt, merge_id):
         H = srrsc(gen, bounds, L, opt.tol)
         info["rank"] = max(H.ranks()) if H.ranks() else 0
     info["max_block_rank"] = max(H.ranks()) if H.ranks() else 0
+    # the (possibly moved) leaf boundaries and every node's (row, column) ID
+    # ranks, levels 1..L, left to right
+    info["bounds"] = [int(x) for x in H.bounds]
+    info["node_ranks"] = [(H.U[(l, q)].shape[1], H.V[(l, q)].shape[1])
+                          for l in range(1, H.L + 1) for q in range(1 << l)]
     return H, info
 
 

@@ -111,10 +111,13 @@ int orc_leaf_qr(int n, const double* a_in, const double* b_in, double* lam, doub
 /*   tau = 8 eps max(max|d|, rho max|z|).                                    */
 /*   Sweep i ascending; j = the last survivor so far.                        */
 /*   (a) rho |z_i| <= tau: i deflates with eigenvalue d_i.                   */
-/*   (b) otherwise, with t = d_i - d_j, r = hypot(z_i, z_j), c = z_i / r,    */
+/*   (b) otherwise, with t = d_i - d_j, r = sqrt(z_i^2 + z_j^2), c = z_i/r,  */
 /*       s = z_j / r: if |t c s| <= tau the rotation [q_j q_i] G,            */
 /*       G = [[c, s], [-s, c]], zeroes z_j; then z_i = r, d_j and d_i take    */
 /*       the diagonal of G^T diag(d_j, d_i) G, and j deflates.              */
+/* Every operation is rounded once, as written (the file is compiled        */
+/* without floating-point contraction): for nearly equal poles t is a few   */
+/* ulp, so the decisions depend on the exact rounding of the rotated poles. */
 /* W (n x n, column-major, leading dim ldw) holds the columns that go with  */
 /* d; rotated columns are updated in place.  keep[i] = 1 for survivors.     */
 /* rot (optional, NULL to skip): the rotations in sweep order, rot_j[t],    */
@@ -136,7 +139,9 @@ int orc_deflate(int n, double* d, double* z, double rho, double* W, int nrow, in
         if (rho * fabs(z[i]) <= tau) { z[i] = 0.0; continue; }
         if (j < 0) { keep[i] = 1; j = i; continue; }
         double t = d[i] - d[j];
-        double r = hypot(z[i], z[j]);
+        /* both weights belong to survivors, rho |z| > tau >= 8 eps rho max|z|:
+           their squares neither underflow nor overflow */
+        double r = sqrt(z[i] * z[i] + z[j] * z[j]);
         double c = z[i] / r, s = z[j] / r;
         if (fabs(t * c * s) <= tau) {
             double dj = d[j], di = d[i];

@@ -216,6 +216,18 @@ def test_deflation_types():
     assert np.all(np.diff(dd[keep]) > 0)
 
 
+def test_sum_squares_is_correctly_rounded():
+    """The norm of the merge vector: sum z_i^2 correctly rounded (exact rational
+    sum, then one rounding), whatever the order of the terms."""
+    from fractions import Fraction
+    rng = np.random.default_rng(12)
+    for n in (1, 2, 7, 1000):
+        z = rng.standard_normal(n) * np.exp(rng.uniform(-20, 5, n))
+        exact = float(sum(Fraction(float(x)) ** 2 for x in z))
+        assert dc.sum_squares(z) == exact
+        assert dc.sum_squares(z[::-1]) == exact
+
+
 def test_deflation_rotation_record():
     """The recorded rotation list (sweep order) reproduces the rotated columns:
     applying each (j, i, c, s) to the identity in order gives W; i ascends, j < i,

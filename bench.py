@@ -31,6 +31,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "full eigendecomp time at N=16384: ADC vs plain DC on GB300, orth/resid ≤1e-10"
+# arithmetic the timed path computes in, per precision flag
+DTYPES = {"fp64": "f64",
+          "split": "split-42/56 (BF16 7-bit digit slices: eigenvector products 42 bits, ADC2 "
+                   "sampling 56 bits; exact FP32 tensor-core sums, FP64 recombination); FP64 "
+                   "elsewhere",
+          "bf16x2": "split-16 (BF16 hi+lo slices) products; FP64 elsewhere",
+          "fp16x2": "split-22 (FP16 hi+lo slices) products; FP64 elsewhere"}
 N_SMS = 152
 SM_MHZ = 2070.0
 FP64_FMA_PER_SM_CLK = 2          # measured: FP64 FMA chain throughput 1.19-1.20 TFLOP/s
@@ -356,12 +363,13 @@ def main():
 
     ms_step, stats, clocks = timed(mode | prof, args.steps, args.warmup)
     launches = sum(int(s.get("launches", 0)) for s in stats)
-    acc = accuracy(a, b, lam, Qt, dev)
+    acc = accuracy(a, b, lam, Qt, dev, sample=None)   # every column of the timed result
 
     out = {"metric": METRIC, "value": ms_step / 1e3, "unit": "s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic",
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": DTYPES[args.prec], "data": "synthetic",
+           "orth": acc["orth"], "resid": acc["resid"],
            "config": {"workload": workload_name(args), "n": N, "matrix": args.matrix,
                       "mode": args.mode, "precision": args.prec, "leaf": 32,
                       "hss_threshold": 2000, "hss_leaf": 128, "tol": 1e-12, "oversample": 10,
@@ -381,6 +389,15 @@ def main():
                                    "stage_ms": st_d[-1]["stage_ms"]}
         out["speedup_vs_plain_dc"] = {pr: out["plain_dc"][pr]["value"] / (ms_step / 1e3)
                                       for pr in ("fp64", "split")}
+    if not args.no_dense_compare and args.prec != "fp64":
+        # the same ADC variant with FP64 products (the paper's precision), timed the
+        # same way: 3 steps after 1 warm-up
+        ms_f, st_f, ck_f = timed(tdeig.mode_code(args.mode, "fp64") | prof, 3, 1)
+        out["adc_fp64"] = {"value": ms_f / 1e3, "unit": "s", "steps": 3, "warmup": 1,
+                           "mode": args.mode, "precision": "fp64",
+                           "accuracy": accuracy(a, b, lam, Qt, dev),
+                           "stage_ms": st_f[-1]["stage_ms"], "clocks": ck_f,
+                           "roofline": roofline(st_f, peaks())}
     out["roofline"] = roofline(stats, peaks())
 
     if not args.no_e2e:
@@ -539,17 +556,23 @@ def run_seed(args, torch, dist, world, rank, local, dev, stream, flush, tdeig):
 
 
 def accuracy(a, b, lam, Qt, dev, sample=1024):
-    """Orthogonality ||Q^T Q - I||_F / N (sampled columns, scaled) and residual
-    ||T Q - Q Lambda||_F / (N ||T||_2) (all columns), closed-form eigenvalue error
-    for Toeplitz(2,1)."""
+    """Orthogonality ||Q^T Q - I||_F / N (sample=None: all columns; else sampled
+    columns, scaled) and residual ||T Q - Q Lambda||_F / (N ||T||_2) (all
+    columns), closed-form eigenvalue error for Toeplitz(2,1)."""
     import torch
     N = lam.shape[0]
     Q = Qt.t()
-    g = torch.Generator(device="cpu").manual_seed(0)
-    idx = torch.randperm(N, generator=g)[:min(sample, N)].to(dev)
-    G = Q.t() @ Q[:, idx]
-    G[idx, torch.arange(len(idx), device=dev)] -= 1.0
-    orth = float(torch.linalg.norm(G)) * math.sqrt(N / len(idx)) / N
+    if sample is None or sample >= N:
+        G = Q.t() @ Q
+        G.diagonal().sub_(1.0)
+        orth = float(torch.linalg.norm(G)) / N
+        idx = torch.arange(N)
+    else:
+        g = torch.Generator(device="cpu").manual_seed(0)
+        idx = torch.randperm(N, generator=g)[:min(sample, N)].to(dev)
+        G = Q.t() @ Q[:, idx]
+        G[idx, torch.arange(len(idx), device=dev)] -= 1.0
+        orth = float(torch.linalg.norm(G)) * math.sqrt(N / len(idx)) / N
     ad = torch.from_numpy(a).to(dev)
     bd = torch.from_numpy(b).to(dev)
     TQ = ad[:, None] * Q
@@ -558,7 +581,8 @@ def accuracy(a, b, lam, Qt, dev, sample=1024):
     TQ -= Q * lam[None, :]
     tn = float(lam.abs().max())
     res = float(torch.linalg.norm(TQ)) / (N * tn)
-    out = {"orth": orth, "orth_note": "%d sampled columns" % len(idx), "resid": res}
+    out = {"orth": orth, "resid": res,
+           "orth_note": "all %d columns" % N if len(idx) == N else "%d sampled columns" % len(idx)}
     if np.all(a == 2.0) and np.all(b == 1.0):
         k = np.arange(1, N + 1)
         ex = np.sort(2 + 2 * np.cos(k * np.pi / (N + 1)))
@@ -591,15 +615,71 @@ def e2e(args, a, b, solver, mode, steps=2):
             "d2h_bytes_per_step": 8 * (N + N * N), "steps": steps}
 
 
+_CPU_JOB = r'''
+import json, os, sys, time
+threads = int(sys.argv[6])
+if threads == 1:
+    os.sched_setaffinity(0, {sorted(os.sched_getaffinity(0))[0]})
+    os.cpu_count = lambda: 1          # the oracle sizes its root-parallel loop by this
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+kind, n, mode, matrix = sys.argv[2], int(sys.argv[3]), sys.argv[4], sys.argv[5]
+from paper_1510_04591_gb300 import inputs
+if matrix == "toeplitz":
+    a, b = inputs.toeplitz(n, 2.0, 1.0)
+else:
+    a, b = inputs.uniform(n, seed=1, lo_b=0.5, hi_b=1.0)
+t = time.perf_counter()
+if kind == "oracle":
+    from oracle import dc
+    dc.solve(a, b, dc.Options(mode={"dense": 0, "adc1": 1, "adc2": 2}[mode]))
+else:
+    import scipy.linalg.lapack as lapack
+    w, v, info = lapack.dstevd(a, b, compute_v=1)
+    assert info == 0
+print(json.dumps({"s": time.perf_counter() - t}))
+'''
+
+
+def _cpu_job(kind, n, mode, matrix, threads, timeout=600):
+    """One timed CPU solve in a fresh process whose thread pools (OpenMP,
+    BLAS) are limited to `threads`; returns seconds or None."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(threads)
+    try:
+        r = subprocess.run([sys.executable, "-c", _CPU_JOB, ROOT, kind, str(n), mode, matrix,
+                            str(threads)], capture_output=True, text=True, timeout=timeout,
+                           env=env)
+        return json.loads(r.stdout.strip().splitlines()[-1])["s"]
+    except Exception:
+        return None
+
+
 def cpu_baseline(args, a, b):
+    """The oracle on the host: one full solve of the workload on all host threads
+    (the reported value), one bounded single-thread sample, and LAPACK dstevd
+    (divide and conquer, scipy) on all threads as the stand-in for the paper's
+    multithreaded MKL comparator (its ratios are context only)."""
     from oracle import dc
     mode = {"dense": dc.MODE_DENSE, "adc1": dc.MODE_ADC1, "adc2": dc.MODE_ADC2}[args.mode]
     t = time.perf_counter()
     dc.solve(a, b, dc.Options(mode=mode))
     v = time.perf_counter() - t
-    return {"value": v, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+    cores = os.cpu_count()
+    n1 = min(args.n, 4096)
+    st = _cpu_job("oracle", n1, args.mode, args.matrix, 1)
+    lp = _cpu_job("lapack", args.n, args.mode, args.matrix, cores)
+    return {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
             "sample": "one full N=%d solve in %s mode, FP64 (C routines with OpenMP over "
-                      "roots, numpy BLAS products, all host threads)" % (args.n, args.mode)}
+                      "roots, numpy BLAS products, all host threads)" % (args.n, args.mode),
+            "single_thread": {"value": st, "unit": "s", "cores": 1, "kind": "oracle",
+                              "sample": "one full N=%d solve (same matrix family and mode), "
+                                        "one thread pinned to one core" % n1},
+            "lapack_dstevd": {"value": lp, "unit": "s", "cores": cores, "kind": "library",
+                              "sample": "scipy LAPACK dstevd (divide and conquer, all "
+                                        "eigenvectors), full N=%d, %d BLAS threads"
+                                        % (args.n, cores)}}
 
 
 if __name__ == "__main__":

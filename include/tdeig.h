@@ -177,6 +177,80 @@ int tdeig_split_gemm(tdeig_handle h, int64_t M, int64_t N, int64_t K, const doub
                      int prec, int bits);
 
 /* ---------------------------------------------------------------------- */
+/* Stage entry points of the integer decisions (deflation, rank estimate,   */
+/* interpolative decomposition) and of the sampling generator.  Each runs   */
+/* the solver's own kernel on the given inputs, so that its decisions can   */
+/* be compared index for index with an independent implementation.  Array  */
+/* pointers may be host or device memory as above unless stated; results   */
+/* are final when the call returns.                                         */
+/* ---------------------------------------------------------------------- */
+
+/* One merge's preparation (eq. T3 and the deflation of Algorithm 1, which
+ * Sec. 4.3 delegates to LAPACK's deflation; reading: Gu & Eisenstat).
+ *   lam1 (n1), lam2 (n2) : the children's eigenvalues, each ascending
+ *   z1 (n1) : the last row of Q1;  z2 (n2) : the first row of Q2
+ *   beta    : the coupling b_k (rho = |beta|, z2 enters with sign(beta))
+ * The entries are merged stably (child 1 first on ties), z is normalised
+ * (rho absorbs |z|^2) and swept in ascending order against the last survivor
+ * j with tau = 8 eps max(max|d|, rho max|z|): rho |z_i| <= tau deflates i;
+ * otherwise, with r = hypot(z_i, z_j), c = z_i / r, s = z_j / r, |(d_i - d_j)
+ * c s| <= tau rotates the pair (z_j -> 0, z_i -> r, d_j, d_i -> the diagonal
+ * of G^T diag(d_j, d_i) G) and deflates j.  Outputs (any may be NULL):
+ *   perm (n, int32) : sorted position p holds entry perm[p] of [lam1, lam2]
+ *   d_out, z_out (n): poles and weights after the sweep (z = 0 where deflated)
+ *   keep (n, int32) : 0 deflated, else the survivor's support: 1 rows of
+ *                     child 1 only, 2 child 2 only, 3 both (rotated across)
+ *   rho_out (host, 1), counts (host, 2): K survivors and the rotation count
+ *   rot_j, rot_i (int32), rot_c, rot_s : the rotations in sweep order
+ *                     (capacity n each; counts[1] are written)
+ * TDEIG_EINVAL for n1 < 1, n2 < 1, n1 + n2 > 2^24 or non-finite beta. */
+int tdeig_merge_deflate(tdeig_handle h, int64_t n1, int64_t n2, const double* lam1,
+                        const double* lam2, const double* z1, const double* z2, double beta,
+                        int32_t* perm, double* d_out, double* z_out, int32_t* keep,
+                        double* rho_out, int64_t* counts, int32_t* rot_j, int32_t* rot_i,
+                        double* rot_c, double* rot_s);
+
+/* Off-diagonal rank estimate of one HSS merge (eq. bounds, with the rules of
+ * Sec. 4.1): for each inner boundary b of the leaf partition, dist =
+ * lambda_b - d_{b-1} = (d_b - d_{b-1}) + gamma_b (reading of eq. dist_xy);
+ * a boundary with dist < 1e-10 moves by up to the handle's boundary_shift
+ * rows (within its neighbours) to the largest dist; r = min(rank_cap, max_b
+ * ceil(ln(16 / rank_eps) ln(8 R) / pi^2)), R = (lambda_K - d_1) / dist.
+ *   d, gamma (K >= 2) : deflated poles and gaps gamma_i = lambda_i - d_i
+ *   bounds (HOST int32, nl + 1, in/out): 0 = b_0 < b_1 < ... < b_nl = K
+ *   r_out (HOST int32, 1) */
+int tdeig_rank_estimate(tdeig_handle h, int64_t K, const double* d, const double* gamma,
+                        int64_t nl, int32_t* bounds, int32_t* r_out);
+
+/* Row interpolative decomposition Phi ~= U Phi[piv, :] (Sec. 3; Algorithm 2)
+ * by Householder QR with column pivoting of Phi^T, stopped at the first k
+ * with |R_kk| <= tol |R_00| (tol: the handle's option).
+ *   Phi   : m x s column-major, leading dimension ldphi (1 <= m, s <= 4096;
+ *           m * s doubles must fit the kernel's shared memory, else EINVAL)
+ *   U     : m x rank written (leading dimension ldu), U[piv, :] = I
+ *   piv   : rank int32 entries (the skeleton rows, in pivot order)
+ *   rank_out (HOST int32, 1) */
+int tdeig_interp_decomp(tdeig_handle h, int64_t m, int64_t s, const double* Phi, int64_t ldphi,
+                        double* U, int64_t ldu, int32_t* piv, int32_t* rank_out);
+
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), the counter-based
+ * generator of the Gaussian sampling matrix of Sec. 3: out[4t..4t+3] =
+ * Philox(ctr[4t..4t+3], key[2t..2t+1]) for t < n (uint32 words). */
+int tdeig_philox4x32_10(tdeig_handle h, int64_t n, const uint32_t* ctr, const uint32_t* key,
+                        uint32_t* out);
+
+/* The sampling matrix Omega of ADC2 (Sec. 3) as the solver draws it:
+ * out[i + j nrow] from Philox at counter (i, j, stream_id, 0), key (seed low
+ * word, seed high word), Box-Muller on the first two words with u = (x + 0.5)
+ * 2^-32.  (The solver uses the DC node as stream_id.) */
+int tdeig_gaussian(tdeig_handle h, int64_t nrow, int64_t ncol, uint64_t seed, uint32_t stream_id,
+                   double* out);
+
+/* Architecture of the library's device code as the current device loads it:
+ * *arch = major * 10 + minor (103 for sm_103a).  TDEIG_ECUDA without a GPU. */
+int tdeig_binary_arch(int* arch);
+
+/* ---------------------------------------------------------------------- */
 /* Learned rank seed for ADC2 (not in the paper; it replaces the rank       */
 /* estimate of eq. (bounds) as the first guess of the sampling rank r,      */
 /* with that estimate kept as the fallback).                                */
@@ -243,26 +317,30 @@ int tdeig_rank_records(tdeig_handle h, float* buf, int64_t cap);
 /* Largest K accepted by tdeig_secular_noalloc. */
 #define TDEIG_NOALLOC_MAX_K 65536
 
-/* Secular roots as tdeig_secular computes them, but without allocating any
- * memory.  The paper has no counterpart: this entry point exists for callers
- * that cannot allocate device memory when they need the roots -- code that
- * has handed all free device memory to its own pool allocator (where a
- * cudaMalloc would fail or fragment that pool), and code on a latency-bound
- * path where cudaMalloc's implicit device synchronisation is not acceptable.
- * It needs no handle and calls no cudaMalloc, cudaFree or allocating library
- * routine.
+/* Secular roots exactly as tdeig_secular computes them (the same iteration
+ * from the same FP32 start, bit-identical results), but without allocating
+ * any memory.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory when they need the roots --
+ * code that has handed all free device memory to its own pool allocator
+ * (where a cudaMalloc would fail or fragment that pool), and code on a
+ * latency-bound path where cudaMalloc's implicit device synchronisation is
+ * not acceptable.  It needs no handle and calls no cudaMalloc, cudaFree or
+ * allocating library routine.
  *   K      : 1 <= K <= TDEIG_NOALLOC_MAX_K (65536); larger K -> TDEIG_EINVAL
- *   d, z   : K entries each, DEVICE memory (host pointers -> TDEIG_EINVAL)
- *   lambda, gamma, mu : K entries each, DEVICE memory, written as by tdeig_secular
+ *   d, z   : K entries each, DEVICE memory of the current device (host,
+ *            managed or another device's memory -> TDEIG_EINVAL)
+ *   lambda, gamma, mu : K entries each, same kind of memory, written as by
+ *            tdeig_secular
  *   cuda_stream : cudaStream_t to run on (NULL: the legacy default stream)
- * Scratch (K weights and a status word, 512 KiB in all) is a fixed array in
- * the library's device image, held by every GPU that loads the library until
- * the process exits; each call clears the status word before use.  The first
- * call on a device, with that device current, looks up the array's device
- * address (cudaGetSymbolAddress) -- make that first call before any stream
- * capture.  All calls share the array: calls whose work overlaps on the GPU
- * (other streams or host threads) race.  The call synchronises the stream and
- * returns TDEIG_ENOTCONV if a root hit the iteration cap. */
+ * Scratch (the weights in FP64 and FP32, an FP32 pair per pole and a status
+ * word: 1.25 MiB in all) is a fixed array in the library's device image, held
+ * by every GPU that loads the library until the process exits; each call
+ * clears the status word before use.  The first call on a device, with that
+ * device current, looks up the array's device address (cudaGetSymbolAddress)
+ * -- make that first call before any stream capture.  All calls share the
+ * array: calls whose work overlaps on the GPU (other streams or host threads)
+ * race.  The call synchronises the stream and returns TDEIG_ENOTCONV if a
+ * root hit the iteration cap. */
 int tdeig_secular_noalloc(int64_t K, const double* d, const double* z, double rho,
                           double* lambda, double* gamma, double* mu, void* cuda_stream);
 

@@ -34,6 +34,10 @@ struct MergeDesc {
     int node_id;           // node of the DC tree: root 0, children of i are 2i+1, 2i+2
     int tile0;             // first GEMM tile of this merge in the level's tile numbering
     int tiles_m;           // row tiles of this merge
+    // stage entry point only (NULL in a solve): the merge vector's halves given
+    // directly, z1 = last row of Q1 (n1), z2 = first row of Q2 (n2)
+    const double* z1;
+    const double* z2;
 };
 
 struct LeafDesc {
@@ -75,12 +79,9 @@ struct LevelWS {
     float* wfK;        // wK in FP32
 };
 
-// Number of kernels launched by this library (host counter, read per solve).
-extern long long g_td_launches;
-
 // Per-kernel timing of a solve made with TDEIG_FLAG_PROFILE: td_prof_begin
 // records an event before a launch, td_prof_end one after it (and counts the
-// launch).  Events are kept in launch order; one profiled solve at a time.
+// launch).  Events are kept in launch order.
 struct TdProf {
     bool on = false;
     std::vector<cudaEvent_t> ev;
@@ -88,7 +89,31 @@ struct TdProf {
     std::vector<std::string> note;   // optional shape of the launch, same index
     size_t n = 0;
 };
-extern TdProf g_td_prof;
+
+// Launch count, split-product work counters and kernel timing of the calls
+// made on one handle.  While a call runs, the calling thread's current record
+// is its handle's own (TdCtxScope); outside calls a thread-local record takes
+// the counts.  With one handle per host thread, records of different handles
+// never mix.
+struct TdCtx {
+    long long launches = 0;
+    double split_tensor_flops = 0.0;   // tensor work issued: 2 M N K per slice pair
+    double split_slice_bytes = 0.0;    // algorithmic bytes of k_slice (read 8 B, write 2 s B per element)
+    double split_exp_bytes = 0.0;      // algorithmic bytes of k_slice_exp (read 8 B per element)
+    TdProf prof;
+};
+TdCtx& td_ctx();
+struct TdCtxScope {
+    TdCtx* prev;
+    explicit TdCtxScope(TdCtx* c);
+    ~TdCtxScope();
+};
+// Raises a kernel's dynamic shared-memory limit to `bytes` on the current
+// device (once per kernel, device and size).
+void td_smem_attr(const void* kernel, size_t bytes);
+// Number of SMs of the current device.
+int td_sm_count();
+
 void td_prof_begin(cudaStream_t st);
 void td_prof_end(cudaStream_t st, const char* name);
 // Attaches a note (a JSON array of numbers) to the last profiled launch.
@@ -102,6 +127,10 @@ void td_launch_leaf(const LeafDesc* leaves, int nleaves, const double* A, const 
                     const LeafRot& R, int* status, cudaStream_t st);
 void td_launch_merge_level(const MergeDesc* M, int nmerge, int nmax, int rows, int total_tiles,
                            const LevelWS& ws, int* status, int use_hss_mask, cudaStream_t st);
+// binaryVersion (major * 10 + minor) of the library's device code on the current device.
+int td_binary_version(int* out);
+// k_prep alone (eq. T3, sort, deflation, compaction), for the deflation stage entry point.
+void td_launch_prep(const MergeDesc* M, int nmerge, const LevelWS& ws, cudaStream_t st);
 void td_launch_secular(const MergeDesc* M, int nmerge, int rows, const LevelWS& ws, int* status,
                        cudaStream_t st);
 void td_launch_lowner_cauchy(const MergeDesc* M, int nmerge, int rows, int kmax, const LevelWS& ws,

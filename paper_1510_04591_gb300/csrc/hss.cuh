@@ -111,6 +111,16 @@ struct RankDesc {
     int* r_out;
 };
 
+// Stage launchers (the stage entry points of include/tdeig.h).
+void hss_launch_rank_estimate(const RankDesc* dev, int nr, double eps, int cap, int shift,
+                              cudaStream_t st);
+// TDEIG_EINVAL when an m x s ID does not fit the kernel's shared memory.
+int hss_launch_id(const IdDesc* dev, int nd, int smax, int mmax, double tol, cudaStream_t st);
+void hss_launch_philox_words(const unsigned* ctr, const unsigned* key, unsigned* out, int64_t n,
+                             cudaStream_t st);
+void hss_launch_gaussian(double* Om, int K, int s, unsigned long long seed, unsigned stream,
+                         cudaStream_t st);
+
 // Launches one grouped product; returns its algorithmic flops (2 M N Kd summed).
 double hss_launch_gemm(const std::vector<GemmDesc>& g, GemmDesc* dev, cudaStream_t st);
 void hss_free(HssWS& w);

@@ -26,37 +26,86 @@
 
 #define TD_NOALLOC_MAX_DEVICES 64
 
-long long g_td_launches = 0;
-TdProf g_td_prof;
+static thread_local TdCtx t_idle_ctx;            // counts of launches outside handle calls
+static thread_local TdCtx* t_ctx = nullptr;
 
-static cudaEvent_t prof_next(const char* name)
+TdCtx& td_ctx() { return t_ctx ? *t_ctx : t_idle_ctx; }
+TdCtxScope::TdCtxScope(TdCtx* c) : prev(t_ctx) { t_ctx = c; }
+TdCtxScope::~TdCtxScope() { t_ctx = prev; }
+
+#define TD_MAX_DEVICES 64
+static std::mutex g_attr_mu;
+
+void td_smem_attr(const void* kernel, size_t bytes)
 {
-    if (g_td_prof.n >= g_td_prof.ev.size()) {
+    // per (kernel, device): the largest limit set so far
+    static std::vector<std::pair<const void*, size_t>> done[TD_MAX_DEVICES];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= TD_MAX_DEVICES) {
+        cudaGetLastError();
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        return;
+    }
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    for (auto& e : done[dev])
+        if (e.first == kernel) {
+            if (e.second >= bytes) return;
+            cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+            e.second = bytes;
+            return;
+        }
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    done[dev].push_back({kernel, bytes});
+}
+
+int td_sm_count()
+{
+    static int nsm[TD_MAX_DEVICES];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= TD_MAX_DEVICES) {
+        cudaGetLastError();
+        return 1;
+    }
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    if (!nsm[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        nsm[dev] = n > 0 ? n : 1;
+    }
+    return nsm[dev];
+}
+
+static cudaEvent_t prof_next(TdProf& P, const char* name)
+{
+    if (P.n >= P.ev.size()) {
         cudaEvent_t e = nullptr;
         cudaEventCreate(&e);
-        g_td_prof.ev.push_back(e);
-        g_td_prof.name.push_back(nullptr);
-        g_td_prof.note.emplace_back();
+        P.ev.push_back(e);
+        P.name.push_back(nullptr);
+        P.note.emplace_back();
     }
-    g_td_prof.name[g_td_prof.n] = name;
-    g_td_prof.note[g_td_prof.n].clear();
-    return g_td_prof.ev[g_td_prof.n++];
+    P.name[P.n] = name;
+    P.note[P.n].clear();
+    return P.ev[P.n++];
 }
 
 void td_prof_begin(cudaStream_t st)
 {
-    if (g_td_prof.on) cudaEventRecord(prof_next(nullptr), st);
+    TdProf& P = td_ctx().prof;
+    if (P.on) cudaEventRecord(prof_next(P, nullptr), st);
 }
 
 void td_prof_note(const std::string& s)
 {
-    if (g_td_prof.on && g_td_prof.n > 0) g_td_prof.note[g_td_prof.n - 1] = s;
+    TdProf& P = td_ctx().prof;
+    if (P.on && P.n > 0) P.note[P.n - 1] = s;
 }
 
 void td_prof_end(cudaStream_t st, const char* name)
 {
-    g_td_launches++;
-    if (g_td_prof.on) cudaEventRecord(prof_next(name), st);
+    TdCtx& c = td_ctx();
+    c.launches++;
+    if (c.prof.on) cudaEventRecord(prof_next(c.prof, name), st);
 }
 
 // ---------------------------------------------------------------------------
@@ -373,18 +422,60 @@ __device__ int blk_scan(int f, int* red, int* total)
     return base + pre;
 }
 
+// s + c += a with s carrying the rounded sum and c the accumulated rounding
+// errors (Knuth's TwoSum; Ogita, Rump & Oishi's compensated summation).
+__device__ __forceinline__ void cs_add(double& s, double& c, double a)
+{
+    const double t = __dadd_rn(s, a);
+    const double bp = __dsub_rn(t, s);
+    const double err = __dadd_rn(__dsub_rn(s, __dsub_rn(t, bp)), __dsub_rn(a, bp));
+    s = t;
+    c = __dadd_rn(c, err);
+}
+
+// sum over the block of the thread values (s, c), rounded once at the end:
+// the sum as if computed in twice the working precision, then rounded, which
+// is the correctly rounded sum except within ~n^2 eps^2 of a rounding
+// boundary (whatever the order of the terms).
+__device__ double blk_sum_compensated(double s, double c, double* red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double s2 = __shfl_xor_sync(0xffffffffu, s, o);
+        const double c2 = __shfl_xor_sync(0xffffffffu, c, o);
+        cs_add(s, c, s2);
+        c = __dadd_rn(c, c2);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) { red[2 * w] = s; red[2 * w + 1] = c; }
+    __syncthreads();
+    double ts = red[0], tc = red[1];
+    for (int i = 1; i < (int)(blockDim.x >> 5); i++) {
+        cs_add(ts, tc, red[2 * i]);
+        tc = __dadd_rn(tc, red[2 * i + 1]);
+    }
+    return __dadd_rn(ts, tc);
+}
+
 // ---------------------------------------------------------------------------
 // k_prep: one CTA per merge.  eq. T3 (u from Q1's last row and Q2's first row,
 // rho = |b_k|, sign folded into u), stable merge of D1 and D2, normalisation of
 // u (rho absorbs |u|^2), deflation, compaction of the survivors.
 // Deflation reading (Gu & Eisenstat): tau = 8 eps max(max|d|, rho max|z|);
 // sweep ascending against the last survivor j: rho|z_i| <= tau deflates i;
-// else with r = hypot(z_i, z_j), c = z_i/r, s = z_j/r, |(d_i - d_j) c s| <= tau
-// rotates the pair (z_j -> 0, z_i -> r) and deflates j.
+// else with r = sqrt(z_i^2 + z_j^2), c = z_i/r, s = z_j/r, |(d_i - d_j) c s|
+// <= tau rotates the pair (z_j -> 0, z_i -> r) and deflates j.
+// The decisions are a function of the inputs alone: |z|^2 is summed with
+// compensation (the correctly rounded sum but for ties within ~n^2 eps^2),
+// and every operation of the sweep is rounded once as written (no fused
+// multiply-add): for nearly equal poles t is a few ulp, so a differently
+// rounded rotated pole would change later decisions.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(PREP_NT) k_prep(const MergeDesc* M, LevelWS ws)
 {
     __shared__ double red[32];
+    __shared__ double red2[2 * (PREP_NT / 32)];
     __shared__ int ired[32];
     __shared__ double s_tau, s_rho;
     MergeDesc md = M[blockIdx.x];
@@ -392,7 +483,7 @@ __global__ void __launch_bounds__(PREP_NT) k_prep(const MergeDesc* M, LevelWS ws
     const double* lam = md.lam_in;
     const double beta = *md.beta_ptr;
     const double sgn = (beta < 0.0) ? -1.0 : 1.0;
-    double zz = 0.0, dmax = 0.0, zmax = 0.0;
+    double zz = 0.0, zzc = 0.0, dmax = 0.0, zmax = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         double v = lam[i], z;
         int r;
@@ -400,22 +491,25 @@ __global__ void __launch_bounds__(PREP_NT) k_prep(const MergeDesc* M, LevelWS ws
             int lo = 0, hi = n2;   // count of D2 < v
             while (lo < hi) { int mid = (lo + hi) >> 1; if (lam[n1 + mid] < v) lo = mid + 1; else hi = mid; }
             r = i + lo;
-            z = md.qin1[(int64_t)i * n1 + (n1 - 1)];
+            z = md.z1 ? md.z1[i] : md.qin1[(int64_t)i * n1 + (n1 - 1)];
         } else {
             int j = i - n1;
             int lo = 0, hi = n1;   // count of D1 <= v
             while (lo < hi) { int mid = (lo + hi) >> 1; if (lam[mid] <= v) lo = mid + 1; else hi = mid; }
             r = j + lo;
-            z = sgn * md.qin2[(int64_t)j * n2];
+            z = sgn * (md.z2 ? md.z2[j] : md.qin2[(int64_t)j * n2]);
         }
         ws.dsort[g0 + r] = v;
         ws.zsort[g0 + r] = z;
         ws.src[g0 + r] = i;
-        zz += z * z;
+        // z^2 = p + e exactly (e from a fused multiply-add), both summed
+        const double p = __dmul_rn(z, z);
+        cs_add(zz, zzc, p);
+        zzc = __dadd_rn(zzc, fma(z, z, -p));
         dmax = fmax(dmax, fabs(v));
         zmax = fmax(zmax, fabs(z));
     }
-    zz = blk_sum(zz, red);
+    zz = blk_sum_compensated(zz, zzc, red2);
     dmax = blk_max(dmax, red);
     zmax = blk_max(zmax, red);
     double nrm = sqrt(zz);
@@ -474,12 +568,15 @@ __global__ void __launch_bounds__(PREP_NT) k_prep(const MergeDesc* M, LevelWS ws
                 int nm = m0;
                 if (cand && has_pred) {
                     const double t = d0 - pd;
-                    const double r = hypot(z0, pz);
+                    // survivors' weights: rho |z| > tau >= 8 eps rho max|z|, so the
+                    // squares neither underflow nor overflow
+                    const double r = sqrt(__dadd_rn(__dmul_rn(z0, z0), __dmul_rn(pz, pz)));
                     const double cc = z0 / r, ss = pz / r;
-                    if (fabs(t * cc * ss) <= tau) {
+                    if (fabs(__dmul_rn(__dmul_rn(t, cc), ss)) <= tau) {
                         nr = true;
-                        nj = cc * cc * pd + ss * ss * d0;
-                        nd = ss * ss * pd + cc * cc * d0;
+                        const double c2 = __dmul_rn(cc, cc), s2 = __dmul_rn(ss, ss);
+                        nj = __dadd_rn(__dmul_rn(c2, pd), __dmul_rn(s2, d0));
+                        nd = __dadd_rn(__dmul_rn(s2, pd), __dmul_rn(c2, d0));
                         nz = r;
                         nm = m0 | pmk;
                         nc = cc;
@@ -702,6 +799,22 @@ __global__ void __launch_bounds__(64) k_rotate(const MergeDesc* M, LevelWS ws)
         rot_apply(B, W, n, r, cur, cv);
     }
     if (cur >= 0) W[(int64_t)cur * n + r] = cv;
+}
+
+int td_binary_version(int* out)
+{
+    cudaFuncAttributes a;
+    if (cudaFuncGetAttributes(&a, k_prep) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    *out = a.binaryVersion;
+    return 0;
+}
+
+void td_launch_prep(const MergeDesc* M, int nmerge, const LevelWS& ws, cudaStream_t st)
+{
+    td_prof_begin(st); k_prep<<<nmerge, PREP_NT, 0, st>>>(M, ws); td_prof_end(st, "k_prep");
 }
 
 void td_launch_merge_level(const MergeDesc* M, int nmerge, int nmax, int rows, int total_tiles,
@@ -1056,12 +1169,7 @@ void td_launch_lowner_cauchy(const MergeDesc* M, int nmerge, int rows, int kmax,
     td_prof_begin(st); k_lowner<<<td_cdiv(rows, 8), 256, 0, st>>>(M, nmerge, rows, ws); td_prof_end(st, "k_lowner");
     size_t sm = (size_t)kmax * sizeof(double);
     if (sm <= CAUCHY_SMEM_MAX) {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_cauchy<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 CAUCHY_SMEM_MAX);
-            attr = true;
-        }
+        td_smem_attr((const void*)k_cauchy<true>, CAUCHY_SMEM_MAX);
         td_prof_begin(st); k_cauchy<true><<<rows, CAUCHY_NT, sm, st>>>(M, nmerge, rows, ws, write_qhat); td_prof_end(st, "k_cauchy");
     } else {
         td_prof_begin(st); k_cauchy<false><<<rows, CAUCHY_NT, 0, st>>>(M, nmerge, rows, ws, write_qhat); td_prof_end(st, "k_cauchy");
@@ -1336,9 +1444,12 @@ void td_launch_stage_init(const LevelWS& ws, int K, double rho, cudaStream_t st)
 // roots: code that has handed all free device memory to its own pool
 // allocator (a cudaMalloc there fails or fragments the pool), and code on a
 // latency-bound path where cudaMalloc's implicit device synchronisation is not
-// acceptable.  This variant of k_secular keeps its scratch -- the weights
-// rho z_j^2 and a status word -- in the file-scope array below, which every
-// GPU that loads the library holds until the process exits.
+// acceptable.  This variant of the secular stage keeps its scratch -- the
+// weights rho z_j^2 in FP64 and FP32, the FP32 pair of each pole, and a status
+// word -- in the file-scope array below, which every GPU that loads the
+// library holds until the process exits.  With that scratch it runs the same
+// per-root iteration as k_secular (FP32 midpoint value, two-pole start), so
+// its roots are those of tdeig_secular bit for bit.
 //
 // Host code cannot use the array's name as a device address: it is a host-side
 // stand-in.  The first call on each device (with that device current) looks
@@ -1346,28 +1457,43 @@ void td_launch_stage_init(const LevelWS& ws, int K, double rho, cudaStream_t st)
 // first call before any stream capture.  All calls share the array, so calls
 // whose work overlaps on the GPU (other streams, other host threads) race.
 // ---------------------------------------------------------------------------
-#define TD_NOALLOC_SLOTS (TDEIG_NOALLOC_MAX_K + 32)
+// layout in doubles: w [0, MAX_K); then MAX_K floats each of wf, dh, dl
+// (1.5 MAX_K doubles); then the status word
+#define TD_NOALLOC_F32 TDEIG_NOALLOC_MAX_K
+#define TD_NOALLOC_STATUS (TDEIG_NOALLOC_MAX_K + (3 * TDEIG_NOALLOC_MAX_K) / 2)
+#define TD_NOALLOC_SLOTS (TD_NOALLOC_STATUS + 32)
 static __device__ __align__(256) double td_noalloc_scratch[TD_NOALLOC_SLOTS];
 
 static std::mutex g_noalloc_mu;
 static double* g_noalloc_ptr[TD_NOALLOC_MAX_DEVICES];
 
-__global__ void k_noalloc_weights(const double* z, double rho, int K, double* w, int* status)
+// The weights and FP32 copies of one problem (as k_stage_init forms them for
+// tdeig_secular), and the status word cleared for this call.
+__global__ void k_noalloc_weights(const double* d, const double* z, double rho, int K, double* w,
+                                  float* wf, float* dh, float* dl, int* status)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) *status = 0;   // clear the status word the previous call left in the array
-    if (i < K) w[i] = rho * z[i] * z[i];
+    if (i < K) {
+        const double wi = rho * z[i] * z[i], di = d[i];
+        w[i] = wi;
+        const float h = __double2float_rn(di);
+        dh[i] = h;
+        dl[i] = __double2float_rn(di - (double)h);
+        wf[i] = __double2float_rn(wi);
+    }
 }
 
-__global__ void k_secular_noalloc(const double* d, const double* w, int K, int* status, double* lam,
-                                  double* gam, double* mu)
+__global__ void k_secular_noalloc(const double* d, const double* w, const float* wf,
+                                  const float* dh, const float* dl, int K, int* status,
+                                  double* lam, double* gam, double* mu)
 {
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= K) return;
     double l, g, m;
     int it;
-    secular_root_warp(d, w, K, i, lane, &l, &g, &m, &it);
+    secular_root_warp(d, w, K, i, lane, &l, &g, &m, &it, dh, dl, wf);
     if (lane == 0) {
         lam[i] = l;
         gam[i] = g;
@@ -1376,14 +1502,16 @@ __global__ void k_secular_noalloc(const double* d, const double* w, int K, int* 
     }
 }
 
-static bool noalloc_is_device(const void* p)
+// Device memory of the current device (host, managed or another device's
+// memory is rejected).
+static bool noalloc_on_device(const void* p, int dev)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 extern "C" int tdeig_secular_noalloc(int64_t K, const double* d, const double* z, double rho,
@@ -1391,12 +1519,15 @@ extern "C" int tdeig_secular_noalloc(int64_t K, const double* d, const double* z
 {
     if (K < 1 || K > TDEIG_NOALLOC_MAX_K) return TDEIG_EINVAL;
     if (!d || !z || !lambda || !gamma || !mu || !(rho > 0.0) || !isfinite(rho)) return TDEIG_EINVAL;
-    if (!noalloc_is_device(d) || !noalloc_is_device(z) || !noalloc_is_device(lambda) ||
-        !noalloc_is_device(gamma) || !noalloc_is_device(mu))
-        return TDEIG_EINVAL;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= TD_NOALLOC_MAX_DEVICES)
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= TD_NOALLOC_MAX_DEVICES) {
+        cudaGetLastError();
         return TDEIG_ECUDA;
+    }
+    if (!noalloc_on_device(d, dev) || !noalloc_on_device(z, dev) ||
+        !noalloc_on_device(lambda, dev) || !noalloc_on_device(gamma, dev) ||
+        !noalloc_on_device(mu, dev))
+        return TDEIG_EINVAL;
     double* scratch;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
@@ -1411,11 +1542,15 @@ extern "C" int tdeig_secular_noalloc(int64_t K, const double* d, const double* z
         scratch = g_noalloc_ptr[dev];
     }
     double* w = scratch;
-    int* status = (int*)(scratch + TDEIG_NOALLOC_MAX_K);
+    float* f32 = (float*)(scratch + TD_NOALLOC_F32);
+    float* wf = f32;
+    float* dh = f32 + TDEIG_NOALLOC_MAX_K;
+    float* dl = f32 + 2 * TDEIG_NOALLOC_MAX_K;
+    int* status = (int*)(scratch + TD_NOALLOC_STATUS);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int k = (int)K;
-    k_noalloc_weights<<<td_cdiv(k, 256), 256, 0, st>>>(z, rho, k, w, status);
-    k_secular_noalloc<<<td_cdiv(k, 8), 256, 0, st>>>(d, w, k, status, lambda, gamma, mu);
+    k_noalloc_weights<<<td_cdiv(k, 256), 256, 0, st>>>(d, z, rho, k, w, wf, dh, dl, status);
+    k_secular_noalloc<<<td_cdiv(k, 8), 256, 0, st>>>(d, w, wf, dh, dl, k, status, lambda, gamma, mu);
     if (cudaGetLastError() != cudaSuccess) return TDEIG_ECUDA;
     int hs = 0;
     if (cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||

@@ -337,6 +337,18 @@ __global__ void __launch_bounds__(HSS_NT) k_id(const IdDesc* D, int nd, double t
 
 static size_t id_smem(int s, int m) { return (size_t)s * m * 8 + (size_t)m * 20 + (size_t)s * 8 + 64; }
 
+int hss_launch_id(const IdDesc* dev, int nd, int smax, int mmax, double tol, cudaStream_t st)
+{
+    const size_t sm = id_smem(smax, mmax);
+    if (sm > 220 * 1024) return TDEIG_EINVAL;
+    if (nd <= 0) return TDEIG_OK;
+    td_smem_attr((const void*)k_id, 220 * 1024);
+    td_prof_begin(st);
+    k_id<<<(unsigned)nd, HSS_NT, sm, st>>>(dev, nd, tol);
+    td_prof_end(st, "k_id");
+    return TDEIG_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Gaussian sampling matrix: Omega[i, j] from Philox4x32-10 (Salmon, Moraes,
 // Dror, Shaw, SC'11) with counter (i, j, stream, 0) and key (seed low, seed
@@ -366,6 +378,38 @@ __global__ void k_philox_omega(double* Om, int K, int s, unsigned long long seed
     const double u1 = ((double)r.x + 0.5) * 2.3283064365386963e-10;
     const double u2 = ((double)r.y + 0.5) * 2.3283064365386963e-10;
     Om[t] = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+}
+
+// Raw Philox words for n counters (the stage entry point tdeig_philox4x32_10).
+__global__ void k_philox_words(const unsigned* ctr, const unsigned* key, unsigned* out, int64_t n)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const uint4 r = philox4x32_10(make_uint4(ctr[4 * t], ctr[4 * t + 1], ctr[4 * t + 2], ctr[4 * t + 3]),
+                                  make_uint2(key[2 * t], key[2 * t + 1]));
+    out[4 * t] = r.x;
+    out[4 * t + 1] = r.y;
+    out[4 * t + 2] = r.z;
+    out[4 * t + 3] = r.w;
+}
+
+void hss_launch_philox_words(const unsigned* ctr, const unsigned* key, unsigned* out, int64_t n,
+                             cudaStream_t st)
+{
+    if (n <= 0) return;
+    td_prof_begin(st);
+    k_philox_words<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ctr, key, out, n);
+    td_prof_end(st, "k_philox_words");
+}
+
+void hss_launch_gaussian(double* Om, int K, int s, unsigned long long seed, unsigned stream,
+                         cudaStream_t st)
+{
+    const int64_t tot = (int64_t)K * s;
+    if (tot <= 0) return;
+    td_prof_begin(st);
+    k_philox_omega<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Om, K, s, seed, stream);
+    td_prof_end(st, "k_philox_omega");
 }
 
 // ---------------------------------------------------------------------------
@@ -412,6 +456,15 @@ __global__ void k_rank_estimate(const RankDesc* Rd, int nr, double eps, int cap,
         r = max(r, rb);
     }
     *R.r_out = min(r, cap);
+}
+
+void hss_launch_rank_estimate(const RankDesc* dev, int nr, double eps, int cap, int shift,
+                              cudaStream_t st)
+{
+    if (nr <= 0) return;
+    td_prof_begin(st);
+    k_rank_estimate<<<td_cdiv(nr, 64), 64, 0, st>>>(dev, nr, eps, cap, shift);
+    td_prof_end(st, "k_rank_estimate");
 }
 
 // ---------------------------------------------------------------------------
@@ -1193,11 +1246,7 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
             int mmax = 0, smax = 0;
             for (auto& a : ids) { mmax = std::max(mmax, a.m); smax = std::max(smax, a.s); }
             size_t sm = id_smem(smax, mmax);
-            static bool attr = false;
-            if (!attr) {
-                cudaFuncSetAttribute(k_id, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-                attr = true;
-            }
+            td_smem_attr((const void*)k_id, 220 * 1024);
             td_prof_begin(st);
             k_id<<<(unsigned)ids.size(), HSS_NT, sm, st>>>(did, (int)ids.size(), opt.tol);
             td_prof_end(st, "k_id");
@@ -1423,10 +1472,26 @@ int hss_update_level(const tdeig_options& opt, int variant, int prec,
             }
         snprintf(buf, sizeof(buf),
                  "%s{\"n\":%d,\"K\":%d,\"L\":%d,\"r\":%d,\"s\":%d,\"kmax\":%d,\"kmean\":%.2f,"
-                 "\"r_est\":%d,\"seed\":%d}",
+                 "\"r_est\":%d,\"seed\":%d,\"node\":%d,\"bounds\":[",
                  js.empty() ? "" : ",", h.n, h.K, h.L, h.r, h.s, kmax, cnt ? ksum / cnt : 0.0, h.r_est,
-                 h.seed);
+                 h.seed, h.node_id);
         js += buf;
+        // the (moved) leaf boundaries, then every node's (row, column) ID ranks,
+        // levels 1..L left to right
+        for (size_t q = 0; q < h.bounds.size(); q++) {
+            snprintf(buf, sizeof(buf), "%s%d", q ? "," : "", h.bounds[q]);
+            js += buf;
+        }
+        js += "],\"node_ranks\":[";
+        bool first = true;
+        for (int l = 1; l <= h.L; l++)
+            for (int q = 0; q < (1 << l); q++) {
+                const HNode& nd = h.nodes[hidx(l, q)];
+                snprintf(buf, sizeof(buf), "%s[%d,%d]", first ? "" : ",", nd.kU, nd.kV);
+                js += buf;
+                first = false;
+            }
+        js += "]}";
     }
     return prc;
 }

@@ -206,11 +206,7 @@ void mlp_launch(const float* params, const float* mean, const float* stdv, const
 {
     if (n <= 0) return;
     const size_t smem = MLP_SMEM_FLOATS * sizeof(float);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    td_smem_attr((const void*)k_mlp, smem);
     td_prof_begin(st);
     k_mlp<<<td_cdiv(n, MLP_NT), MLP_NT, smem, st>>>(params, mean, stdv, X, t, perm, n, n_total, y,
                                                     grad, loss);

@@ -263,10 +263,6 @@ __global__ void __launch_bounds__(256, 4) k_slice7(const SliceDesc* D)
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-double g_split_tensor_flops = 0.0;
-double g_split_slice_bytes = 0.0;
-double g_split_exp_bytes = 0.0;
-
 void split_free(SplitWS& w)
 {
     if (w.base) cudaFree(w.base);
@@ -476,7 +472,8 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
     }
     td_prof_end(st, "k_slice");
     umma_launch(dsg, dt0, (int)sg.size(), tiles, pr.s, pr.nacc, status, st);
-    if (g_td_prof.on) {
+    TdCtx& cx = td_ctx();
+    if (cx.prof.on) {
         // [tiles, k-blocks over all tiles, slices, problems, tensor flops]
         double kbl = 0.0;
         for (size_t i = 0; i < g.size(); i++)
@@ -485,9 +482,9 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
         snprintf(nb, sizeof(nb), "[%d,%.0f,%d,%d,%.6e]", tiles, kbl, pr.s, (int)g.size(), tflops);
         td_prof_note(nb);
     }
-    g_split_tensor_flops += tflops;
-    g_split_slice_bytes += sbytes;
-    g_split_exp_bytes += ebytes;
+    cx.split_tensor_flops += tflops;
+    cx.split_slice_bytes += sbytes;
+    cx.split_exp_bytes += ebytes;
     if (cudaGetLastError() != cudaSuccess) *rc = TDEIG_ECUDA;
     return flops;
 }

@@ -520,18 +520,8 @@ void umma_launch(const SplitGemmDesc* dev, const int* tile0, int ng, int tiles, 
     nacc = nacc < 1 ? 1 : nacc > UM_NACC_MAX ? UM_NACC_MAX : nacc;
     int nst = 0;
     const size_t smem = umma_smem_bytes(smax, ng, &nst);
-    static size_t attr = 0;
-    static int nsm = 0;
-    if (!nsm) {
-        int dev_id = 0;
-        cudaGetDevice(&dev_id);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_id);
-        if (nsm <= 0) nsm = 1;
-    }
-    if (smem > attr) {
-        cudaFuncSetAttribute(k_split_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = smem;
-    }
+    const int nsm = td_sm_count();
+    td_smem_attr((const void*)k_split_umma, smem);
     const int grid = tiles < nsm ? tiles : nsm;
     td_prof_begin(st);
     k_split_umma<<<grid, UM_NT, smem, st>>>(dev, tile0, ng, tiles, smax, nst, nacc, status);

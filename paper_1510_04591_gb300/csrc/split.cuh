@@ -90,8 +90,5 @@ struct SplitWS {
 // status: device word that receives TD_STATUS_TIMEOUT when a bounded wait expires.
 double split_launch_gemm(const std::vector<GemmDesc>& g, SplitWS& ws, cudaStream_t st, int* rc,
                          int* status, int kind, int bits);
-// Tensor-core work issued by split products so far: 2 M N K per slice pair.
-extern double g_split_tensor_flops;
-extern double g_split_slice_bytes;   // algorithmic bytes of k_slice (read 8 B, write 2 s B per element)
-extern double g_split_exp_bytes;     // algorithmic bytes of k_slice_exp (read 8 B per element)
+// Work counters of the launches go to td_ctx() (common.cuh).
 void split_free(SplitWS& ws);

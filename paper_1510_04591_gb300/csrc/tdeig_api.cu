@@ -77,6 +77,7 @@ struct tdeig_ctx {
     float* mlp = nullptr;              // rank model on the device: params, mean, std
     std::vector<float> records;        // TDEIG_FLAG_RECORD output of the last solve
     int mlp_fallbacks = 0;             // merges rebuilt with the estimate in the last solve
+    TdCtx ctx;                         // launch count, split work counters, kernel timing
 };
 
 static const char* kStatusMsg[] = {
@@ -151,6 +152,7 @@ extern "C" int tdeig_destroy(tdeig_handle h)
     split_free(h->split);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     for (cudaEvent_t e : h->tune_ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->ctx.prof.ev) cudaEventDestroy(e);
     if (h->graph.exec) cudaGraphExecDestroy(h->graph.exec);
     if (h->mlp) cudaFree(h->mlp);
     if (h->own_stream) cudaStreamDestroy(h->stream);
@@ -462,15 +464,18 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
         prec != TDEIG_PREC_FP16X2)
         return TDEIG_EINVAL;
     auto t_start = std::chrono::steady_clock::now();
-    const long long launches0 = g_td_launches;
-    const double split_flops0 = g_split_tensor_flops;
-    const double slice_bytes0 = g_split_slice_bytes, exp_bytes0 = g_split_exp_bytes;
+    TdCtx& cx = h->ctx;
+    const long long launches0 = cx.launches;
+    const double split_flops0 = cx.split_tensor_flops;
+    const double slice_bytes0 = cx.split_slice_bytes, exp_bytes0 = cx.split_exp_bytes;
+    TdProf& prof = cx.prof;
     // per-kernel events only for this solve (see TDEIG_FLAG_PROFILE)
     struct ProfOff {
-        ~ProfOff() { g_td_prof.on = false; }
-    } prof_off;
-    g_td_prof.on = false;
-    g_td_prof.n = 0;
+        TdProf& p;
+        ~ProfOff() { p.on = false; }
+    } prof_off{prof};
+    prof.on = false;
+    prof.n = 0;
 
     Plan P;
     P.members = (int)batch;
@@ -639,7 +644,7 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
         cap.active = true;
     }
     CU(cudaMemsetAsync(status, 0, 64 * sizeof(int), st));
-    g_td_prof.on = (mode & TDEIG_FLAG_PROFILE) && !graph;
+    prof.on = (mode & TDEIG_FLAG_PROFILE) && !graph;
 
     // Stage timing: an event before each stage and one at the end, on the
     // handle's stream; read after the final synchronisation (not in graph mode).
@@ -824,20 +829,20 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
         // per-kernel device time of a profiled solve: "after" event minus "before"
         std::string kj;
         char kb[200];
-        if (g_td_prof.on) {
+        if (prof.on) {
             std::vector<std::pair<std::string, std::pair<double, int>>> agg;
-            for (size_t i = 1; i < g_td_prof.n; i++) {
-                if (!g_td_prof.name[i] || g_td_prof.name[i - 1]) continue;
+            for (size_t i = 1; i < prof.n; i++) {
+                if (!prof.name[i] || prof.name[i - 1]) continue;
                 float ms = 0.f;
-                cudaEventElapsedTime(&ms, g_td_prof.ev[i - 1], g_td_prof.ev[i]);
+                cudaEventElapsedTime(&ms, prof.ev[i - 1], prof.ev[i]);
                 bool found = false;
                 for (auto& a : agg)
-                    if (a.first == g_td_prof.name[i]) {
+                    if (a.first == prof.name[i]) {
                         a.second.first += ms;
                         a.second.second++;
                         found = true;
                     }
-                if (!found) agg.push_back({g_td_prof.name[i], {ms, 1}});
+                if (!found) agg.push_back({prof.name[i], {ms, 1}});
             }
             kj = ",\"kernels\":{";
             for (size_t i = 0; i < agg.size(); i++) {
@@ -848,25 +853,25 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
             kj += "}";
             // launches with a shape note: [ms, note...]
             std::string lj;
-            for (size_t i = 1; i < g_td_prof.n; i++) {
-                if (!g_td_prof.name[i] || g_td_prof.name[i - 1] || g_td_prof.note[i].empty()) continue;
+            for (size_t i = 1; i < prof.n; i++) {
+                if (!prof.name[i] || prof.name[i - 1] || prof.note[i].empty()) continue;
                 float ms = 0.f;
-                cudaEventElapsedTime(&ms, g_td_prof.ev[i - 1], g_td_prof.ev[i]);
-                snprintf(kb, sizeof(kb), "%s[\"%s\",%.6f,", lj.empty() ? "" : ",", g_td_prof.name[i], ms);
-                lj += kb + g_td_prof.note[i].substr(1);
+                cudaEventElapsedTime(&ms, prof.ev[i - 1], prof.ev[i]);
+                snprintf(kb, sizeof(kb), "%s[\"%s\",%.6f,", lj.empty() ? "" : ",", prof.name[i], ms);
+                lj += kb + prof.note[i].substr(1);
             }
             if (!lj.empty()) kj += ",\"launch_shapes\":[" + lj + "]";
         }
         snprintf(kb, sizeof(kb), ",\"split_tensor_flops\":%.6e,\"split_slice_bytes\":%.6e,\"split_exp_bytes\":%.6e",
-                 g_split_tensor_flops - split_flops0, g_split_slice_bytes - slice_bytes0,
-                 g_split_exp_bytes - exp_bytes0);
+                 cx.split_tensor_flops - split_flops0, cx.split_slice_bytes - slice_bytes0,
+                 cx.split_exp_bytes - exp_bytes0);
         kj += kb;
         h->stats.pop_back();
         h->stats += kj + "}";
     }
     {
         char lb[64];
-        snprintf(lb, sizeof(lb), ",\"launches\":%lld}", g_td_launches - launches0);
+        snprintf(lb, sizeof(lb), ",\"launches\":%lld}", cx.launches - launches0);
         h->stats.pop_back();
         h->stats += lb;
     }
@@ -880,6 +885,7 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
 extern "C" int tdeig_solve(tdeig_handle h, const double* d, const double* e, int64_t N,
                            double* lambda_out, double* Q_out, int mode)
 {
+    TdCtxScope ctx_scope_(h ? &h->ctx : nullptr);
     if (!h || N < 0) return TDEIG_EINVAL;
     if (N == 0) return TDEIG_OK;
     if (!d || !lambda_out || (N > 1 && !e)) return TDEIG_EINVAL;
@@ -892,6 +898,7 @@ extern "C" int tdeig_solve_batched(tdeig_handle h, int64_t batch, const int64_t*
                                    const double* d_cat, const double* e_cat, double* lambda_cat,
                                    double* Q_cat, int mode)
 {
+    TdCtxScope ctx_scope_(h ? &h->ctx : nullptr);
     if (!h || batch < 0 || (batch > 0 && !N_each)) return TDEIG_EINVAL;
     if (batch == 0) return TDEIG_OK;
     int64_t R = 0, E = 0;
@@ -979,6 +986,7 @@ static int stage_setup(tdeig_ctx* h, int64_t K, int64_t qelems, Arena& ar, Level
 extern "C" int tdeig_secular(tdeig_handle h, int64_t K, const double* d, const double* z, double rho,
                              double* lambda, double* gamma, double* mu)
 {
+    TdCtxScope ctx_scope_(h ? &h->ctx : nullptr);
     if (!h || K < 1 || K > (1 << 24) || !d || !z || !lambda || !gamma || !mu) return TDEIG_EINVAL;
     if (!(rho > 0.0) || !isfinite(rho)) return TDEIG_EINVAL;
     CU(cudaSetDevice(h->device));
@@ -1007,6 +1015,7 @@ extern "C" int tdeig_lowner_cauchy(tdeig_handle h, int64_t K, const double* d, c
                                    const double* mu, const double* z, double rho, double* uhat,
                                    double* v, double* Qhat)
 {
+    TdCtxScope ctx_scope_(h ? &h->ctx : nullptr);
     if (!h || K < 1 || K > (1 << 20) || !d || !gamma || !mu || !z || !uhat || !v) return TDEIG_EINVAL;
     if (!(rho > 0.0) || !isfinite(rho)) return TDEIG_EINVAL;
     CU(cudaSetDevice(h->device));
@@ -1035,6 +1044,225 @@ extern "C" int tdeig_lowner_cauchy(tdeig_handle h, int64_t K, const double* d, c
     if (Qhat && !qdev) CU(cudaMemcpyAsync(Qhat, qbuf, K * K * sizeof(double), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     return TDEIG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Stage entry points of the method's integer decisions -- deflation, the rank
+// estimate, the interpolative decomposition -- and of the Philox generator of
+// the sampling matrix.  Each runs the solver's own kernel on given inputs.
+// ---------------------------------------------------------------------------
+static int copy_bytes_out(void* dst, const void* src, size_t bytes, cudaStream_t st)
+{
+    if (!dst || bytes == 0) return TDEIG_OK;
+    cudaMemcpyKind k = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CU(cudaMemcpyAsync(dst, src, bytes, k, st));
+    return TDEIG_OK;
+}
+
+static int copy_bytes_in(void* dst, const void* src, size_t bytes, cudaStream_t st)
+{
+    if (!src || bytes == 0) return TDEIG_OK;
+    cudaMemcpyKind k = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CU(cudaMemcpyAsync(dst, src, bytes, k, st));
+    return TDEIG_OK;
+}
+
+extern "C" int tdeig_merge_deflate(tdeig_handle h, int64_t n1, int64_t n2, const double* lam1,
+                                   const double* lam2, const double* z1, const double* z2,
+                                   double beta, int32_t* perm, double* d_out, double* z_out,
+                                   int32_t* keep, double* rho_out, int64_t* counts,
+                                   int32_t* rot_j, int32_t* rot_i, double* rot_c, double* rot_s)
+{
+    if (!h || n1 < 1 || n2 < 1 || n1 + n2 > (1 << 24) || !lam1 || !lam2 || !z1 || !z2)
+        return TDEIG_EINVAL;
+    if (!isfinite(beta)) return TDEIG_EINVAL;
+    TdCtxScope ctx_scope_(&h->ctx);
+    CU(cudaSetDevice(h->device));
+    const int64_t n = n1 + n2;
+    cudaStream_t st = h->stream;
+    int rc = ensure_ws(h, level_ws_bytes(n, 1) + (size_t)(2 * n + 8) * sizeof(double) + 64 * 1024);
+    if (rc) return rc;
+    Arena ar{h->ws, 0, h->ws_bytes};
+    LevelWS lws;
+    carve_level_ws(ar, lws, n, 1);
+    double* lam_in = ar.take<double>(n);
+    double* zin = ar.take<double>(n);
+    double* bet = ar.take<double>(1);
+    MergeDesc* md = ar.take<MergeDesc>(1);
+    if (ar.off > ar.cap) return TDEIG_ENOMEM;
+    if ((rc = copy_in(lam_in, lam1, n1, st)) || (rc = copy_in(lam_in + n1, lam2, n2, st)) ||
+        (rc = copy_in(zin, z1, n1, st)) || (rc = copy_in(zin + n1, z2, n2, st)))
+        return rc;
+    MergeDesc m;
+    memset(&m, 0, sizeof(m));
+    m.g0 = 0;
+    m.n = (int)n;
+    m.n1 = (int)n1;
+    m.lam_in = lam_in;
+    m.beta_ptr = bet;
+    m.z1 = zin;
+    m.z2 = zin + n1;
+    m.tiles_m = 1;
+    CU(cudaMemcpyAsync(bet, &beta, sizeof(double), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(md, &m, sizeof(m), cudaMemcpyHostToDevice, st));
+    td_launch_prep(md, 1, lws, st);
+    CU(cudaGetLastError());
+    int kn[2] = {0, 0};
+    double rho = 0.0;
+    CU(cudaMemcpyAsync(&kn[0], lws.K, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(&kn[1], lws.nrot, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(&rho, lws.rho, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    const size_t nr = (size_t)kn[1];
+    if ((rc = copy_bytes_out(perm, lws.src, n * sizeof(int), st)) ||
+        (rc = copy_bytes_out(d_out, lws.dsort, n * sizeof(double), st)) ||
+        (rc = copy_bytes_out(z_out, lws.zsort, n * sizeof(double), st)) ||
+        (rc = copy_bytes_out(keep, lws.keep, n * sizeof(int), st)) ||
+        (rc = copy_bytes_out(rot_j, lws.rot_j, nr * sizeof(int), st)) ||
+        (rc = copy_bytes_out(rot_i, lws.rot_i, nr * sizeof(int), st)) ||
+        (rc = copy_bytes_out(rot_c, lws.rot_c, nr * sizeof(double), st)) ||
+        (rc = copy_bytes_out(rot_s, lws.rot_s, nr * sizeof(double), st)))
+        return rc;
+    CU(cudaStreamSynchronize(st));
+    if (rho_out) *rho_out = rho;
+    if (counts) { counts[0] = kn[0]; counts[1] = kn[1]; }
+    return TDEIG_OK;
+}
+
+extern "C" int tdeig_rank_estimate(tdeig_handle h, int64_t K, const double* d, const double* gamma,
+                                   int64_t nl, int32_t* bounds, int32_t* r_out)
+{
+    if (!h || K < 2 || K > (1 << 26) || !d || !gamma || nl < 1 || nl > K || !bounds || !r_out)
+        return TDEIG_EINVAL;
+    if (bounds[0] != 0 || bounds[nl] != K) return TDEIG_EINVAL;
+    for (int64_t q = 0; q < nl; q++)
+        if (bounds[q + 1] <= bounds[q]) return TDEIG_EINVAL;
+    TdCtxScope ctx_scope_(&h->ctx);
+    CU(cudaSetDevice(h->device));
+    cudaStream_t st = h->stream;
+    int rc = ensure_ws(h, 2 * (size_t)K * sizeof(double) + (size_t)(nl + 1) * sizeof(int) +
+                              sizeof(RankDesc) + 4096);
+    if (rc) return rc;
+    Arena ar{h->ws, 0, h->ws_bytes};
+    double* dd = ar.take<double>(K);
+    double* dg = ar.take<double>(K);
+    int* db = ar.take<int>(nl + 1);
+    int* dr = ar.take<int>(1);
+    RankDesc* drd = ar.take<RankDesc>(1);
+    if (ar.off > ar.cap) return TDEIG_ENOMEM;
+    if ((rc = copy_in(dd, d, K, st)) || (rc = copy_in(dg, gamma, K, st))) return rc;
+    RankDesc r;
+    r.d = dd; r.gam = dg; r.K = (int)K; r.nl = (int)nl; r.bounds = db; r.r_out = dr;
+    CU(cudaMemcpyAsync(db, bounds, (nl + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(drd, &r, sizeof(r), cudaMemcpyHostToDevice, st));
+    hss_launch_rank_estimate(drd, 1, h->opt.rank_eps, h->opt.rank_cap, h->opt.boundary_shift, st);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(bounds, db, (nl + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(r_out, dr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    return TDEIG_OK;
+}
+
+extern "C" int tdeig_interp_decomp(tdeig_handle h, int64_t m, int64_t s, const double* Phi,
+                                   int64_t ldphi, double* U, int64_t ldu, int32_t* piv,
+                                   int32_t* rank_out)
+{
+    if (!h || m < 1 || s < 1 || m > 4096 || s > 4096 || !Phi || ldphi < m || !U || ldu < m ||
+        !piv || !rank_out)
+        return TDEIG_EINVAL;
+    TdCtxScope ctx_scope_(&h->ctx);
+    CU(cudaSetDevice(h->device));
+    cudaStream_t st = h->stream;
+    const int64_t kc = std::min(m, s);
+    int rc = ensure_ws(h, ((size_t)ldphi * s + (size_t)m * kc) * sizeof(double) +
+                              (size_t)(2 * kc + 2) * sizeof(int) + sizeof(IdDesc) + 4096);
+    if (rc) return rc;
+    Arena ar{h->ws, 0, h->ws_bytes};
+    double* dphi = ar.take<double>((size_t)ldphi * s);
+    double* dU = ar.take<double>((size_t)m * kc);
+    int* dpiv = ar.take<int>(kc);
+    int* didx = ar.take<int>(kc);
+    int* drk = ar.take<int>(1);
+    IdDesc* did = ar.take<IdDesc>(1);
+    if (ar.off > ar.cap) return TDEIG_ENOMEM;
+    if ((rc = copy_in(dphi, Phi, ldphi * s, st))) return rc;
+    IdDesc a;
+    memset(&a, 0, sizeof(a));
+    a.Phi = dphi; a.ldphi = (int)ldphi; a.m = (int)m; a.s = (int)s; a.rowbase = 0;
+    a.U = dU; a.ldu = (int)m; a.out_idx = didx; a.out_piv = dpiv; a.out_rank = drk;
+    CU(cudaMemcpyAsync(did, &a, sizeof(a), cudaMemcpyHostToDevice, st));
+    CU(cudaMemsetAsync(dU, 0, (size_t)m * kc * sizeof(double), st));
+    if ((rc = hss_launch_id(did, 1, (int)s, (int)m, h->opt.tol, st))) return rc;
+    CU(cudaGetLastError());
+    int rk = 0;
+    CU(cudaMemcpyAsync(&rk, drk, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (rk > 0) {
+        const bool udev = is_device_ptr(U);
+        CU(cudaMemcpy2DAsync(U, ldu * sizeof(double), dU, m * sizeof(double), m * sizeof(double), rk,
+                             udev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+        if ((rc = copy_bytes_out(piv, dpiv, (size_t)rk * sizeof(int), st))) return rc;
+    }
+    CU(cudaStreamSynchronize(st));
+    *rank_out = rk;
+    return TDEIG_OK;
+}
+
+extern "C" int tdeig_philox4x32_10(tdeig_handle h, int64_t n, const uint32_t* ctr,
+                                   const uint32_t* key, uint32_t* out)
+{
+    if (!h || n < 0 || n > ((int64_t)1 << 28) || (n > 0 && (!ctr || !key || !out)))
+        return TDEIG_EINVAL;
+    if (n == 0) return TDEIG_OK;
+    TdCtxScope ctx_scope_(&h->ctx);
+    CU(cudaSetDevice(h->device));
+    cudaStream_t st = h->stream;
+    int rc = ensure_ws(h, (size_t)n * 10 * sizeof(uint32_t) + 4096);
+    if (rc) return rc;
+    Arena ar{h->ws, 0, h->ws_bytes};
+    unsigned* dc = ar.take<unsigned>(4 * n);
+    unsigned* dk = ar.take<unsigned>(2 * n);
+    unsigned* dout = ar.take<unsigned>(4 * n);
+    if (ar.off > ar.cap) return TDEIG_ENOMEM;
+    if ((rc = copy_bytes_in(dc, ctr, 4 * n * sizeof(unsigned), st)) ||
+        (rc = copy_bytes_in(dk, key, 2 * n * sizeof(unsigned), st)))
+        return rc;
+    hss_launch_philox_words(dc, dk, dout, n, st);
+    CU(cudaGetLastError());
+    if ((rc = copy_bytes_out(out, dout, 4 * n * sizeof(unsigned), st))) return rc;
+    CU(cudaStreamSynchronize(st));
+    return TDEIG_OK;
+}
+
+extern "C" int tdeig_gaussian(tdeig_handle h, int64_t nrow, int64_t ncol, uint64_t seed,
+                              uint32_t stream_id, double* out)
+{
+    if (!h || nrow < 0 || ncol < 0 || nrow > (1 << 28) || ncol > (1 << 20) ||
+        nrow * ncol > ((int64_t)1 << 31) || (nrow * ncol > 0 && !out))
+        return TDEIG_EINVAL;
+    if (nrow * ncol == 0) return TDEIG_OK;
+    TdCtxScope ctx_scope_(&h->ctx);
+    CU(cudaSetDevice(h->device));
+    cudaStream_t st = h->stream;
+    const bool odev = is_device_ptr(out);
+    double* dst = out;
+    if (!odev) {
+        int rc = ensure_ws(h, (size_t)nrow * ncol * sizeof(double) + 4096);
+        if (rc) return rc;
+        dst = (double*)h->ws;
+    }
+    hss_launch_gaussian(dst, (int)nrow, (int)ncol, (unsigned long long)seed, stream_id, st);
+    CU(cudaGetLastError());
+    if (!odev)
+        CU(cudaMemcpyAsync(out, dst, (size_t)nrow * ncol * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    return TDEIG_OK;
+}
+
+extern "C" int tdeig_binary_arch(int* arch)
+{
+    if (!arch) return TDEIG_EINVAL;
+    return td_binary_version(arch) == 0 ? TDEIG_OK : TDEIG_ECUDA;
 }
 
 // ---------------------------------------------------------------------------
@@ -1088,6 +1316,7 @@ static int model_scratch(DevBuf& b, int64_t n, float** P, float** mean, float** 
 extern "C" int tdeig_mlp_forward(tdeig_handle h, const float* params, const float* mean,
                                  const float* std, const float* X, int64_t n, float* y)
 {
+    TdCtxScope ctx_scope_(h ? &h->ctx : nullptr);
     if (!h || !params || !mean || !std || n < 0 || (n > 0 && (!X || !y)) || n > (1 << 26))
         return TDEIG_EINVAL;
     if (n == 0) return TDEIG_OK;
@@ -1112,6 +1341,7 @@ extern "C" int tdeig_mlp_grad(tdeig_handle h, const float* params, const float* 
                               const float* std, const float* X, const float* t, int64_t n,
                               float* loss, float* grad)
 {
+    TdCtxScope ctx_scope_(h ? &h->ctx : nullptr);
     if (!h || !params || !mean || !std || !X || !t || !loss || !grad || n < 1 || n > (1 << 26))
         return TDEIG_EINVAL;
     CU(cudaSetDevice(h->device));
@@ -1138,6 +1368,7 @@ extern "C" int tdeig_mlp_train(tdeig_handle h, float* params, const float* mean,
                                const float* X, const float* t, int64_t n, int epochs, int batch,
                                float lr, uint64_t seed, float* final_loss)
 {
+    TdCtxScope ctx_scope_(h ? &h->ctx : nullptr);
     if (!h || !params || !mean || !std || !X || !t || n < 1 || n > (1 << 26) || epochs < 0 ||
         batch < 1 || !(lr > 0.0f))
         return TDEIG_EINVAL;
@@ -1187,6 +1418,7 @@ extern "C" int tdeig_mlp_train(tdeig_handle h, float* params, const float* mean,
 extern "C" int tdeig_set_rank_model(tdeig_handle h, const float* params, const float* mean,
                                     const float* std)
 {
+    TdCtxScope ctx_scope_(h ? &h->ctx : nullptr);
     if (!h) return TDEIG_EINVAL;
     CU(cudaSetDevice(h->device));
     if (!params) {
@@ -1211,6 +1443,7 @@ extern "C" int tdeig_set_rank_model(tdeig_handle h, const float* params, const f
 
 extern "C" int tdeig_rank_records(tdeig_handle h, float* buf, int64_t cap)
 {
+    TdCtxScope ctx_scope_(h ? &h->ctx : nullptr);
     if (!h || cap < 0 || (cap > 0 && !buf)) return TDEIG_EINVAL;
     const int64_t n = (int64_t)h->records.size() / (MLP_IN + 1);
     const int64_t c = std::min(n, cap);
@@ -1222,6 +1455,7 @@ extern "C" int tdeig_node_features(tdeig_handle h, int64_t K, int64_t n, const d
                                    const double* gamma, const double* mu, const double* uhat,
                                    int64_t nb, const int* ranges, float* out)
 {
+    TdCtxScope ctx_scope_(h ? &h->ctx : nullptr);
     if (!h || K < 1 || K > (1 << 26) || n < K || nb < 0 || nb > (1 << 20)) return TDEIG_EINVAL;
     if (!d || !gamma || !mu || !uhat || (nb > 0 && (!ranges || !out))) return TDEIG_EINVAL;
     for (int64_t i = 0; i < nb; i++)
@@ -1265,6 +1499,7 @@ extern "C" int tdeig_split_gemm(tdeig_handle h, int64_t M, int64_t N, int64_t K,
                                 int64_t lda, int transA, const double* B, int64_t ldb, int transB,
                                 double* C, int64_t ldc, int prec, int bits)
 {
+    TdCtxScope ctx_scope_(h ? &h->ctx : nullptr);
     if (!h || M < 0 || N < 0 || K < 0 || M > (1 << 24) || N > (1 << 24) || K > (1 << 24))
         return TDEIG_EINVAL;
     if (prec != TDEIG_PREC_SPLIT && prec != TDEIG_PREC_BF16X2 && prec != TDEIG_PREC_FP16X2)

@@ -94,6 +94,19 @@ def lib():
         L.tdeig_split_gemm.argtypes = [_vp, _i64, _i64, _i64, _vp, _i64, ctypes.c_int, _vp, _i64,
                                        ctypes.c_int, _vp, _i64, ctypes.c_int, ctypes.c_int]
         L.tdeig_split_gemm.restype = ctypes.c_int
+        L.tdeig_merge_deflate.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp, _vp, ctypes.c_double,
+                                          _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.tdeig_merge_deflate.restype = ctypes.c_int
+        L.tdeig_rank_estimate.argtypes = [_vp, _i64, _vp, _vp, _i64, _vp, _vp]
+        L.tdeig_rank_estimate.restype = ctypes.c_int
+        L.tdeig_interp_decomp.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _vp]
+        L.tdeig_interp_decomp.restype = ctypes.c_int
+        L.tdeig_philox4x32_10.argtypes = [_vp, _i64, _vp, _vp, _vp]
+        L.tdeig_philox4x32_10.restype = ctypes.c_int
+        L.tdeig_gaussian.argtypes = [_vp, _i64, _i64, ctypes.c_uint64, ctypes.c_uint32, _vp]
+        L.tdeig_gaussian.restype = ctypes.c_int
+        L.tdeig_binary_arch.argtypes = [_vp]
+        L.tdeig_binary_arch.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -334,6 +347,78 @@ class Solver:
         if st != OK:
             raise TdeigError(st, "tdeig_split_gemm")
         return C
+
+    # ----------------------------------------------------------------------
+    # stage entry points of the integer decisions (host numpy arrays)
+    # ----------------------------------------------------------------------
+    def merge_deflate(self, lam1, lam2, z1, z2, beta):
+        """Sort and deflation of one merge; returns a dict (perm, d, z, keep, rho, K,
+        rotations (j, i, c, s))."""
+        lam1, lam2, z1, z2 = (np.ascontiguousarray(x, dtype=np.float64) for x in (lam1, lam2, z1, z2))
+        n1, n2 = len(lam1), len(lam2)
+        n = n1 + n2
+        perm = np.empty(n, dtype=np.int32)
+        keep = np.empty(n, dtype=np.int32)
+        d = np.empty(n)
+        z = np.empty(n)
+        rj = np.empty(n, dtype=np.int32)
+        ri = np.empty(n, dtype=np.int32)
+        rc = np.empty(n)
+        rs = np.empty(n)
+        rho = np.zeros(1)
+        cnt = np.zeros(2, dtype=np.int64)
+        st = lib().tdeig_merge_deflate(self.h, n1, n2, _ptr(lam1), _ptr(lam2), _ptr(z1), _ptr(z2),
+                                       float(beta), _ptr(perm), _ptr(d), _ptr(z), _ptr(keep),
+                                       _ptr(rho), _ptr(cnt), _ptr(rj), _ptr(ri), _ptr(rc), _ptr(rs))
+        if st != OK:
+            raise TdeigError(st, "tdeig_merge_deflate")
+        m = int(cnt[1])
+        return {"perm": perm, "d": d, "z": z, "keep": keep, "rho": float(rho[0]), "K": int(cnt[0]),
+                "rot": (rj[:m], ri[:m], rc[:m], rs[:m])}
+
+    def rank_estimate(self, d, gamma, bounds):
+        """(r, moved bounds) of eq. (bounds) with the handle's options."""
+        d, gamma = (np.ascontiguousarray(x, dtype=np.float64) for x in (d, gamma))
+        b = np.ascontiguousarray(np.asarray(bounds, dtype=np.int32)).copy()
+        r = np.zeros(1, dtype=np.int32)
+        st = lib().tdeig_rank_estimate(self.h, len(d), _ptr(d), _ptr(gamma), len(b) - 1, _ptr(b),
+                                       _ptr(r))
+        if st != OK:
+            raise TdeigError(st, "tdeig_rank_estimate")
+        return int(r[0]), b
+
+    def interp_decomp(self, Phi):
+        """Row ID Phi ~= U Phi[piv]: returns (U m x rank, piv)."""
+        Phi = np.asfortranarray(np.asarray(Phi, dtype=np.float64))
+        m, s = Phi.shape
+        k = min(m, s)
+        U = np.zeros((m, k), order="F")
+        piv = np.zeros(k, dtype=np.int32)
+        rk = np.zeros(1, dtype=np.int32)
+        st = lib().tdeig_interp_decomp(self.h, m, s, Phi.ctypes.data, m, U.ctypes.data, m,
+                                       _ptr(piv), _ptr(rk))
+        if st != OK:
+            raise TdeigError(st, "tdeig_interp_decomp")
+        r = int(rk[0])
+        return U[:, :r].copy(), piv[:r].copy()
+
+    def philox(self, ctr, key):
+        """Philox4x32-10 words for counters ctr (n x 4) and keys key (n x 2), uint32."""
+        ctr = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
+        key = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(-1, 2))
+        out = np.empty_like(ctr)
+        st = lib().tdeig_philox4x32_10(self.h, ctr.shape[0], _ptr(ctr), _ptr(key), _ptr(out))
+        if st != OK:
+            raise TdeigError(st, "tdeig_philox4x32_10")
+        return out
+
+    def gaussian(self, nrow, ncol, seed, stream_id):
+        """The sampling matrix Omega (nrow x ncol) as the solver draws it."""
+        out = np.empty((nrow, ncol), order="F")
+        st = lib().tdeig_gaussian(self.h, nrow, ncol, int(seed), int(stream_id), out.ctypes.data)
+        if st != OK:
+            raise TdeigError(st, "tdeig_gaussian")
+        return out
 
     def rank_records(self):
         """(features n x 7, ln(rank + 1) n) recorded by the last TDEIG_FLAG_RECORD solve."""

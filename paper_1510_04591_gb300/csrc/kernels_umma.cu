@@ -17,11 +17,13 @@
 //     sectors); a stage completes its `full` mbarrier by transaction count and
 //     is refilled after its `empty` mbarrier (tcgen05.commit of the MMAs that
 //     read it) completed;
-//   * warp 1, one thread (MMA issuer): tcgen05.mma (M 128, N 32, K 16, 16-bit
-//     in, FP32 out; the two k-steps of a block advance the descriptors' start
-//     address by 32 B inside the swizzle atom) for every pair p + q <= s - 1
-//     into the TMEM accumulator of
-//     its level p + q; a level's integer sum stays exact over a k-chunk of the
+//   * warp 1, one thread (MMA issuer): tcgen05.mma (M 128, K 16, 16-bit in,
+//     FP32 out; the two k-steps of a block advance the descriptors' start
+//     address by 32 B inside the swizzle atom), one per slice p of op(A)
+//     against the partner slices q = 0..s-1-p of op(B) taken together as one
+//     operand of N = 32 (s - p) rows, into the TMEM accumulators of levels
+//     p..s-1 (32 columns each, side by side), so that every pair p + q <= s - 1
+//     lands in the accumulator of its level p + q; a level's integer sum stays exact over a k-chunk of the
 //     problem's `chunk` (at most 8 pairs x 127^2 x 128 < 2^24 for 7-bit
 //     digits).  Levels are never mixed in one FP32 accumulator: measured, the
 //     tensor cores' accumulation of mixed-scale products loses far more than
@@ -232,49 +234,49 @@ __device__ __forceinline__ UmTile um_tile(const SplitGemmDesc* G, const int* t0,
 
 #define UM_T0_SMEM 2048   // problems whose first tiles are kept in shared memory
 
-// MMAs of one k-block for S slices: every pair p + q <= S - 1, both k-steps,
-// into the accumulator of its level (levels >= nacc share the last one).
+// MMAs of one k-block for S slices.  For slice p of op(A) the partner slices
+// q = 0..S-1-p of op(B)^T lie back to back in the stage (32 rows each, the
+// same K-major 64-byte-swizzled layout), so together they are one operand of
+// N = 32 (S - p) rows; and the TMEM accumulators of the levels lie back to
+// back, level L at column 32 L.  One MMA of N = 32 (S - p) into column 32 p
+// therefore adds A_p B_q^T to the accumulator of level p + q for every q at
+// once: S MMAs per k-step, each A slice read once (the pairwise form issued
+// S (S + 1) / 2 MMAs of N = 32 and read A_p once per partner).  Every level
+// still sums only its own pairs' integer products.
 // Descriptors differ only in their start-address field (the low 14 bits,
-// address >> 4), so they are formed by adding offsets to a base descriptor.
-// `first` (uniform): the k-block starts a chunk, so each level's first MMA
-// overwrites its accumulator.
+// address >> 4), so they are formed by adding offsets to a base descriptor;
+// the instruction descriptors differ only in their N field (bits 17-22, N >> 3).
+// `first` (uniform): the k-block starts a chunk, so the p = 0 MMA of k-step 0,
+// which covers every level, overwrites the accumulators.
 template <int S>
 __device__ __forceinline__ void um_issue(uint32_t acc, uint64_t da, uint64_t db, uint32_t idesc,
-                                         int nacc, bool first)
+                                         bool first)
 {
+    const uint32_t id0 = idesc & ~(0x3Fu << 17);
 #pragma unroll
     for (int kk = 0; kk < UM_BK / 16; kk++)
 #pragma unroll
         for (int p = 0; p < S; p++)
-#pragma unroll
-            for (int q = 0; p + q < S; q++) {
-                const int L = p + q < nacc ? p + q : nacc - 1;
-                // the level's first pair (p = 0 for levels below nacc) at k-step 0
-                const bool lead = kk == 0 && (p + q < nacc ? p == 0 : (p == 0 && q == nacc - 1));
-                umma_f16kind(acc + L * UM_BN, da + (uint64_t)((p * UM_ASLICE + kk * 32) >> 4),
-                             db + (uint64_t)((q * UM_BSLICE + kk * 32) >> 4), idesc,
-                             (lead && first) ? 0u : 1u);
-            }
+            umma_f16kind(acc + p * UM_BN, da + (uint64_t)((p * UM_ASLICE + kk * 32) >> 4),
+                         db + (uint64_t)((kk * 32) >> 4), id0 | ((uint32_t)(4 * (S - p)) << 17),
+                         (kk == 0 && p == 0 && first) ? 0u : 1u);
 }
 
 __device__ __noinline__ void um_issue_any(int s, uint32_t acc, uint64_t da, uint64_t db,
-                                          uint32_t idesc, int nacc, bool first)
+                                          uint32_t idesc, bool first)
 {
     switch (s) {
-    case 2: um_issue<2>(acc, da, db, idesc, nacc, first); break;
-    case 6: um_issue<6>(acc, da, db, idesc, nacc, first); break;
-    case 8: um_issue<8>(acc, da, db, idesc, nacc, first); break;
+    case 2: um_issue<2>(acc, da, db, idesc, first); break;
+    case 6: um_issue<6>(acc, da, db, idesc, first); break;
+    case 8: um_issue<8>(acc, da, db, idesc, first); break;
     default: {
         // other slice counts (rare): same order, loops not unrolled
+        const uint32_t id0 = idesc & ~(0x3Fu << 17);
         for (int kk = 0; kk < UM_BK / 16; kk++)
             for (int p = 0; p < s; p++)
-                for (int q = 0; p + q < s; q++) {
-                    const int L = min(p + q, nacc - 1);
-                    const bool lead = kk == 0 && (p + q < nacc ? p == 0 : (p == 0 && q == nacc - 1));
-                    umma_f16kind(acc + L * UM_BN, da + (uint64_t)((p * UM_ASLICE + kk * 32) >> 4),
-                                 db + (uint64_t)((q * UM_BSLICE + kk * 32) >> 4), idesc,
-                                 (lead && first) ? 0u : 1u);
-                }
+                umma_f16kind(acc + p * UM_BN, da + (uint64_t)((p * UM_ASLICE + kk * 32) >> 4),
+                             db + (uint64_t)((kk * 32) >> 4), id0 | ((uint32_t)(4 * (s - p)) << 17),
+                             (kk == 0 && p == 0 && first) ? 0u : 1u);
     }
     }
 }
@@ -377,7 +379,7 @@ __global__ void __launch_bounds__(UM_NT, 1)
                         tc_fence_after();
                         const uint32_t a0 = sbase + slot * stage_bytes;
                         const uint32_t b0 = a0 + (uint32_t)smax * UM_ASLICE;
-                        um_issue_any(s, acc, umma_desc(a0), umma_desc(b0), idesc, nacc, kb == kstart);
+                        um_issue_any(s, acc, umma_desc(a0), umma_desc(b0), idesc, kb == kstart);
                         umma_commit(smem_u32(&empty_b[slot]));   // frees the stage when done
                     }
                     if (!ok) break;
@@ -517,7 +519,10 @@ void umma_launch(const SplitGemmDesc* dev, const int* tile0, int ng, int tiles, 
                  int* status, cudaStream_t st)
 {
     if (tiles <= 0) return;
-    nacc = nacc < 1 ? 1 : nacc > UM_NACC_MAX ? UM_NACC_MAX : nacc;
+    // one accumulator per level: the merged MMAs of um_issue write the levels
+    // p..s-1 of slice p side by side
+    (void)nacc;
+    nacc = smax < 1 ? 1 : smax > UM_NACC_MAX ? UM_NACC_MAX : smax;
     int nst = 0;
     const size_t smem = umma_smem_bytes(smax, ng, &nst);
     const int nsm = td_sm_count();

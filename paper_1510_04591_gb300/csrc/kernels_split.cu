@@ -201,13 +201,20 @@ __global__ void __launch_bounds__(256) k_slice(const SliceDesc* D)
     }
 }
 
-// The 7-bit-digit BF16 form with the slice count fixed at compile time.  Two
-// digits t0, t1 < 128 of neighbouring entries are packed as the BF16 pair
-// (128 + t0, 128 + t1) (bit patterns 0x4300 | t) and turned into
-// (t0, t1) 2^(-7p) by one fma.rn.bf16x2 with the exact constants 2^(-7p) and
-// -128 2^(-7p); the entries' signs are then set by an XOR of the sign bits.
-// Every value is exact, and the slices are bit-identical to the general form's
-// except that a negative zero keeps its sign.
+// The 7-bit-digit BF16 form with the slice count fixed at compile time, in
+// balanced digits.  The magnitude m = floor(|x| 2^(7S - e)) is written as
+//   m = t_0 128^(S-1) + sum_{p>=1} t_p 128^(S-1-p),  t_p in [-64, 63] (p >= 1),
+//   t_0 in [0, 128],
+// read off m + B, B = 64 sum_{j<S-1} 128^j: digit p >= 1 is u_p - 64 with u_p
+// the base-128 digit of m + B, and t_0 its top part.  Smaller digits bound a
+// level's integer sum per k by 2 * 128 * 64 + 6 * 64^2 = 40960 (at most 8 pairs,
+// two of them with t_0), so it stays exact in FP32 over 384 k (the unbalanced
+// digits 0..127 allowed 128 k).  Two digits of neighbouring entries are packed
+// as the BF16 pair (128 + u0, 128 + u1) (bit patterns 0x4300 | u) and turned
+// into (u0 - 64, u1 - 64) 2^(-7p) by one fma.rn.bf16x2 with the exact constants
+// 2^(-7p) and -192 2^(-7p); t_0 <= 128 has at most 8 significant bits and is
+// converted exactly through FP32.  The entries' signs are then set by an XOR of
+// the sign bits.  Every value is exact.
 template <int S>
 __global__ void __launch_bounds__(256, 4) k_slice7(const SliceDesc* D)
 {
@@ -219,6 +226,10 @@ __global__ void __launch_bounds__(256, 4) k_slice7(const SliceDesc* D)
     slice_tile_load(d, T, r0, k0);
     __syncthreads();
     constexpr int BS = 7 * S;
+    // 64 in every base-128 digit below the top one
+    unsigned long long B = 0;
+#pragma unroll
+    for (int j = 0; j < S - 1; j++) B |= 64ull << (7 * j);
 #pragma unroll
     for (int i = 0; i < (SL_T * SL_T / 8) / 256; i++) {
         const int u = tid + 256 * i;
@@ -232,15 +243,28 @@ __global__ void __launch_bounds__(256, 4) k_slice7(const SliceDesc* D)
 #pragma unroll
         for (int j = 0; j < 4; j++) {
             const double2 x2 = src[j];
-            m[2 * j] = (unsigned long long)slice_mag(x2.x, e, BS);
-            m[2 * j + 1] = (unsigned long long)slice_mag(x2.y, e, BS);
+            m[2 * j] = (unsigned long long)slice_mag(x2.x, e, BS) + B;
+            m[2 * j + 1] = (unsigned long long)slice_mag(x2.y, e, BS) + B;
             sgn[j] = (((unsigned)__double2hiint(x2.x) >> 31) << 15) | ((unsigned)__double2hiint(x2.y) & 0x80000000u);
         }
+        {
+            // top digit t_0 = (m + B) >> 7 (S - 1) in [0, 128], exact through FP32
+            unsigned w[4];
 #pragma unroll
-        for (int p = 0; p < S; p++) {
+            for (int j = 0; j < 4; j++) {
+                const unsigned t0 = (unsigned)(m[2 * j] >> (7 * (S - 1)));
+                const unsigned t1 = (unsigned)(m[2 * j + 1] >> (7 * (S - 1)));
+                const unsigned h0 = __float_as_uint(__uint_as_float(0x4B000000u | t0) - 8388608.0f) >> 16;
+                const unsigned h1 = __float_as_uint(__uint_as_float(0x4B000000u | t1) - 8388608.0f) >> 16;
+                w[j] = (h0 | (h1 << 16)) ^ sgn[j];
+            }
+            *(uint4*)(d.S + (size_t)row * d.Kp + kk) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+#pragma unroll
+        for (int p = 1; p < S; p++) {
             const int sh = 7 * (S - 1 - p);
-            const unsigned sc = (unsigned)(127 - 7 * p) << 7;             // BF16 2^(-7p)
-            const unsigned nc = ((unsigned)(134 - 7 * p) << 7) | 0x8000u;  // BF16 -128 2^(-7p)
+            const unsigned sc = (unsigned)(127 - 7 * p) << 7;                     // BF16 2^(-7p)
+            const unsigned nc = ((unsigned)(134 - 7 * p) << 7) | 0x8040u;         // BF16 -192 2^(-7p)
             const __nv_bfloat162 sc2 = __halves2bfloat162(__ushort_as_bfloat16((unsigned short)sc),
                                                           __ushort_as_bfloat16((unsigned short)sc));
             const __nv_bfloat162 nc2 = __halves2bfloat162(__ushort_as_bfloat16((unsigned short)nc),
@@ -316,8 +340,9 @@ SplitPrec split_prec(int kind, int bits)
     case SPLIT_FP16X2:   // two 11-bit digits: FP32 accumulation rounds
         p.beta = 11; p.s = 2; p.chunk = UM_BK; p.f16 = 1; p.nacc = 2;
         break;
-    default:             // 7-bit digits, s <= 8: every level exact over 128, 8 x 127^2 x 128 < 2^24
-        p.beta = 7; p.s = (bits + 6) / 7; p.chunk = 128; p.f16 = 0; p.nacc = p.s;
+    default:             // balanced 7-bit digits, s <= 8: every level exact over 384 k,
+                         // (2 x 128 x 64 + 6 x 64^2) x 384 < 2^24
+        p.beta = 7; p.s = (bits + 6) / 7; p.chunk = 384; p.f16 = 0; p.nacc = p.s;
         break;
     }
     return p;

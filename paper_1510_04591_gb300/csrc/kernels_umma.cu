@@ -24,8 +24,8 @@
 //     operand of N = 32 (s - p) rows, into the TMEM accumulators of levels
 //     p..s-1 (32 columns each, side by side), so that every pair p + q <= s - 1
 //     lands in the accumulator of its level p + q; a level's integer sum stays exact over a k-chunk of the
-//     problem's `chunk` (at most 8 pairs x 127^2 x 128 < 2^24 for 7-bit
-//     digits).  Levels are never mixed in one FP32 accumulator: measured, the
+//     problem's `chunk` (balanced 7-bit digits: at most 40960 per k, so 384 k
+//     stay below 2^24).  Levels are never mixed in one FP32 accumulator: measured, the
 //     tensor cores' accumulation of mixed-scale products loses far more than
 //     one rounding per add.  Accumulators are double-buffered (two sets of
 //     levels in 512 TMEM columns), so one chunk is drained while the next is

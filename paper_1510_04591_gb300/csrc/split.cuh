@@ -3,7 +3,8 @@
 // C = alpha op(A) op(B) + beta C for FP64 operands, computed from 16-bit
 // slices: every row i of op(A) is scaled by 2^-e_i (e_i its exponent bound)
 // and cut into s signed beta-bit integer digits t_p, stored as t_p 2^(-beta p)
-// (exact in BF16 for beta <= 8, in FP16 for beta <= 11), so that
+// (exact in BF16 for beta <= 8, in FP16 for beta <= 11; the 7-bit form uses
+// balanced digits, |t_p| <= 64 below the top one), so that
 //   op(A)[i, k] ~= 2^(e_i - beta) sum_p S_p[i, k]
 // (likewise the columns of op(B) with 2^f_j).  A slice-pair product S_p S_q^T
 // is an integer sum scaled by 2^(-beta (p + q)); pairs with p + q <= s - 1

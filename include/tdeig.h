@@ -332,8 +332,8 @@ int tdeig_rank_records(tdeig_handle h, float* buf, int64_t cap);
  *   lambda, gamma, mu : K entries each, same kind of memory, written as by
  *            tdeig_secular
  *   cuda_stream : cudaStream_t to run on (NULL: the legacy default stream)
- * Scratch (the weights in FP64 and FP32, an FP32 pair per pole and a status
- * word: 1.25 MiB in all) is a fixed array in the library's device image, held
+ * Scratch (the weights in FP64 and as FP32 pairs, an FP32 pair per pole and
+ * a status word: 1.5 MiB in all) is a fixed array in the library's device image, held
  * by every GPU that loads the library until the process exits; each call
  * clears the status word before use.  The first call on a device, with that
  * device current, looks up the array's device address (cudaGetSymbolAddress)

@@ -15,7 +15,9 @@
 #define TD_STATUS_TIMEOUT 4
 #define TD_STATUS_BADRANK 8
 // status[TD_STATUS_SECULAR_TERMS .. +1]: 64-bit count of secular terms evaluated
+// in FP64; status[TD_STATUS_SECULAR_DFTERMS .. +1]: in double-float
 #define TD_STATUS_SECULAR_TERMS 2
+#define TD_STATUS_SECULAR_DFTERMS 4
 
 // One merge of the DC tree (Algorithm 1): the node covers global rows
 // [g0, g0 + n); child 1 is [g0, g0 + n1), child 2 the rest.
@@ -75,8 +77,9 @@ struct LevelWS {
     int* ordr;         // final ordering of an unsorted merge: rank of each value
     int* unsorted;     // per merge: 1 when the deflated poles are not ascending
     double* rho;       // per merge, after normalisation of z
-    float *dhK, *dlK;  // FP32 pair of dK (dK ~ dhK + dlK, 48 bits) for the FP32 midpoint test
-    float* wfK;        // wK in FP32
+    float *dhK, *dlK;  // FP32 pair of dK (dK ~ dhK + dlK, 48 bits): FP32 midpoint test and
+                       // the double-float secular iterations
+    float *wfK, *wlK;  // wK as an FP32 pair (wK ~ wfK + wlK)
 };
 
 // Per-kernel timing of a solve made with TDEIG_FLAG_PROFILE: td_prof_begin

@@ -637,7 +637,9 @@ __global__ void __launch_bounds__(PREP_NT) k_prep(const MergeDesc* M, LevelWS ws
                 const float dh = __double2float_rn(di);
                 ws.dhK[g0 + k] = dh;
                 ws.dlK[g0 + k] = __double2float_rn(di - (double)dh);
-                ws.wfK[g0 + k] = __double2float_rn(wi);
+                const float wh = __double2float_rn(wi);
+                ws.wfK[g0 + k] = wh;
+                ws.wlK[g0 + k] = __double2float_rn(wi - (double)wh);
             } else {
                 int l = run_d + ((int)threadIdx.x - pre);
                 ws.deflIdx[g0 + l] = i;
@@ -872,23 +874,136 @@ __device__ __forceinline__ float td_rcp_f32(float x)
     return r;
 }
 
-// dh, dl, wf (optional): d as an FP32 pair and w in FP32; with them the
-// midpoint value that picks the origin and seeds the start is taken in FP32
-// (about 1/50 of the cost of an FP64 evaluation here) and the bracket is the
-// whole interval on the origin's side, (0, d_i+1 - d_i) or (-(d_i+1 - d_i), 0):
-// a wrong sign from FP32 rounding can then only choose the farther pole as
-// origin for a root near the midpoint, where either origin is accurate.
+// ---- double-float (FP32 pair, value = hi + lo, about 48 bits) helpers -----
+// a + b = s + e exactly (Knuth's TwoSum; no products, so nothing is contracted).
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// One term w_j / (delta_j - tau) of a secular sum in double-float, added to
+// (sh, sl), its derivative term w_j / (delta_j - tau)^2 to sd in FP32 (the
+// derivatives only scale the model step).  delta_j = d_j - d_org comes from the
+// FP32 pairs of d (dh_j - dh_org is exact, the rest carries the 48-bit
+// representation error of d, about 2^-48 |d| absolute), except for the near
+// pole, whose exact FP64 difference from tau the caller passes as (xh, xl):
+// every other pole is at least one pole gap from tau, so each term keeps a
+// relative error of about 2^-46 when the poles are not clustered.
+__device__ __forceinline__ void df_term(float dhj, float dlj, float oh, float ol, float th,
+                                        float tl, float wh, float wl, bool nearp, float xh,
+                                        float xl, float& sh, float& sl, float& sd)
+{
+    float Dh, Dl;
+    if (nearp) {
+        Dh = xh;
+        Dl = xl;
+    } else {
+        float s1, e1, s2, e2;
+        df_two_sum(dhj, -oh, s1, e1);
+        df_two_sum(s1, -th, s2, e2);
+        const float lo = __fadd_rn(__fadd_rn(e1, __fsub_rn(dlj, ol)), __fsub_rn(e2, tl));
+        Dh = __fadd_rn(s2, lo);
+        Dl = __fsub_rn(lo, __fsub_rn(Dh, s2));
+    }
+    // 1 / D = q (1 + r + ...), r = 1 - D q from the approximate reciprocal q
+    const float q = td_rcp_f32(Dh);
+    float r = fmaf(-Dh, q, 1.0f);
+    r = fmaf(-Dl, q, r);
+    const float ql = q * r;
+    const float Th = wh * q;
+    const float Tl = fmaf(wh, q, -Th) + fmaf(wh, ql, wl * q);
+    float t, e;
+    df_two_sum(sh, Th, t, e);
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(e, Tl));
+    sd = fmaf(Th, q, sd);
+}
+
+__device__ __forceinline__ void df_warp_sum(float& h, float& l)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+        float t, e;
+        df_two_sum(h, oh, t, e);
+        h = t;
+        l = __fadd_rn(l, __fadd_rn(e, ol));
+    }
+}
+
+// The model step of the iteration (Bunch, Nielsen & Sorensen's two-pole
+// rational model of psi (poles <= i) and phi (poles > i) fitted in value and
+// slope at tau; for the last root one pole): returns tau + step when the model
+// root lies inside the bracket (lo, hi), else the bracket's midpoint.
+__device__ __forceinline__ double secular_step(double f, double dpsi, double dphi, double tau,
+                                               double lo, double hi, double deli, double deli1,
+                                               bool last, double* step_out, bool* model_out)
+{
+    const double a1 = deli - tau;
+    double step = 0.0;
+    bool ok = true;
+    if (!last) {
+        const double a2 = deli1 - tau;
+        const double E = f - dpsi * a1 - dphi * a2;
+        const double beta = E * (a1 + a2) + dpsi * a1 * a1 + dphi * a2 * a2;
+        const double c0 = a1 * a2 * f;
+        double disc = beta * beta - 4.0 * E * c0;
+        if (disc < 0.0) disc = 0.0;
+        const double den = beta + (beta >= 0.0 ? sqrt(disc) : -sqrt(disc));
+        if (den == 0.0) ok = false; else step = 2.0 * c0 / den;
+    } else {
+        const double E = f - dpsi * a1;
+        if (E == 0.0) ok = false; else step = a1 * f / E;
+    }
+    const bool model = ok && tau + step > lo && tau + step < hi;
+    *step_out = step;
+    *model_out = model;
+    return model ? tau + step : 0.5 * (lo + hi);
+}
+
+// Merges with K >= this many poles run the double-float iterations before the
+// FP64 ones: below it the lane-0 scalar work of an iteration (FP64 issue costs a
+// whole warp slot whatever the active lanes) is not small next to an FP64 sum.
+#define TD_SECULAR_DF_MINK 1024
+#define TD_SECULAR_DF_MAXIT 16
+
+// One root of the secular equation by one warp (Theorem 1; Remark 1 for gamma
+// and mu).  dh, dl, wf, wl: d and w as FP32 pairs.
+//   Origin: the midpoint value that picks the origin pole and seeds the start
+//   is taken in FP32 (about 1/50 of the cost of an FP64 evaluation here) and
+//   the bracket is the whole interval on the origin's side, (0, d_i+1 - d_i) or
+//   (-(d_i+1 - d_i), 0): a wrong sign from FP32 rounding can then only choose
+//   the farther pole as origin for a root near the midpoint, where either
+//   origin is accurate.
+//   Start: the root of the two-pole model with the other terms frozen at their
+//   midpoint value.
+//   Double-float iterations (K >= TD_SECULAR_DF_MINK): the same safeguarded
+//   model iteration on psi, phi summed in double-float (an FP32 pair per term,
+//   ~30 FP32 operations, against ~14 FP64 issue slots per term on a part whose
+//   FP64 rate is 1/64 of FP32), until f is within the double-float noise
+//   (2^-40 of its scale) or the step is below 1e-12 of tau: tau is then within
+//   ~1e-11 of the root.
+//   FP64 iterations: the same iteration and stopping test as the oracle,
+//   |f| <= 8 eps (1 + |psi| + |phi| + |tau| f'); a model step below 1e-9 of
+//   tau is taken as converged without evaluating at the new point (the step is
+//   second order in an error of that size).  After the double-float phase one
+//   FP64 evaluation normally ends the root.
+// *iters: FP64 evaluations; *df_iters: double-float evaluations.
 __device__ void secular_root_warp(const double* __restrict__ d, const double* __restrict__ w, int K,
                                   int i, int lane, double* lam, double* gam, double* mu, int* iters,
-                                  const float* __restrict__ dh = nullptr,
-                                  const float* __restrict__ dl = nullptr,
-                                  const float* __restrict__ wf = nullptr)
+                                  int* df_iters, const float* __restrict__ dh,
+                                  const float* __restrict__ dl, const float* __restrict__ wf,
+                                  const float* __restrict__ wl)
 {
+    *df_iters = 0;
     if (K == 1) { *lam = d[0] + w[0]; *gam = w[0]; *mu = 0.0; *iters = 0; return; }
     const bool last = (i == K - 1);
     int org;
     double lo, hi, fmid = 0.0;
-    if (!last && dh) {
+    if (!last) {
         const double gap = d[i + 1] - d[i];
         const float hf = __double2float_rn(0.5 * gap);
         const float ohi = dh[i], olo = dl[i];
@@ -902,14 +1017,6 @@ __device__ void secular_root_warp(const double* __restrict__ d, const double* __
         fmid = 1.0 + (double)f;
         if (fmid >= 0.0) { org = i; lo = 0.0; hi = gap; }
         else { org = i + 1; lo = -gap; hi = 0.0; }
-    } else if (!last) {
-        const double di = d[i];
-        const double half = 0.5 * (d[i + 1] - di);
-        double f = 0.0;
-        for (int j = lane; j < K; j += 32) f += w[j] / ((d[j] - di) - half);
-        fmid = 1.0 + td_warp_sum(f);
-        if (fmid >= 0.0) { org = i; lo = 0.0; hi = half; }
-        else { org = i + 1; lo = -half; hi = 0.0; }
     } else {
         double zz = 0.0;
         for (int j = lane; j < K; j += 32) zz += w[j];
@@ -924,11 +1031,9 @@ __device__ void secular_root_warp(const double* __restrict__ d, const double* __
     // by 32 lanes it cost as much FP64 issue as the sums of a small merge.
     double tau = 0.5 * (lo + hi);
     if (!last && lane == 0) {
-        // Starting point: the two nearest poles kept exactly and the other terms
-        // frozen at their midpoint value, 1 + c + w_i/(deli - t) + w_i1/(deli1 - t)
-        // = 0, a quadratic a t^2 - b t + c0 = 0 solved for its root in the bracket
-        // (the midpoint is the fallback).  Only the start differs from a midpoint
-        // start; the iteration and its stopping test are unchanged.
+        // Start: 1 + c + w_i/(deli - t) + w_i1/(deli1 - t) = 0 with c the other
+        // terms' midpoint value, a quadratic a t^2 - b t + c0 = 0 solved for its
+        // root in the bracket (the midpoint is the fallback).
         const double mid = 0.5 * (d[i + 1] - d[i]);   // midpoint offset from d_i
         const double wi = w[i], wi1 = w[i + 1];
         const double a = fmid - wi / (-mid) - wi1 / (mid);   // 1 + c
@@ -951,6 +1056,67 @@ __device__ void secular_root_warp(const double* __restrict__ d, const double* __
         }
     }
     tau = __shfl_sync(0xffffffffu, tau, 0);
+
+    // ---- double-float iterations ------------------------------------------
+    // Their bracket updates trust the sign of a double-float f, which clustered
+    // poles (terms of poles other than the two nearest, at distances near the
+    // 2^-48 |d| representation error) can get wrong; the FP64 iterations start
+    // again from the whole bracket, so only the start can suffer from that.
+    const double lo0 = lo, hi0 = hi;
+    if (K >= TD_SECULAR_DF_MINK) {
+        const float oh = dh[org], ol = dl[org];
+        // the near pole other than the origin, and its exact offset from it
+        const int jn = last ? -1 : (org == i ? i + 1 : i);
+        const double djn = last ? 0.0 : d[jn] - dorg;
+        int itdf = 0;
+        for (; itdf < TD_SECULAR_DF_MAXIT; itdf++) {
+            const float th = __double2float_rn(tau);
+            const float tl = __double2float_rn(tau - (double)th);
+            const double x = djn - tau;
+            const float xh = __double2float_rn(x);
+            const float xl = __double2float_rn(x - (double)xh);
+            float ph = 0.0f, pl = 0.0f, pd = 0.0f, fh = 0.0f, fl = 0.0f, fd = 0.0f;
+            for (int j = lane; j <= i; j += 32)
+                df_term(dh[j], dl[j], oh, ol, th, tl, wf[j], wl[j], j == jn, xh, xl, ph, pl, pd);
+            for (int j = i + 1 + lane; j < K; j += 32)
+                df_term(dh[j], dl[j], oh, ol, th, tl, wf[j], wl[j], j == jn, xh, xl, fh, fl, fd);
+            df_warp_sum(ph, pl);
+            df_warp_sum(fh, fl);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                pd += __shfl_xor_sync(0xffffffffu, pd, o);
+                fd += __shfl_xor_sync(0xffffffffu, fd, o);
+            }
+            int stop = 0;
+            double nt = tau;
+            if (lane == 0) {
+                const double psi = (double)ph + (double)pl, phi = (double)fh + (double)fl;
+                const double dpsi = pd, dphi = fd;
+                const double f = 1.0 + psi + phi;
+                const double noise = 9.094947017729282e-13 *   // 2^-40
+                                     (1.0 + fabs(psi) + fabs(phi) + fabs(tau) * (dpsi + dphi));
+                if (fabs(f) <= noise) {
+                    stop = 1;
+                } else {
+                    if (f > 0.0) hi = tau; else lo = tau;
+                    double step;
+                    bool model;
+                    nt = secular_step(f, dpsi, dphi, tau, lo, hi, deli, deli1, last, &step, &model);
+                    if (hi - lo <= 4.0 * TD_EPS * fmax(fabs(lo), fabs(hi)) ||
+                        (model && fabs(step) <= 1e-12 * fabs(tau)))
+                        stop = 1;
+                }
+            }
+            stop = __shfl_sync(0xffffffffu, stop, 0);
+            tau = __shfl_sync(0xffffffffu, nt, 0);
+            if (stop) { itdf++; break; }
+        }
+        *df_iters = itdf;
+    }
+    lo = lo0;
+    hi = hi0;
+
+    // ---- FP64 iterations ---------------------------------------------------
     int it;
     for (it = 1; it <= TD_SECULAR_MAXIT; it++) {
         double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
@@ -978,24 +1144,9 @@ __device__ void secular_root_warp(const double* __restrict__ d, const double* __
                 if (hi - lo <= 4.0 * TD_EPS * fmax(fabs(lo), fabs(hi))) {
                     stop = 1;
                 } else {
-                    const double a1 = deli - tau;
-                    double step = 0.0;
-                    bool ok = true;
-                    if (!last) {
-                        const double a2 = deli1 - tau;
-                        const double E = f - dpsi * a1 - dphi * a2;
-                        const double beta = E * (a1 + a2) + dpsi * a1 * a1 + dphi * a2 * a2;
-                        const double c0 = a1 * a2 * f;
-                        double disc = beta * beta - 4.0 * E * c0;
-                        if (disc < 0.0) disc = 0.0;
-                        const double den = beta + (beta >= 0.0 ? sqrt(disc) : -sqrt(disc));
-                        if (den == 0.0) ok = false; else step = 2.0 * c0 / den;
-                    } else {
-                        const double E = f - dpsi * a1;
-                        if (E == 0.0) ok = false; else step = a1 * f / E;
-                    }
-                    const bool model = ok && tau + step > lo && tau + step < hi;
-                    nt = model ? tau + step : 0.5 * (lo + hi);
+                    double step;
+                    bool model;
+                    nt = secular_step(f, dpsi, dphi, tau, lo, hi, deli, deli1, last, &step, &model);
                     if (nt == tau) stop = 1;
                     // a model step below 1e-9 of tau: tau is within about that of the
                     // root and the step (second order in that error) lands within
@@ -1028,19 +1179,22 @@ __global__ void k_secular(const MergeDesc* M, int nmerge, int rows, LevelWS ws, 
     const int K = ws.K[m];
     if (i >= K) return;
     double lam, gam, mu;
-    int it;
-    secular_root_warp(ws.dK + g0, ws.wK + g0, K, i, lane, &lam, &gam, &mu, &it, ws.dhK + g0,
-                      ws.dlK + g0, ws.wfK + g0);
+    int it, itdf;
+    secular_root_warp(ws.dK + g0, ws.wK + g0, K, i, lane, &lam, &gam, &mu, &it, &itdf,
+                      ws.dhK + g0, ws.dlK + g0, ws.wfK + g0, ws.wlK + g0);
     if (lane == 0) {
         ws.lamK[g0 + i] = lam;
         ws.gamK[g0 + i] = gam;
         ws.muK[g0 + i] = mu;
         if (it > TD_SECULAR_MAXIT) atomicOr(status, TD_STATUS_NOTCONV);
-        // work count: K FP64 terms per evaluation of the iteration (the FP32
-        // midpoint value is not counted; the last root's FP64 start is)
+        // work count: K FP64 terms per FP64 evaluation (the last root's FP64
+        // bracket sum included), K double-float terms per double-float one (the
+        // FP32 midpoint value is not counted)
         atomicAdd((unsigned long long*)(status + TD_STATUS_SECULAR_TERMS),
                   (unsigned long long)(min(it, TD_SECULAR_MAXIT) + (i == K - 1 ? 1 : 0)) *
                       (unsigned long long)K);
+        atomicAdd((unsigned long long*)(status + TD_STATUS_SECULAR_DFTERMS),
+                  (unsigned long long)itdf * (unsigned long long)K);
     }
 }
 
@@ -1428,7 +1582,9 @@ __global__ void k_stage_init(LevelWS ws, int K, double rho)
         const float dh = __double2float_rn(di);
         ws.dhK[i] = dh;
         ws.dlK[i] = __double2float_rn(di - (double)dh);
-        ws.wfK[i] = __double2float_rn(w);
+        const float wh = __double2float_rn(w);
+        ws.wfK[i] = wh;
+        ws.wlK[i] = __double2float_rn(w - (double)wh);
     }
 }
 
@@ -1445,8 +1601,8 @@ void td_launch_stage_init(const LevelWS& ws, int K, double rho, cudaStream_t st)
 // allocator (a cudaMalloc there fails or fragments the pool), and code on a
 // latency-bound path where cudaMalloc's implicit device synchronisation is not
 // acceptable.  This variant of the secular stage keeps its scratch -- the
-// weights rho z_j^2 in FP64 and FP32, the FP32 pair of each pole, and a status
-// word -- in the file-scope array below, which every GPU that loads the
+// weights rho z_j^2 in FP64 and as FP32 pairs, the FP32 pair of each pole, and
+// a status word -- in the file-scope array below, which every GPU that loads the
 // library holds until the process exits.  With that scratch it runs the same
 // per-root iteration as k_secular (FP32 midpoint value, two-pole start), so
 // its roots are those of tdeig_secular bit for bit.
@@ -1457,10 +1613,10 @@ void td_launch_stage_init(const LevelWS& ws, int K, double rho, cudaStream_t st)
 // first call before any stream capture.  All calls share the array, so calls
 // whose work overlaps on the GPU (other streams, other host threads) race.
 // ---------------------------------------------------------------------------
-// layout in doubles: w [0, MAX_K); then MAX_K floats each of wf, dh, dl
-// (1.5 MAX_K doubles); then the status word
+// layout in doubles: w [0, MAX_K); then MAX_K floats each of wf, wl, dh, dl
+// (2 MAX_K doubles); then the status word
 #define TD_NOALLOC_F32 TDEIG_NOALLOC_MAX_K
-#define TD_NOALLOC_STATUS (TDEIG_NOALLOC_MAX_K + (3 * TDEIG_NOALLOC_MAX_K) / 2)
+#define TD_NOALLOC_STATUS (3 * TDEIG_NOALLOC_MAX_K)
 #define TD_NOALLOC_SLOTS (TD_NOALLOC_STATUS + 32)
 static __device__ __align__(256) double td_noalloc_scratch[TD_NOALLOC_SLOTS];
 
@@ -1470,7 +1626,7 @@ static double* g_noalloc_ptr[TD_NOALLOC_MAX_DEVICES];
 // The weights and FP32 copies of one problem (as k_stage_init forms them for
 // tdeig_secular), and the status word cleared for this call.
 __global__ void k_noalloc_weights(const double* d, const double* z, double rho, int K, double* w,
-                                  float* wf, float* dh, float* dl, int* status)
+                                  float* wf, float* wl, float* dh, float* dl, int* status)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) *status = 0;   // clear the status word the previous call left in the array
@@ -1480,11 +1636,13 @@ __global__ void k_noalloc_weights(const double* d, const double* z, double rho, 
         const float h = __double2float_rn(di);
         dh[i] = h;
         dl[i] = __double2float_rn(di - (double)h);
-        wf[i] = __double2float_rn(wi);
+        const float wh = __double2float_rn(wi);
+        wf[i] = wh;
+        wl[i] = __double2float_rn(wi - (double)wh);
     }
 }
 
-__global__ void k_secular_noalloc(const double* d, const double* w, const float* wf,
+__global__ void k_secular_noalloc(const double* d, const double* w, const float* wf, const float* wl,
                                   const float* dh, const float* dl, int K, int* status,
                                   double* lam, double* gam, double* mu)
 {
@@ -1492,8 +1650,8 @@ __global__ void k_secular_noalloc(const double* d, const double* w, const float*
     const int lane = threadIdx.x & 31;
     if (i >= K) return;
     double l, g, m;
-    int it;
-    secular_root_warp(d, w, K, i, lane, &l, &g, &m, &it, dh, dl, wf);
+    int it, itdf;
+    secular_root_warp(d, w, K, i, lane, &l, &g, &m, &it, &itdf, dh, dl, wf, wl);
     if (lane == 0) {
         lam[i] = l;
         gam[i] = g;
@@ -1544,13 +1702,15 @@ extern "C" int tdeig_secular_noalloc(int64_t K, const double* d, const double* z
     double* w = scratch;
     float* f32 = (float*)(scratch + TD_NOALLOC_F32);
     float* wf = f32;
+    float* wl = f32 + 3 * TDEIG_NOALLOC_MAX_K;
     float* dh = f32 + TDEIG_NOALLOC_MAX_K;
     float* dl = f32 + 2 * TDEIG_NOALLOC_MAX_K;
     int* status = (int*)(scratch + TD_NOALLOC_STATUS);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int k = (int)K;
-    k_noalloc_weights<<<td_cdiv(k, 256), 256, 0, st>>>(d, z, rho, k, w, wf, dh, dl, status);
-    k_secular_noalloc<<<td_cdiv(k, 8), 256, 0, st>>>(d, w, wf, dh, dl, k, status, lambda, gamma, mu);
+    k_noalloc_weights<<<td_cdiv(k, 256), 256, 0, st>>>(d, z, rho, k, w, wf, wl, dh, dl, status);
+    k_secular_noalloc<<<td_cdiv(k, 8), 256, 0, st>>>(d, w, wf, wl, dh, dl, k, status, lambda, gamma,
+                                                      mu);
     if (cudaGetLastError() != cudaSuccess) return TDEIG_ECUDA;
     int hs = 0;
     if (cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||

@@ -338,7 +338,7 @@ static void build_plan(Plan& P, const Bufs& B, int leaf)
 
 static size_t level_ws_bytes(int64_t R, int64_t Mmax)
 {
-    return (size_t)R * (12 * sizeof(double) + 11 * sizeof(int) + 3 * sizeof(float)) +
+    return (size_t)R * (12 * sizeof(double) + 11 * sizeof(int) + 4 * sizeof(float)) +
            Mmax * (5 * sizeof(int) + 8) + 37 * 256;
 }
 
@@ -375,6 +375,7 @@ static void carve_level_ws(Arena& a, LevelWS& w, int64_t R, int64_t Mmax)
     w.dhK = a.take<float>(R);
     w.dlK = a.take<float>(R);
     w.wfK = a.take<float>(R);
+    w.wlK = a.take<float>(R);
 }
 
 // Statistics of the last solve: per level the merge sizes n, n1, deflated sizes
@@ -788,8 +789,8 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     if (!l_dev) CU(cudaMemcpyAsync(lam_out, B.Lfinal, R * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (Q_out && !q_dev)
         CU(cudaMemcpyAsync(Q_out, B.Qfinal, Qsz * sizeof(double), cudaMemcpyDeviceToHost, st));
-    int hstat[4] = {0, 0, 0, 0};
-    CU(cudaMemcpyAsync(hstat, status, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    int hstat[6] = {0, 0, 0, 0, 0, 0};
+    CU(cudaMemcpyAsync(hstat, status, 6 * sizeof(int), cudaMemcpyDeviceToHost, st));
     std::vector<int> kh(std::max<size_t>(ndesc, 1)), gh(2 * std::max<size_t>(ndesc, 1));
     if (ndesc) {
         CU(cudaMemcpyAsync(kh.data(), kstat, ndesc * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -817,10 +818,12 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     h->mlp_fallbacks = learn.fallbacks;
     h->stats = stats_json(h, P, kh, gh, hss_js, secs, hstat[0]);
     {
-        unsigned long long terms = 0;
+        unsigned long long terms = 0, dfterms = 0;
         memcpy(&terms, hstat + TD_STATUS_SECULAR_TERMS, sizeof(terms));
-        char tb[64];
-        snprintf(tb, sizeof(tb), ",\"secular_terms\":%llu}", terms);
+        memcpy(&dfterms, hstat + TD_STATUS_SECULAR_DFTERMS, sizeof(dfterms));
+        char tb[96];
+        snprintf(tb, sizeof(tb), ",\"secular_terms\":%llu,\"secular_df_terms\":%llu}", terms,
+                 dfterms);
         h->stats.pop_back();
         h->stats += tb;
     }

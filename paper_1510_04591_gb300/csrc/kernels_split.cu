@@ -33,16 +33,31 @@ __device__ __forceinline__ double slice_load(const SliceDesc& d, int r, int k)
 // (subnormal entries are sliced as zero).  Eight independent loads per thread
 // are in flight.
 #define SE_K 1024
+
+// Operand of flattened tile t: the last operand whose first tile is <= t
+// (every launch covers exactly the tiles of its operands, whatever their sizes).
+__device__ __forceinline__ int sl_operand(const SliceDesc* D, int nop, int t, bool exp_pass)
+{
+    int lo = 0, hi = nop - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((exp_pass ? D[mid].t_exp : D[mid].t_sl) <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
 __device__ __forceinline__ int exp_field(double x)
 {
     return (__double2hiint(x) >> 20) & 0x7ff;
 }
 
-__global__ void k_slice_exp(const SliceDesc* D)
+__global__ void k_slice_exp(const SliceDesc* D, int nop)
 {
-    const SliceDesc d = D[blockIdx.x];
-    const int r0 = blockIdx.y * 32;
-    const int kb = blockIdx.z * SE_K;
+    const int t = blockIdx.x;
+    const SliceDesc d = D[sl_operand(D, nop, t, true)];
+    const int ry = (d.rows + 31) / 32;
+    const int local = t - d.t_exp;
+    const int r0 = (local % ry) * 32;
+    const int kb = (local / ry) * SE_K;
     if (r0 >= d.rows || kb >= d.K) return;
     const int ke = min(d.K, kb + SE_K);
     __shared__ int red[8][33];
@@ -144,10 +159,12 @@ __device__ __forceinline__ void slice_tile_load(const SliceDesc& d, double (*T)[
 // stride of 82 doubles keeps the transposing stores at most 2-way).  Digits
 // come from the 64-bit magnitude by 32-bit funnel shifts (beta s <= 56 < 64).
 // General form (any beta, BF16 or FP16 slices).
-__global__ void __launch_bounds__(256) k_slice(const SliceDesc* D)
+__global__ void __launch_bounds__(256) k_slice(const SliceDesc* D, int nop)
 {
-    const SliceDesc d = D[blockIdx.x];   // grid: (operand, 64-wide k tile, 64-row tile)
-    const int k0 = blockIdx.y * SL_T, r0 = blockIdx.z * SL_T;
+    const int t = blockIdx.x;   // flattened (operand, 64-row tile, 64-wide k tile)
+    const SliceDesc d = D[sl_operand(D, nop, t, false)];
+    const int ky = (d.Kp + SL_T - 1) / SL_T;
+    const int k0 = ((t - d.t_sl) % ky) * SL_T, r0 = ((t - d.t_sl) / ky) * SL_T;
     if (k0 >= d.Kp || r0 >= d.rows) return;
     __shared__ __align__(16) double T[SL_T][SL_ROW];
     const int tid = threadIdx.x;
@@ -216,10 +233,12 @@ __global__ void __launch_bounds__(256) k_slice(const SliceDesc* D)
 // converted exactly through FP32.  The entries' signs are then set by an XOR of
 // the sign bits.  Every value is exact.
 template <int S>
-__global__ void __launch_bounds__(256, 4) k_slice7(const SliceDesc* D)
+__global__ void __launch_bounds__(256, 4) k_slice7(const SliceDesc* D, int nop)
 {
-    const SliceDesc d = D[blockIdx.x];
-    const int k0 = blockIdx.y * SL_T, r0 = blockIdx.z * SL_T;
+    const int t = blockIdx.x;   // flattened (operand, 64-row tile, 64-wide k tile)
+    const SliceDesc d = D[sl_operand(D, nop, t, false)];
+    const int ky = (d.Kp + SL_T - 1) / SL_T;
+    const int k0 = ((t - d.t_sl) % ky) * SL_T, r0 = ((t - d.t_sl) / ky) * SL_T;
     if (k0 >= d.Kp || r0 >= d.rows) return;
     __shared__ __align__(16) double T[SL_T][SL_ROW];
     const int tid = threadIdx.x;
@@ -458,6 +477,18 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
         tiles += s.tiles_m * td_cdiv(d.N, UM_BN);
         sg.push_back(s);
     }
+    // flattened tile lists of the two slicing launches
+    long long nexp = 0, nsl = 0;
+    for (auto& o : sl) {
+        o.t_exp = (int)nexp;
+        o.t_sl = (int)nsl;
+        nexp += (long long)td_cdiv(o.rows, 32) * td_cdiv(o.K, SE_K);
+        nsl += (long long)td_cdiv(o.Kp, SL_T) * td_cdiv(o.rows, SL_T);
+    }
+    if (nexp >= (1ll << 31) || nsl >= (1ll << 31)) {
+        *rc = TDEIG_EINVAL;
+        return 0.0;
+    }
     std::vector<int> t0(sg.size());
     for (size_t i = 0; i < sg.size(); i++) t0[i] = sg[i].tile0;
     if (cudaMemcpyAsync(dtm, tm.data(), tm.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st) !=
@@ -475,25 +506,25 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
         *rc = TDEIG_ECUDA;
         return 0.0;
     }
-    const unsigned ry = (unsigned)td_cdiv(maxrows, 32);
+    const int nop = (int)sl.size();
     td_prof_begin(st);
-    k_slice_exp<<<dim3((unsigned)sl.size(), ry, (unsigned)td_cdiv(maxkp, SE_K)), 256, 0, st>>>(dsl);
+    k_slice_exp<<<(unsigned)nexp, 256, 0, st>>>(dsl, nop);
     td_prof_end(st, "k_slice_exp");
-    const dim3 gs((unsigned)sl.size(), (unsigned)td_cdiv(maxkp, SL_T), (unsigned)td_cdiv(maxrows, SL_T));
+    const unsigned gs = (unsigned)nsl;
     td_prof_begin(st);
     if (pr.beta == 7 && !pr.f16) {
         switch (pr.s) {
-        case 1: k_slice7<1><<<gs, 256, 0, st>>>(dsl); break;
-        case 2: k_slice7<2><<<gs, 256, 0, st>>>(dsl); break;
-        case 3: k_slice7<3><<<gs, 256, 0, st>>>(dsl); break;
-        case 4: k_slice7<4><<<gs, 256, 0, st>>>(dsl); break;
-        case 5: k_slice7<5><<<gs, 256, 0, st>>>(dsl); break;
-        case 6: k_slice7<6><<<gs, 256, 0, st>>>(dsl); break;
-        case 7: k_slice7<7><<<gs, 256, 0, st>>>(dsl); break;
-        default: k_slice7<8><<<gs, 256, 0, st>>>(dsl); break;
+        case 1: k_slice7<1><<<gs, 256, 0, st>>>(dsl, nop); break;
+        case 2: k_slice7<2><<<gs, 256, 0, st>>>(dsl, nop); break;
+        case 3: k_slice7<3><<<gs, 256, 0, st>>>(dsl, nop); break;
+        case 4: k_slice7<4><<<gs, 256, 0, st>>>(dsl, nop); break;
+        case 5: k_slice7<5><<<gs, 256, 0, st>>>(dsl, nop); break;
+        case 6: k_slice7<6><<<gs, 256, 0, st>>>(dsl, nop); break;
+        case 7: k_slice7<7><<<gs, 256, 0, st>>>(dsl, nop); break;
+        default: k_slice7<8><<<gs, 256, 0, st>>>(dsl, nop); break;
         }
     } else {
-        k_slice<<<gs, 256, 0, st>>>(dsl);
+        k_slice<<<gs, 256, 0, st>>>(dsl, nop);
     }
     td_prof_end(st, "k_slice");
     umma_launch(dsg, dt0, (int)sg.size(), tiles, pr.s, pr.nacc, status, st);

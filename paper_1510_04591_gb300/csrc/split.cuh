@@ -39,6 +39,7 @@ struct SliceDesc {
     int f16;            // slices are FP16 (else BF16)
     __nv_bfloat16* S;   // slice p, row r at S + (p * rows + r) * Kp (16-bit values)
     int* e;             // exponent bound per row: max |row| < 2^e
+    int t_exp, t_sl;    // first tile of this operand in the exponent and slicing launches
 };
 
 // One slice-pair product C = alpha 2^(ea+eb) sum_{p+q<=s-1} ... + betac C.

@@ -246,6 +246,27 @@ int tdeig_philox4x32_10(tdeig_handle h, int64_t n, const uint32_t* ctr, const ui
 int tdeig_gaussian(tdeig_handle h, int64_t nrow, int64_t ncol, uint64_t seed, uint32_t stream_id,
                    double* out);
 
+/* The HSS eigenvector update of one merge on given generators, as a kernel
+ * benchmark and stage check (Algorithm 1's "else" branch): the Cauchy-like
+ * matrix Qhat[k, j] = uhat_k v_j / (d_k - lambda_j) (eq. Ev-Q, v its column
+ * normalisation, lambda_j = d_j + gamma_j, every difference by Remark 1) is
+ * approximated by an HSS matrix H -- ADC1: structured rank-revealing Schur
+ * complements; ADC2: the rank estimate of eq. (bounds) and Algorithm 2 -- and
+ * out = X H is formed by Algorithm 3.
+ *   K (>= 2): size; d, gamma, mu, uhat: K entries (as tdeig_secular and
+ *   tdeig_lowner_cauchy return them)
+ *   P: rows of X; X, out: P x K column-major, leading dimension P
+ *   mode: TDEIG_MODE_ADC1 or _ADC2 | a precision flag
+ * The handle's HSS options apply (hss_leaf, tol, oversample, rank_eps,
+ * rank_cap, boundary_shift, seed; the Philox stream id is 0); the HSS branch
+ * is taken whatever hss_threshold says.  tdeig_last_stats then gives the
+ * device milliseconds of each sub-stage ("cauchy": v and, for ADC2, the
+ * sampled matrix; "hss_sample", "hss_build", "hss_mult") and the HSS record
+ * (rank estimate, sample size, node ranks, moved leaf boundaries, flops). */
+int tdeig_hss_apply(tdeig_handle h, int64_t K, const double* d, const double* gamma,
+                    const double* mu, const double* uhat, int64_t P, const double* X, double* out,
+                    int mode);
+
 /* Architecture of the library's device code as the current device loads it:
  * *arch = major * 10 + minor (103 for sm_103a).  TDEIG_ECUDA without a GPU. */
 int tdeig_binary_arch(int* arch);

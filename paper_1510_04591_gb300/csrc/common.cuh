@@ -138,6 +138,9 @@ void td_launch_secular(const MergeDesc* M, int nmerge, int rows, const LevelWS& 
                        cudaStream_t st);
 void td_launch_lowner_cauchy(const MergeDesc* M, int nmerge, int rows, int kmax, const LevelWS& ws,
                              int write_qhat, cudaStream_t st);
+// k_cauchy alone (v and, with write_qhat, the Cauchy-like matrix) from uhat.
+void td_launch_cauchy(const MergeDesc* M, int nmerge, int rows, int kmax, const LevelWS& ws,
+                      int write_qhat, cudaStream_t st);
 // Tile-shape variants of the FP64 update product (picked per level by the autotuner).
 #define TD_GEMM_VARIANTS 4
 void td_gemm_tiles(int variant, int n, int* bm, int* bn);

@@ -1316,11 +1316,9 @@ __global__ void __launch_bounds__(CAUCHY_NT) k_cauchy(const MergeDesc* M, int nm
 }
 
 #define CAUCHY_SMEM_MAX 200000
-void td_launch_lowner_cauchy(const MergeDesc* M, int nmerge, int rows, int kmax, const LevelWS& ws,
-                             int write_qhat, cudaStream_t st)
+static void launch_cauchy(const MergeDesc* M, int nmerge, int rows, int kmax, const LevelWS& ws,
+                          int write_qhat, cudaStream_t st)
 {
-    if (rows <= 0) return;
-    td_prof_begin(st); k_lowner<<<td_cdiv(rows, 8), 256, 0, st>>>(M, nmerge, rows, ws); td_prof_end(st, "k_lowner");
     size_t sm = (size_t)kmax * sizeof(double);
     if (sm <= CAUCHY_SMEM_MAX) {
         td_smem_attr((const void*)k_cauchy<true>, CAUCHY_SMEM_MAX);
@@ -1328,6 +1326,21 @@ void td_launch_lowner_cauchy(const MergeDesc* M, int nmerge, int rows, int kmax,
     } else {
         td_prof_begin(st); k_cauchy<false><<<rows, CAUCHY_NT, 0, st>>>(M, nmerge, rows, ws, write_qhat); td_prof_end(st, "k_cauchy");
     }
+}
+
+void td_launch_cauchy(const MergeDesc* M, int nmerge, int rows, int kmax, const LevelWS& ws,
+                      int write_qhat, cudaStream_t st)
+{
+    if (rows <= 0) return;
+    launch_cauchy(M, nmerge, rows, kmax, ws, write_qhat, st);
+}
+
+void td_launch_lowner_cauchy(const MergeDesc* M, int nmerge, int rows, int kmax, const LevelWS& ws,
+                             int write_qhat, cudaStream_t st)
+{
+    if (rows <= 0) return;
+    td_prof_begin(st); k_lowner<<<td_cdiv(rows, 8), 256, 0, st>>>(M, nmerge, rows, ws); td_prof_end(st, "k_lowner");
+    launch_cauchy(M, nmerge, rows, kmax, ws, write_qhat, st);
 }
 
 // ---------------------------------------------------------------------------

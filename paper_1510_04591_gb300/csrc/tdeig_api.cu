@@ -1553,3 +1553,114 @@ extern "C" int tdeig_split_gemm(tdeig_handle h, int64_t M, int64_t N, int64_t K,
     CU(cudaStreamSynchronize(st));
     return (hs & TD_STATUS_TIMEOUT) ? TDEIG_ETIMEOUT : TDEIG_OK;
 }
+
+// ---------------------------------------------------------------------------
+// HSS construction and multiplication on given generators (Algorithms 2, 3)
+// ---------------------------------------------------------------------------
+extern "C" int tdeig_hss_apply(tdeig_handle h, int64_t K, const double* d, const double* gamma,
+                               const double* mu, const double* uhat, int64_t P, const double* X,
+                               double* out, int mode)
+{
+    if (!h || K < 2 || K > (1 << 20) || P < 1 || P > (1 << 20) || !d || !gamma || !mu || !uhat ||
+        !X || !out)
+        return TDEIG_EINVAL;
+    const int variant = mode & TDEIG_MODE_MASK;
+    const int prec = mode & TDEIG_PREC_MASK;
+    if ((variant != TDEIG_MODE_ADC1 && variant != TDEIG_MODE_ADC2) ||
+        (mode & ~(TDEIG_MODE_MASK | TDEIG_PREC_MASK)) ||
+        (prec != TDEIG_PREC_FP64 && prec != TDEIG_PREC_SPLIT && prec != TDEIG_PREC_BF16X2 &&
+         prec != TDEIG_PREC_FP16X2))
+        return TDEIG_EINVAL;
+    TdCtxScope ctx_scope_(&h->ctx);
+    CU(cudaSetDevice(h->device));
+    cudaStream_t st = h->stream;
+    const int64_t R = std::max(K, P);
+    const bool xdev = is_device_ptr(X), odev = is_device_ptr(out);
+    size_t bytes = level_ws_bytes(R, 1) + (size_t)K * K * sizeof(double) +
+                   ((xdev ? 0 : 1) + (odev ? 0 : 1)) * (size_t)P * K * sizeof(double) +
+                   (size_t)R * 2 * sizeof(int) + 64 * 1024;
+    int rc = ensure_ws(h, bytes);
+    if (rc) return rc;
+    Arena ar{h->ws, 0, h->ws_bytes};
+    LevelWS lws;
+    carve_level_ws(ar, lws, R, 1);
+    double* qh = ar.take<double>((size_t)K * K);
+    double* Xd = xdev ? (double*)X : ar.take<double>((size_t)P * K);
+    double* Od = odev ? out : ar.take<double>((size_t)P * K);
+    int* status = ar.take<int>(64);
+    MergeDesc* dmd = ar.take<MergeDesc>(2);
+    if (ar.off > ar.cap) return TDEIG_ENOMEM;
+    if ((rc = copy_in(lws.dK, d, K, st)) || (rc = copy_in(lws.gamK, gamma, K, st)) ||
+        (rc = copy_in(lws.muK, mu, K, st)) || (rc = copy_in(lws.uhat, uhat, K, st)))
+        return rc;
+    if (!xdev) CU(cudaMemcpyAsync(Xd, X, (size_t)P * K * sizeof(double), cudaMemcpyHostToDevice, st));
+    std::vector<int> iota(R);
+    for (int64_t i = 0; i < R; i++) iota[i] = (int)i;
+    CU(cudaMemcpyAsync(lws.survIdx, iota.data(), R * sizeof(int), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(lws.posNew, iota.data(), R * sizeof(int), cudaMemcpyHostToDevice, st));
+    // merge 0 for k_cauchy (K rows: v and the Cauchy-like matrix), and the HSS
+    // update's merge: W = X (P x K), output columns in place
+    MergeDesc mc;
+    memset(&mc, 0, sizeof(mc));
+    mc.g0 = 0; mc.n = (int)K; mc.n1 = 0; mc.qhat = qh; mc.tiles_m = 1;
+    MergeDesc mh = mc;
+    mh.n = (int)P; mh.W = Xd; mh.qout = Od; mh.node_id = 0;
+    CU(cudaMemcpyAsync(dmd, &mc, sizeof(mc), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(dmd + 1, &mh, sizeof(mh), cudaMemcpyHostToDevice, st));
+    const int Ki = (int)K;
+    CU(cudaMemcpyAsync(lws.K, &Ki, sizeof(int), cudaMemcpyHostToDevice, st));
+    CU(cudaMemsetAsync(status, 0, 64 * sizeof(int), st));
+    CU(cudaStreamSynchronize(st));   // the host values above are on this stack frame
+
+    h->ev_names.clear();
+    h->ev_level.clear();
+    auto mark = [&](const char* name) -> int {
+        size_t i = h->ev_names.size();
+        if (i >= h->events.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return TDEIG_ECUDA;
+            h->events.push_back(e);
+        }
+        h->ev_names.push_back(name);
+        h->ev_level.push_back(-1);
+        return cudaEventRecord(h->events[i], st) == cudaSuccess ? TDEIG_OK : TDEIG_ECUDA;
+    };
+    auto t0 = std::chrono::steady_clock::now();
+    if ((rc = mark("cauchy"))) return rc;
+    td_launch_cauchy(dmd, 1, Ki, Ki, lws, variant == TDEIG_MODE_ADC2 ? 1 : 0, st);
+    CU(cudaGetLastError());
+    tdeig_options o = h->opt;
+    o.hss_threshold = 0;   // always the HSS branch
+    std::string hss_js;
+    std::vector<MergeDesc> ms{mh};
+    std::vector<int> Kv{Ki};
+    rc = hss_update_level(o, variant, prec, ms, dmd + 1, Kv, lws, h->hss, status, st, hss_js, mark,
+                          prec != TDEIG_PREC_FP64 ? &h->split : nullptr, nullptr);
+    if (rc) return rc;
+    if ((rc = mark("end"))) return rc;
+    if (!odev) CU(cudaMemcpyAsync(out, Od, (size_t)P * K * sizeof(double), cudaMemcpyDeviceToHost, st));
+    int hs = 0;
+    CU(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    CU(cudaGetLastError());
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    // statistics: sub-stage device times, the HSS merge record (ranks, flops)
+    std::string js = "{\"stage_ms\":{";
+    char buf[160];
+    for (size_t e = 0; e + 1 < h->ev_names.size(); e++) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->events[e], h->events[e + 1]);
+        snprintf(buf, sizeof(buf), "%s\"%s\":%.6f", e ? "," : "", h->ev_names[e], ms);
+        js += buf;
+    }
+    float all = 0.f;
+    if (h->ev_names.size() >= 2)
+        cudaEventElapsedTime(&all, h->events[0], h->events[h->ev_names.size() - 1]);
+    snprintf(buf, sizeof(buf), "},\"device_ms\":%.6f,\"seconds\":%.6f,\"status\":%d", all, secs, hs);
+    js += buf;
+    if (!hss_js.empty()) js += ",\"hss\":[" + hss_js + "]";
+    js += "}";
+    h->stats = js;
+    if (hs & TD_STATUS_TIMEOUT) return TDEIG_ETIMEOUT;
+    return TDEIG_OK;
+}

@@ -105,6 +105,8 @@ def lib():
         L.tdeig_philox4x32_10.restype = ctypes.c_int
         L.tdeig_gaussian.argtypes = [_vp, _i64, _i64, ctypes.c_uint64, ctypes.c_uint32, _vp]
         L.tdeig_gaussian.restype = ctypes.c_int
+        L.tdeig_hss_apply.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, ctypes.c_int]
+        L.tdeig_hss_apply.restype = ctypes.c_int
         L.tdeig_binary_arch.argtypes = [_vp]
         L.tdeig_binary_arch.restype = ctypes.c_int
         _lib = L
@@ -418,6 +420,24 @@ class Solver:
         st = lib().tdeig_gaussian(self.h, nrow, ncol, int(seed), int(stream_id), out.ctypes.data)
         if st != OK:
             raise TdeigError(st, "tdeig_gaussian")
+        return out
+
+    def hss_apply(self, d, gamma, mu, uhat, X, mode="adc2", prec="fp64"):
+        """out = X H with H the HSS approximation (ADC1 / ADC2) of the Cauchy-like
+        matrix of the generators; X: P x K (torch CUDA or numpy, column-major)."""
+        d, gamma, mu, uhat = (_as_f64(x) for x in (d, gamma, mu, uhat))
+        K = d.shape[0]
+        if _is_torch(X):
+            import torch
+            Xc = X.t().contiguous().t() if not X.t().is_contiguous() else X
+            out = torch.empty((X.shape[1], X.shape[0]), dtype=torch.float64, device=X.device).t()
+        else:
+            Xc = np.asfortranarray(np.asarray(X, dtype=np.float64))
+            out = np.empty(Xc.shape, order="F")
+        st = lib().tdeig_hss_apply(self.h, K, _ptr(d), _ptr(gamma), _ptr(mu), _ptr(uhat),
+                                   Xc.shape[0], _ptr(Xc), _ptr(out), mode_code(mode, prec))
+        if st != OK:
+            raise TdeigError(st, "tdeig_hss_apply")
         return out
 
     def rank_records(self):

@@ -30,9 +30,12 @@
 //     one rounding per add.  Accumulators are double-buffered (two sets of
 //     levels in 512 TMEM columns), so one chunk is drained while the next is
 //     computed;
-//   * warps 2-9 (drain / epilogue, TMEM lane = tile row, two warps per lane
-//     quarter, 16 columns each: two warps per SM sub-partition hide each
-//     other's latencies in this instruction-bound part): after every chunk
+//   * warps 2-17 (drain / epilogue, TMEM lane = tile row, four warps per lane
+//     quarter, 8 columns each: measured with per-role wait counters, the
+//     epilogue bounded the kernel with two warps per SM sub-partition while
+//     its pipes were far from busy, so four hide each other's latencies; two
+//     levels are loaded from TMEM per wait, and with balanced 7-bit digits two
+//     levels combine exactly in one int32 before the 64-bit sums): after every chunk
 //     they read the levels with tcgen05.ld and sum them per output entry
 //     exactly as integers (the first UM_HI levels in one int64, the finer ones
 //     in a second, each level shifted by beta relative to the next; a rounded
@@ -49,9 +52,9 @@
 #include "split.cuh"
 
 
-#define UM_NT 320                        // warp 0 loads, warp 1 issues MMAs, warps 2-9 drain and write
-#define UM_EPI 256                       // drain / epilogue threads (TMEM lane = tile row, two column halves)
-#define UM_EH 16                         // columns of the tile per epilogue warp
+#define UM_NT 576                        // warp 0 loads, warp 1 issues MMAs, warps 2-17 drain and write
+#define UM_EPI 512                       // drain / epilogue threads (TMEM lane = tile row, four column quarters)
+#define UM_EH 8                          // columns of the tile per epilogue warp
 #define UM_HI 4                          // levels in the first int64 sum (the rest in the second)
 #define UM_MAXST 8                       // shared-memory ring stages
 #define UM_TCOLS 512                     // two accumulator buffers of up to 8 levels x 32 columns
@@ -155,27 +158,32 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity)
     return true;
 }
 
-// 16 consecutive FP32 columns of this warp's 32 TMEM lanes (one row per thread).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
+// 8 consecutive FP32 columns of this warp's 32 TMEM lanes (one row per thread),
+// issued without waiting: the registers are valid after tmem_wait8.
+__device__ __forceinline__ void tmem_ld8_issue(uint32_t taddr, uint32_t* r)
 {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-        "%14,%15}, [%16];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+
+// Waits for this thread's TMEM loads; the registers are in-out operands so that
+// no use of them is scheduled before the wait.
+__device__ __forceinline__ void tmem_wait8(uint32_t* r)
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                   "+r"(r[6]), "+r"(r[7])
+                 :
+                 : "memory");
 }
 
 // x 2^k as an FP64 value (x an int64): one rounding conversion, then the scale
 // added to the exponent field with an integer add (normal results: |k| stays
 // far inside the exponent range here).  Measured: building the value with
-// 64-bit integer normalisation and rounding cost about 600 cycles per output
-// column of a warp, the conversion about 16.
+// integer normalisation and rounding added ~20 ALU instructions per value and
+// slowed the kernel (the ALU pipe, not the FP64 one, bounds this epilogue).
 __device__ __forceinline__ double i2d_scaled(long long x, int k)
 {
     if (x == 0) return 0.0;
@@ -389,9 +397,9 @@ __global__ void __launch_bounds__(UM_NT, 1)
             }
         }
     } else {
-        // ---------------- drain / epilogue (warps 2..5) ----------------
-        // warp w reaches TMEM lanes 32 (w % 4) ... + 31: warps 2..9 cover each
-        // lane quarter twice, the two warps of a quarter taking 16 columns each
+        // ---------------- drain / epilogue (warps 2..17) ----------------
+        // warp w reaches TMEM lanes 32 (w % 4) ... + 31: warps 2..17 cover each
+        // lane quarter four times, the four warps of a quarter taking 8 columns each
         const int quarter = warp & 3;
         const int cb = UM_EH * ((warp - 2) >> 2);
         const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
@@ -419,24 +427,60 @@ __global__ void __launch_bounds__(UM_NT, 1)
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t tb = trow + ab * bufcols;
+                // two levels per TMEM round trip: both loads issued, one wait
 #pragma unroll 1
-                for (int L = 0; L < UM_NACC_MAX; L++) {
-                    if (L >= s || L >= nacc) break;   // level L exists only for s > L
-                    float v[UM_EH];
-                    tmem_ld16(tb + L * UM_BN + cb, v);
-                    // acc_L = I_L 2^(-beta L) with I_L an integer, |I_L| < 2^24: a 32-bit
-                    // conversion (a 64-bit one issues on the FP64 pipe here)
-                    const float up = __int_as_float((127 + beta * L) << 23);
-                    if (L < hl) {
-                        const int sh = beta * (hl - 1 - L);
+                for (int L0 = 0; L0 < UM_NACC_MAX; L0 += 2) {
+                    if (L0 >= s || L0 >= nacc) break;   // level L exists only for s > L
+                    const bool two = L0 + 1 < s && L0 + 1 < nacc;
+                    uint32_t r[2][UM_EH];
+                    tmem_ld8_issue(tb + L0 * UM_BN + cb, r[0]);
+                    if (two) tmem_ld8_issue(tb + (L0 + 1) * UM_BN + cb, r[1]);
+                    tmem_wait8(r[0]);
+                    if (two) tmem_wait8(r[1]);
+                    if (two && beta == 7) {
+                        // balanced 7-bit digits over chunks of at most 384 k: |I_L| <=
+                        // 40960 * 384 < 2^24, so I_L0 * 128 + I_L0+1 < 2^31 is exact in one
+                        // int32 (one IMAD) and takes one 64-bit shift and add for two levels
+                        // (L0 even, so both levels lie in the same half, ihi or ilo)
+                        const float up0 = __int_as_float((127 + 7 * L0) << 23);
+                        const float up1 = __int_as_float((127 + 7 * (L0 + 1)) << 23);
+                        if (L0 + 1 < hl) {
+                            const int sh = 7 * (hl - 2 - L0);
 #pragma unroll
-                        for (int c = 0; c < UM_EH; c++)
-                            ihi[c] += (long long)__float2int_rn(v[c] * up) << sh;
-                    } else {
-                        const int sh = beta * (s - 1 - L);
+                            for (int c = 0; c < UM_EH; c++) {
+                                const int pr = __float2int_rn(__uint_as_float(r[0][c]) * up0) * 128 +
+                                               __float2int_rn(__uint_as_float(r[1][c]) * up1);
+                                ihi[c] += (long long)pr << sh;
+                            }
+                        } else {
+                            const int sh = 7 * (s - 2 - L0);
 #pragma unroll
-                        for (int c = 0; c < UM_EH; c++)
-                            ilo[c] += (long long)__float2int_rn(v[c] * up) << sh;
+                            for (int c = 0; c < UM_EH; c++) {
+                                const int pr = __float2int_rn(__uint_as_float(r[0][c]) * up0) * 128 +
+                                               __float2int_rn(__uint_as_float(r[1][c]) * up1);
+                                ilo[c] += (long long)pr << sh;
+                            }
+                        }
+                        continue;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 2; q++) {
+                        const int L = L0 + q;
+                        if (q == 1 && !two) break;
+                        // acc_L = I_L 2^(-beta L) with I_L an integer, |I_L| < 2^24: a 32-bit
+                        // conversion (a 64-bit one issues on the FP64 pipe here)
+                        const float up = __int_as_float((127 + beta * L) << 23);
+                        if (L < hl) {
+                            const int sh = beta * (hl - 1 - L);
+#pragma unroll
+                            for (int c = 0; c < UM_EH; c++)
+                                ihi[c] += (long long)__float2int_rn(__uint_as_float(r[q][c]) * up) << sh;
+                        } else {
+                            const int sh = beta * (s - 1 - L);
+#pragma unroll
+                            for (int c = 0; c < UM_EH; c++)
+                                ilo[c] += (long long)__float2int_rn(__uint_as_float(r[q][c]) * up) << sh;
+                        }
                     }
                 }
                 tc_fence_before();

@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-profile", action="store_true")
     p.add_argument("--stats-out", default=None)
+    p.add_argument("--graph", action="store_true",
+                   help="--workload batched: replay the solve as a captured CUDA graph")
     return p.parse_args()
 
 
@@ -459,6 +461,8 @@ def run_batched(args, torch, dist, world, rank, local, dev, stream, solver, flus
             raise tdeig.TdeigError(st, "tdeig_solve_batched")
         return json.loads(solver.stats())
 
+    if args.graph:
+        mode |= tdeig.FLAG_GRAPH
     for _ in range(args.warmup):
         one(mode)
     torch.cuda.synchronize()
@@ -479,7 +483,7 @@ def run_batched(args, torch, dist, world, rank, local, dev, stream, solver, flus
     v = float(np.mean(ms)) / 1e3
     stats = None
     if prof:
-        stats = one(mode | prof)   # one extra, untimed solve with per-kernel events
+        stats = one((mode & ~tdeig.FLAG_GRAPH) | prof)   # one extra, untimed profiled solve
         if args.stats_out and rank == 0:
             with open(args.stats_out, "w") as f:
                 json.dump(stats, f)
@@ -488,7 +492,8 @@ def run_batched(args, torch, dist, world, rank, local, dev, stream, solver, flus
            "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": workload_name(args), "members": len(sizes),
-                      "rows": int(sum(sizes)), "q_entries": int(sum(n * n for n in sizes))},
+                      "rows": int(sum(sizes)), "q_entries": int(sum(n * n for n in sizes)),
+                      "graph": bool(args.graph)},
            "clocks": ck, "matrices_per_s": len(sizes) / v}
     if stats is not None:
         ch = stats.get("chunks", [stats])

@@ -57,10 +57,12 @@ enum {
      * FP64.  A precision-study variant. */
     TDEIG_PREC_FP16X2 = 3 << 8,
     TDEIG_PREC_MASK = 0xf << 8,
-    /* DENSE | FP64 with device buffers only: capture the whole launch sequence
-     * (every level of every matrix) in a CUDA graph on the first call and
-     * replay it on later calls with the same sizes and buffers.  Ignored
-     * otherwise (those modes read deflated sizes back to the host). */
+    /* DENSE (any precision) with device buffers only: capture the whole launch
+     * sequence (every level of every matrix) in a CUDA graph on the first call
+     * and replay it on later calls with the same sizes and buffers.  With split
+     * products the launches are sized by upper bounds and read each merge's
+     * deflated sizes on the device.  Ignored otherwise (the HSS modes read
+     * ranks back to the host). */
     TDEIG_FLAG_GRAPH = 1 << 12,
     /* Time every kernel launch of the solve with CUDA events on the solve's
      * stream; tdeig_last_stats then lists per kernel its launches and device

@@ -41,6 +41,12 @@ struct GemmDesc {
     const double* A2;
     const double* B2;
     int Kd2, lda2, ldb2, transA2, transB2;
+    // optional (split products only): sizes known only on the device, so that the
+    // launch sequence needs no host read-back (CUDA-graph capture).  N and Kd
+    // above are then upper bounds; the actual N = Kd = *dynK, and with the block
+    // structure ktop_end = dynG[0] + dynG[1], kbot_beg = dynG[0].
+    const int* dynK;
+    const int* dynG;
 };
 
 // out[a + b ld] = uhat[row] v[col] / (d[row] - lambda[col]) (Remark 1), for

@@ -1307,7 +1307,9 @@ __global__ void __launch_bounds__(CAUCHY_NT) k_cauchy(const MergeDesc* M, int nm
     __syncthreads();
     const double vj = s_vj;
     if (!write_qhat) return;
-    double* out = md.qhat + (int64_t)j * K;
+    // leading dimension: n in the product order used by the dense update (its
+    // launches can then be sized without knowing K), K in secular order
+    double* out = md.qhat + (int64_t)j * (write_qhat == 2 ? md.n : K);
     for (int p = threadIdx.x; p < K; p += blockDim.x) {
         const int k = perm ? perm[p] : p;
         double t = SMEM ? col[p] : uh[k] * td_recip(td_dminus(d, gam, mu, k, j));
@@ -1521,7 +1523,7 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const MergeDesc* M, const int*
             const int idx = threadIdx.x + 256 * q;
             const int kb = idx & 15, c = idx >> 4;
             const int kg = k0 + kb, cg = col0 + c;
-            Bs[kb][c] = (kg < kend && cg < K) ? B[(int64_t)cg * K + kg] : 0.0;
+            Bs[kb][c] = (kg < kend && cg < K) ? B[(int64_t)cg * n + kg] : 0.0;   // Qhat: ld n
         }
         __syncthreads();
 #pragma unroll

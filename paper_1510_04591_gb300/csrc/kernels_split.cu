@@ -50,35 +50,48 @@ __device__ __forceinline__ int exp_field(double x)
     return (__double2hiint(x) >> 20) & 0x7ff;
 }
 
+// Rows of an exponent-pass tile: 128 when rows are contiguous in memory (four
+// warps read 1 KiB runs of a column: measured, 256-byte runs of columns 64 KiB
+// apart held the pass at a third of the DRAM bandwidth), else 32.
+__host__ __device__ __forceinline__ int se_rows(long long sr) { return sr == 1 ? 128 : 32; }
+// k range of an exponent-pass tile: 256 with 128-row tiles (so the CTA count,
+// and the loads in flight, match the 32-row form), SE_K otherwise
+__host__ __device__ __forceinline__ int se_kchunk(long long sr) { return sr == 1 ? 256 : SE_K; }
+
 __global__ void k_slice_exp(const SliceDesc* D, int nop)
 {
     const int t = blockIdx.x;
     const SliceDesc d = D[sl_operand(D, nop, t, true)];
-    const int ry = (d.rows + 31) / 32;
+    const int RT = se_rows(d.sr);
+    const int ry = (d.rows + RT - 1) / RT;
     const int local = t - d.t_exp;
-    const int r0 = (local % ry) * 32;
-    const int kb = (local / ry) * SE_K;
-    if (r0 >= d.rows || kb >= d.K) return;
-    const int ke = min(d.K, kb + SE_K);
+    const int r0 = (local % ry) * RT;
+    const int kb = (local / ry) * se_kchunk(d.sr);
+    const int nrows = (d.dynK && d.dyn_rows) ? *d.dynK : d.rows;   // actual sizes
+    const int Kact = d.dynK ? *d.dynK : d.K;
+    if (r0 >= nrows || kb >= Kact) return;
+    const int ke = min(Kact, kb + se_kchunk(d.sr));
     __shared__ int red[8][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     if (d.sr == 1) {
-        // rows contiguous: lane = row, warps stride over k
-        const int r = r0 + tx;
+        // rows contiguous: lane = row; warp ty takes rows 32 (ty & 3) + lane and
+        // every other column (phase ty >> 2), sixteen independent loads in flight
+        // (the pass is bound by load latency)
+        const int r = r0 + 32 * (ty & 3) + tx;
+        const int kp = ty >> 2;
         int mx = 0;
-        if (r < d.rows)
-            for (int k = kb + ty; k < ke; k += 64) {
-                double v[8];
+        if (r < nrows)
+            for (int k = kb + kp; k < ke; k += 32) {
+                double v[16];
 #pragma unroll
-                for (int j = 0; j < 8; j++) v[j] = (k + 8 * j < ke) ? slice_load(d, r, k + 8 * j) : 0.0;
+                for (int j = 0; j < 16; j++) v[j] = (k + 2 * j < ke) ? slice_load(d, r, k + 2 * j) : 0.0;
 #pragma unroll
-                for (int j = 0; j < 8; j++) mx = max(mx, exp_field(v[j]));
+                for (int j = 0; j < 16; j++) mx = max(mx, exp_field(v[j]));
             }
         red[ty][tx] = mx;
         __syncthreads();
-        if (ty == 0 && r < d.rows) {
-            int m = 0;
-            for (int w = 0; w < 8; w++) m = max(m, red[w][tx]);
+        if (ty < 4 && r < nrows) {
+            const int m = max(red[ty][tx], red[ty + 4][tx]);
             if (m > 0) atomicMax(d.e + r, m - 1022);
         }
     } else {
@@ -86,16 +99,16 @@ __global__ void k_slice_exp(const SliceDesc* D, int nop)
         for (int q = 0; q < 4; q++) {
             const int r = r0 + ty + 8 * q;
             int m = 0;
-            if (r < d.rows)
-                for (int k = kb + tx; k < ke; k += 256) {
-                    double v[8];
+            if (r < nrows)
+                for (int k = kb + tx; k < ke; k += 512) {
+                    double v[16];
 #pragma unroll
-                    for (int j = 0; j < 8; j++) v[j] = (k + 32 * j < ke) ? slice_load(d, r, k + 32 * j) : 0.0;
+                    for (int j = 0; j < 16; j++) v[j] = (k + 32 * j < ke) ? slice_load(d, r, k + 32 * j) : 0.0;
 #pragma unroll
-                    for (int j = 0; j < 8; j++) m = max(m, exp_field(v[j]));
+                    for (int j = 0; j < 16; j++) m = max(m, exp_field(v[j]));
                 }
             m = __reduce_max_sync(0xffffffffu, m);
-            if (tx == 0 && r < d.rows && m > 0) atomicMax(d.e + r, m - 1022);
+            if (tx == 0 && r < nrows && m > 0) atomicMax(d.e + r, m - 1022);
         }
     }
 }
@@ -123,28 +136,31 @@ __device__ __forceinline__ long long slice_mag(double x, int e, int bs)
 // keeps the transposing stores at most 2-way).  Digits come from the 64-bit
 // magnitude by 32-bit funnel shifts (beta s <= 56 < 64).
 #define SL_T 64
+#define SL_R 128  // rows of a slicing tile (1 KiB runs of a column-major operand's columns)
+#define SL_NT 512 // threads of a slicing CTA
 #define SL_G 10   // padded group length (doubles)
 #define SL_ROW (8 * SL_G + 2)   // +2: row stride 164 words
 
 // The 64 x 64 tile of the operand at (r0, k0) into shared memory, rows of 8
 // padded groups of 8 doubles; all 16 loads of a thread are issued before any
 // shared-memory store.
-__device__ __forceinline__ void slice_tile_load(const SliceDesc& d, double (*T)[SL_ROW], int r0, int k0)
+__device__ __forceinline__ void slice_tile_load(const SliceDesc& d, double (*T)[SL_ROW], int r0, int k0,
+                                                int nrows, int Kact)
 {
     const int tid = threadIdx.x;
-    double v[SL_T * SL_T / 256];
+    double v[SL_R * SL_T / SL_NT];
 #pragma unroll
-    for (int t = 0; t < SL_T * SL_T / 256; t++) {
-        const int idx = tid + 256 * t;
+    for (int t = 0; t < SL_R * SL_T / SL_NT; t++) {
+        const int idx = tid + SL_NT * t;
         int r, k;
-        if (d.sr == 1) { r = idx % SL_T; k = idx / SL_T; } else { k = idx % SL_T; r = idx / SL_T; }
-        v[t] = (r0 + r < d.rows && k0 + k < d.K) ? slice_load(d, r0 + r, k0 + k) : 0.0;
+        if (d.sr == 1) { r = idx % SL_R; k = idx / SL_R; } else { k = idx % SL_T; r = idx / SL_T; }
+        v[t] = (r0 + r < nrows && k0 + k < Kact) ? slice_load(d, r0 + r, k0 + k) : 0.0;
     }
 #pragma unroll
-    for (int t = 0; t < SL_T * SL_T / 256; t++) {
-        const int idx = tid + 256 * t;
+    for (int t = 0; t < SL_R * SL_T / SL_NT; t++) {
+        const int idx = tid + SL_NT * t;
         int r, k;
-        if (d.sr == 1) { r = idx % SL_T; k = idx / SL_T; } else { k = idx % SL_T; r = idx / SL_T; }
+        if (d.sr == 1) { r = idx % SL_R; k = idx / SL_R; } else { k = idx % SL_T; r = idx / SL_T; }
         T[r][(k >> 3) * SL_G + (k & 7)] = v[t];
     }
 }
@@ -159,25 +175,31 @@ __device__ __forceinline__ void slice_tile_load(const SliceDesc& d, double (*T)[
 // stride of 82 doubles keeps the transposing stores at most 2-way).  Digits
 // come from the 64-bit magnitude by 32-bit funnel shifts (beta s <= 56 < 64).
 // General form (any beta, BF16 or FP16 slices).
-__global__ void __launch_bounds__(256) k_slice(const SliceDesc* D, int nop)
+__global__ void __launch_bounds__(SL_NT) k_slice(const SliceDesc* D, int nop)
 {
     const int t = blockIdx.x;   // flattened (operand, 64-row tile, 64-wide k tile)
     const SliceDesc d = D[sl_operand(D, nop, t, false)];
     const int ky = (d.Kp + SL_T - 1) / SL_T;
-    const int k0 = ((t - d.t_sl) % ky) * SL_T, r0 = ((t - d.t_sl) / ky) * SL_T;
-    if (k0 >= d.Kp || r0 >= d.rows) return;
-    __shared__ __align__(16) double T[SL_T][SL_ROW];
+    const int k0 = ((t - d.t_sl) % ky) * SL_T, r0 = ((t - d.t_sl) / ky) * SL_R;
+    // actual sizes (device-sized operands: the upper bounds only place the tiles);
+    // digits are written up to the actual K rounded to 32, zero past K
+    const int nrows = (d.dynK && d.dyn_rows) ? *d.dynK : d.rows;
+    const int Kact = d.dynK ? *d.dynK : d.K;
+    const int Kpa = d.dynK ? min(d.Kp, max(32, ((Kact + 31) / 32) * 32)) : d.Kp;
+    if (k0 >= Kpa || r0 >= nrows) return;
+    extern __shared__ __align__(16) double sl_smem[];
+    double (*T)[SL_ROW] = (double (*)[SL_ROW])sl_smem;   // SL_R rows
     const int tid = threadIdx.x;
-    slice_tile_load(d, T, r0, k0);
+    slice_tile_load(d, T, r0, k0, nrows, Kact);
     __syncthreads();
     const int bs = d.beta * d.s;
     const unsigned mask = (1u << d.beta) - 1u;
 #pragma unroll
-    for (int i = 0; i < (SL_T * SL_T / 8) / 256; i++) {
-        const int u = tid + 256 * i;
+    for (int i = 0; i < (SL_R * SL_T / 8) / SL_NT; i++) {
+        const int u = tid + SL_NT * i;
         const int r = u / (SL_T / 8), kg = u % (SL_T / 8);
         const int row = r0 + r, kk = k0 + kg * 8;
-        if (row >= d.rows || kk >= d.Kp) continue;
+        if (row >= nrows || kk >= Kpa) continue;
         const int e = d.e[row];
         unsigned mlo[8], mhi[8];
         float sg[8];
@@ -233,16 +255,22 @@ __global__ void __launch_bounds__(256) k_slice(const SliceDesc* D, int nop)
 // converted exactly through FP32.  The entries' signs are then set by an XOR of
 // the sign bits.  Every value is exact.
 template <int S>
-__global__ void __launch_bounds__(256, 4) k_slice7(const SliceDesc* D, int nop)
+__global__ void __launch_bounds__(SL_NT, 2) k_slice7(const SliceDesc* D, int nop)
 {
     const int t = blockIdx.x;   // flattened (operand, 64-row tile, 64-wide k tile)
     const SliceDesc d = D[sl_operand(D, nop, t, false)];
     const int ky = (d.Kp + SL_T - 1) / SL_T;
-    const int k0 = ((t - d.t_sl) % ky) * SL_T, r0 = ((t - d.t_sl) / ky) * SL_T;
-    if (k0 >= d.Kp || r0 >= d.rows) return;
-    __shared__ __align__(16) double T[SL_T][SL_ROW];
+    const int k0 = ((t - d.t_sl) % ky) * SL_T, r0 = ((t - d.t_sl) / ky) * SL_R;
+    // actual sizes (device-sized operands: the upper bounds only place the tiles);
+    // digits are written up to the actual K rounded to 32, zero past K
+    const int nrows = (d.dynK && d.dyn_rows) ? *d.dynK : d.rows;
+    const int Kact = d.dynK ? *d.dynK : d.K;
+    const int Kpa = d.dynK ? min(d.Kp, max(32, ((Kact + 31) / 32) * 32)) : d.Kp;
+    if (k0 >= Kpa || r0 >= nrows) return;
+    extern __shared__ __align__(16) double sl_smem[];
+    double (*T)[SL_ROW] = (double (*)[SL_ROW])sl_smem;   // SL_R rows
     const int tid = threadIdx.x;
-    slice_tile_load(d, T, r0, k0);
+    slice_tile_load(d, T, r0, k0, nrows, Kact);
     __syncthreads();
     constexpr int BS = 7 * S;
     // 64 in every base-128 digit below the top one
@@ -250,11 +278,11 @@ __global__ void __launch_bounds__(256, 4) k_slice7(const SliceDesc* D, int nop)
 #pragma unroll
     for (int j = 0; j < S - 1; j++) B |= 64ull << (7 * j);
 #pragma unroll
-    for (int i = 0; i < (SL_T * SL_T / 8) / 256; i++) {
-        const int u = tid + 256 * i;
+    for (int i = 0; i < (SL_R * SL_T / 8) / SL_NT; i++) {
+        const int u = tid + SL_NT * i;
         const int r = u / (SL_T / 8), kg = u % (SL_T / 8);
         const int row = r0 + r, kk = k0 + kg * 8;
-        if (row >= d.rows || kk >= d.Kp) continue;
+        if (row >= nrows || kk >= Kpa) continue;
         const int e = d.e[row];
         unsigned long long m[8];
         unsigned sgn[4];   // sign bits of the pairs at bits 15 and 31
@@ -367,48 +395,56 @@ SplitPrec split_prec(int kind, int bits)
     return p;
 }
 
-double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStream_t st, int* rc,
-                         int* status, int kind, int bits)
+// Byte counts of a prepared launch: descriptors, tensor maps, tile offsets and
+// exponents (small), and the slices of every operand (large).
+static void split_sizes(const std::vector<GemmDesc>& g, const SplitPrec& pr, size_t* desc_bytes,
+                        size_t* slice_bytes)
+{
+    size_t erows = 0, sb = 0;
+    for (const GemmDesc& d : g) {
+        const int Kt = d.Kd + d.Kd2;
+        const int kp = std::max(32, ((Kt + 31) / 32) * 32);
+        sb += al256((size_t)pr.s * d.M * kp * 2) + al256((size_t)pr.s * d.N * kp * 2);
+        erows += (size_t)d.M + d.N;
+    }
+    *desc_bytes = al256(erows * 4) + al256(g.size() * 2 * sizeof(SliceDesc)) +
+                  al256(g.size() * sizeof(SplitGemmDesc)) + al256(g.size() * sizeof(int)) +
+                  al256(g.size() * 2 * sizeof(CUtensorMap)) + 1024;
+    *slice_bytes = sb + 256;
+}
+
+// Builds the descriptors of one split-product launch (ng problems) with their
+// tensor maps, in device memory at desc (descriptors, exponents) and slices
+// (operand slices); the uploads are ordered on st.  Problems with device sizes
+// (GemmDesc::dynK) are described by their upper bounds.
+static int split_prepare(const std::vector<GemmDesc>& gin, char* desc, char* slices,
+                         cudaStream_t st, int kind, int bits, SplitLaunch* L)
 {
     const SplitPrec pr = split_prec(kind, bits);
-    *rc = TDEIG_OK;
+    L->pr = pr;
+    L->ng = 0;
     std::vector<GemmDesc> g;
     for (const GemmDesc& d : gin)
         if (d.M > 0 && d.N > 0) g.push_back(d);
-    if (g.empty()) return 0.0;
-    // scratch: slices and exponents of both operands of every problem, descriptors
-    size_t bytes = al256(g.size() * 2 * sizeof(SliceDesc)) + al256(g.size() * sizeof(SplitGemmDesc)) +
-                   al256(g.size() * sizeof(int)) + al256(g.size() * 2 * sizeof(CUtensorMap));
-    std::vector<int> betas(g.size()), ss(g.size()), kps(g.size());
+    if (g.empty()) return TDEIG_OK;
+    std::vector<int> kps(g.size());
     double flops = 0.0, tflops = 0.0, sbytes = 0.0, ebytes = 0.0;
+    const int s = pr.s;
     for (size_t i = 0; i < g.size(); i++) {
-        betas[i] = pr.beta;
-        ss[i] = pr.s;
         const int Kt = g[i].Kd + g[i].Kd2;
         kps[i] = std::max(32, ((Kt + 31) / 32) * 32);
-        bytes += al256((size_t)ss[i] * g[i].M * kps[i] * 2) + al256((size_t)ss[i] * g[i].N * kps[i] * 2);
-        bytes += ((size_t)g[i].M + g[i].N) * 4;
         flops += 2.0 * g[i].M * g[i].N * Kt;
-        tflops += 2.0 * g[i].M * g[i].N * Kt * (ss[i] * (ss[i] + 1) / 2);
+        tflops += 2.0 * g[i].M * g[i].N * Kt * (s * (s + 1) / 2);
         // algorithmic traffic: every operand element read once by each slicing kernel,
         // 2 s bytes of slices written per padded element
         const double elems = (double)(g[i].M + g[i].N) * Kt;
-        sbytes += 8.0 * elems + 2.0 * ss[i] * (double)(g[i].M + g[i].N) * kps[i];
+        sbytes += 8.0 * elems + 2.0 * s * (double)(g[i].M + g[i].N) * kps[i];
         ebytes += 8.0 * elems;
     }
-    if (bytes > ws.cap) {
-        cudaStreamSynchronize(st);
-        split_free(ws);
-        const size_t want = bytes + bytes / 4;
-        if (cudaMalloc(&ws.base, want) != cudaSuccess) {
-            cudaGetLastError();
-            *rc = TDEIG_ENOMEM;
-            return 0.0;
-        }
-        ws.cap = want;
-    }
-    char* p = ws.base;
+    char* p = desc;
     auto take = [&](size_t n) { char* r = p; p += al256(n); return r; };
+    char* q = slices;
+    auto take_sl = [&](size_t n) { char* r = q; q += al256(n); return r; };
     // exponents of every operand row in one region, filled with 0xC0 bytes
     // (-1061109568: far below any exponent, and two of them still add without
     // overflow) before k_slice_exp raises them
@@ -423,7 +459,7 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
     std::vector<CUtensorMap> tm(g.size() * 2);
     std::vector<SliceDesc> sl;
     std::vector<SplitGemmDesc> sg;
-    int maxrows = 0, maxkp = 0, tiles = 0;
+    int tiles = 0;
     for (size_t i = 0; i < g.size(); i++) {
         const GemmDesc& d = g[i];
         SliceDesc a;
@@ -437,9 +473,11 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
             a.X2 = d.A2;
             if (!d.transA2) { a.sr2 = 1; a.sk2 = d.lda2; } else { a.sr2 = d.lda2; a.sk2 = 1; }
         }
-        a.rows = d.M; a.K = d.Kd + d.Kd2; a.Kp = kps[i]; a.s = ss[i]; a.beta = betas[i]; a.f16 = pr.f16;
-        a.S = (__nv_bfloat16*)take((size_t)ss[i] * d.M * kps[i] * 2);
+        a.rows = d.M; a.K = d.Kd + d.Kd2; a.Kp = kps[i]; a.s = s; a.beta = pr.beta; a.f16 = pr.f16;
+        a.S = (__nv_bfloat16*)take_sl((size_t)s * d.M * kps[i] * 2);
         a.e = ebase + eoff;
+        a.dynK = d.dynK;
+        a.dyn_rows = 0;
         eoff += d.M;
         SliceDesc b;
         memset(&b, 0, sizeof(b));
@@ -450,45 +488,42 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
             b.X2 = d.B2;
             if (!d.transB2) { b.sr2 = d.ldb2; b.sk2 = 1; } else { b.sr2 = 1; b.sk2 = d.ldb2; }
         }
-        b.rows = d.N; b.K = d.Kd + d.Kd2; b.Kp = kps[i]; b.s = ss[i]; b.beta = betas[i]; b.f16 = pr.f16;
-        b.S = (__nv_bfloat16*)take((size_t)ss[i] * d.N * kps[i] * 2);
+        b.rows = d.N; b.K = d.Kd + d.Kd2; b.Kp = kps[i]; b.s = s; b.beta = pr.beta; b.f16 = pr.f16;
+        b.S = (__nv_bfloat16*)take_sl((size_t)s * d.N * kps[i] * 2);
         b.e = ebase + eoff;
+        b.dynK = d.dynK;
+        b.dyn_rows = 1;   // op(B)^T rows are the N columns, N = K in device-sized products
         eoff += d.N;
         sl.push_back(a);
         sl.push_back(b);
-        maxrows = std::max(maxrows, std::max(d.M, d.N));
-        maxkp = std::max(maxkp, kps[i]);
-        SplitGemmDesc s;
-        memset(&s, 0, sizeof(s));
-        s.SA = a.S; s.SB = b.S; s.ea = a.e; s.eb = b.e;
-        s.M = d.M; s.N = d.N; s.Kp = kps[i]; s.s = ss[i]; s.beta = betas[i];
-        s.C = d.C; s.ldc = d.ldc; s.ccol = d.ccol; s.alpha = d.alpha; s.betac = d.beta;
-        s.rsplit = d.rsplit; s.ktop_end = d.ktop_end; s.kbot_beg = d.kbot_beg;
-        s.chunk = pr.chunk; s.f16 = pr.f16;
-        if (!encode_slices(&tm[2 * i], a.S, kps[i], d.M, ss[i], UM_BM) ||
-            !encode_slices(&tm[2 * i + 1], b.S, kps[i], d.N, ss[i], UM_BN)) {
-            *rc = TDEIG_ECUDA;
-            return 0.0;
-        }
-        s.tmA = dtm + 2 * i;
-        s.tmB = dtm + 2 * i + 1;
-        s.tiles_m = td_cdiv(d.M, UM_BM);
-        s.tile0 = tiles;
-        tiles += s.tiles_m * td_cdiv(d.N, UM_BN);
-        sg.push_back(s);
+        SplitGemmDesc sd;
+        memset(&sd, 0, sizeof(sd));
+        sd.SA = a.S; sd.SB = b.S; sd.ea = a.e; sd.eb = b.e;
+        sd.M = d.M; sd.N = d.N; sd.Kp = kps[i]; sd.s = s; sd.beta = pr.beta;
+        sd.C = d.C; sd.ldc = d.ldc; sd.ccol = d.ccol; sd.alpha = d.alpha; sd.betac = d.beta;
+        sd.rsplit = d.rsplit; sd.ktop_end = d.ktop_end; sd.kbot_beg = d.kbot_beg;
+        sd.chunk = pr.chunk; sd.f16 = pr.f16;
+        sd.dynK = d.dynK; sd.dynG = d.dynG;
+        if (!encode_slices(&tm[2 * i], a.S, kps[i], d.M, s, UM_BM) ||
+            !encode_slices(&tm[2 * i + 1], b.S, kps[i], d.N, s, UM_BN))
+            return TDEIG_ECUDA;
+        sd.tmA = dtm + 2 * i;
+        sd.tmB = dtm + 2 * i + 1;
+        sd.tiles_m = td_cdiv(d.M, UM_BM);
+        sd.tiles_n = td_cdiv(d.N, UM_BN);
+        sd.tile0 = tiles;
+        tiles += sd.tiles_m * sd.tiles_n;
+        sg.push_back(sd);
     }
     // flattened tile lists of the two slicing launches
     long long nexp = 0, nsl = 0;
     for (auto& o : sl) {
         o.t_exp = (int)nexp;
         o.t_sl = (int)nsl;
-        nexp += (long long)td_cdiv(o.rows, 32) * td_cdiv(o.K, SE_K);
-        nsl += (long long)td_cdiv(o.Kp, SL_T) * td_cdiv(o.rows, SL_T);
+        nexp += (long long)td_cdiv(o.rows, se_rows(o.sr)) * td_cdiv(o.K, se_kchunk(o.sr));
+        nsl += (long long)td_cdiv(o.Kp, SL_T) * td_cdiv(o.rows, SL_R);
     }
-    if (nexp >= (1ll << 31) || nsl >= (1ll << 31)) {
-        *rc = TDEIG_EINVAL;
-        return 0.0;
-    }
+    if (nexp >= (1ll << 31) || nsl >= (1ll << 31)) return TDEIG_EINVAL;
     std::vector<int> t0(sg.size());
     for (size_t i = 0; i < sg.size(); i++) t0[i] = sg[i].tile0;
     if (cudaMemcpyAsync(dtm, tm.data(), tm.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st) !=
@@ -498,49 +533,111 @@ double split_launch_gemm(const std::vector<GemmDesc>& gin, SplitWS& ws, cudaStre
         cudaMemcpyAsync(dsl, sl.data(), sl.size() * sizeof(SliceDesc), cudaMemcpyHostToDevice, st) !=
             cudaSuccess ||
         cudaMemcpyAsync(dsg, sg.data(), sg.size() * sizeof(SplitGemmDesc), cudaMemcpyHostToDevice, st) !=
-            cudaSuccess) {
+            cudaSuccess)
+        return TDEIG_ECUDA;
+    // the host vectors are pageable: the copies are staged before returning
+    L->dsl = dsl; L->nop = (int)sl.size(); L->nexp = nexp; L->nsl = nsl;
+    L->dsg = dsg; L->dt0 = dt0; L->ng = (int)sg.size(); L->tiles = tiles;
+    L->ebase = ebase; L->erows = erows;
+    L->flops = flops; L->tflops = tflops; L->sbytes = sbytes; L->ebytes = ebytes;
+    double kbl = 0.0;
+    for (size_t i = 0; i < g.size(); i++)
+        kbl += (double)sg[i].tiles_m * sg[i].tiles_n * (kps[i] / UM_BK);
+    snprintf(L->note, sizeof(L->note), "[%d,%.0f,%d,%d,%.6e]", tiles, kbl, s, (int)g.size(), tflops);
+    return TDEIG_OK;
+}
+
+// The kernels of a prepared launch: exponents, slices, the tensor-core product.
+void split_run(const SplitLaunch& L, int* status, cudaStream_t st, int* rc)
+{
+    *rc = TDEIG_OK;
+    if (L.ng == 0) return;
+    const SplitPrec& pr = L.pr;
+    if (cudaMemsetAsync(L.ebase, 0xC0, L.erows * 4, st) != cudaSuccess) {
         *rc = TDEIG_ECUDA;
-        return 0.0;
+        return;
     }
-    if (cudaMemsetAsync(ebase, 0xC0, erows * 4, st) != cudaSuccess) {
-        *rc = TDEIG_ECUDA;
-        return 0.0;
-    }
-    const int nop = (int)sl.size();
     td_prof_begin(st);
-    k_slice_exp<<<(unsigned)nexp, 256, 0, st>>>(dsl, nop);
+    k_slice_exp<<<(unsigned)L.nexp, 256, 0, st>>>(L.dsl, L.nop);
     td_prof_end(st, "k_slice_exp");
-    const unsigned gs = (unsigned)nsl;
+    const unsigned gs = (unsigned)L.nsl;
+    const size_t tile_smem = (size_t)SL_R * SL_ROW * sizeof(double);   // 82 KiB: opt-in size
     td_prof_begin(st);
     if (pr.beta == 7 && !pr.f16) {
+        const void* fn;
         switch (pr.s) {
-        case 1: k_slice7<1><<<gs, 256, 0, st>>>(dsl, nop); break;
-        case 2: k_slice7<2><<<gs, 256, 0, st>>>(dsl, nop); break;
-        case 3: k_slice7<3><<<gs, 256, 0, st>>>(dsl, nop); break;
-        case 4: k_slice7<4><<<gs, 256, 0, st>>>(dsl, nop); break;
-        case 5: k_slice7<5><<<gs, 256, 0, st>>>(dsl, nop); break;
-        case 6: k_slice7<6><<<gs, 256, 0, st>>>(dsl, nop); break;
-        case 7: k_slice7<7><<<gs, 256, 0, st>>>(dsl, nop); break;
-        default: k_slice7<8><<<gs, 256, 0, st>>>(dsl, nop); break;
+        case 1: fn = (const void*)k_slice7<1>; break;
+        case 2: fn = (const void*)k_slice7<2>; break;
+        case 3: fn = (const void*)k_slice7<3>; break;
+        case 4: fn = (const void*)k_slice7<4>; break;
+        case 5: fn = (const void*)k_slice7<5>; break;
+        case 6: fn = (const void*)k_slice7<6>; break;
+        case 7: fn = (const void*)k_slice7<7>; break;
+        default: fn = (const void*)k_slice7<8>; break;
+        }
+        td_smem_attr(fn, tile_smem);
+        switch (pr.s) {
+        case 1: k_slice7<1><<<gs, SL_NT, tile_smem, st>>>(L.dsl, L.nop); break;
+        case 2: k_slice7<2><<<gs, SL_NT, tile_smem, st>>>(L.dsl, L.nop); break;
+        case 3: k_slice7<3><<<gs, SL_NT, tile_smem, st>>>(L.dsl, L.nop); break;
+        case 4: k_slice7<4><<<gs, SL_NT, tile_smem, st>>>(L.dsl, L.nop); break;
+        case 5: k_slice7<5><<<gs, SL_NT, tile_smem, st>>>(L.dsl, L.nop); break;
+        case 6: k_slice7<6><<<gs, SL_NT, tile_smem, st>>>(L.dsl, L.nop); break;
+        case 7: k_slice7<7><<<gs, SL_NT, tile_smem, st>>>(L.dsl, L.nop); break;
+        default: k_slice7<8><<<gs, SL_NT, tile_smem, st>>>(L.dsl, L.nop); break;
         }
     } else {
-        k_slice<<<gs, 256, 0, st>>>(dsl, nop);
+        td_smem_attr((const void*)k_slice, tile_smem);
+        k_slice<<<gs, SL_NT, tile_smem, st>>>(L.dsl, L.nop);
     }
     td_prof_end(st, "k_slice");
-    umma_launch(dsg, dt0, (int)sg.size(), tiles, pr.s, pr.nacc, status, st);
+    umma_launch(L.dsg, L.dt0, L.ng, L.tiles, pr.s, pr.nacc, status, st);
     TdCtx& cx = td_ctx();
-    if (cx.prof.on) {
-        // [tiles, k-blocks over all tiles, slices, problems, tensor flops]
-        double kbl = 0.0;
-        for (size_t i = 0; i < g.size(); i++)
-            kbl += (double)sg[i].tiles_m * td_cdiv(g[i].N, UM_BN) * (kps[i] / UM_BK);
-        char nb[160];
-        snprintf(nb, sizeof(nb), "[%d,%.0f,%d,%d,%.6e]", tiles, kbl, pr.s, (int)g.size(), tflops);
-        td_prof_note(nb);
-    }
-    cx.split_tensor_flops += tflops;
-    cx.split_slice_bytes += sbytes;
-    cx.split_exp_bytes += ebytes;
+    // [tiles, k-blocks over all tiles, slices, problems, tensor flops]
+    td_prof_note(L.note);
+    cx.split_tensor_flops += L.tflops;
+    cx.split_slice_bytes += L.sbytes;
+    cx.split_exp_bytes += L.ebytes;
     if (cudaGetLastError() != cudaSuccess) *rc = TDEIG_ECUDA;
-    return flops;
+}
+
+size_t split_launch_bytes(const std::vector<GemmDesc>& g, int kind, int bits, size_t* desc_bytes)
+{
+    size_t db = 0, sb = 0;
+    split_sizes(g, split_prec(kind, bits), &db, &sb);
+    if (desc_bytes) *desc_bytes = db;
+    return sb;
+}
+
+int split_prepare_at(const std::vector<GemmDesc>& g, char* desc, char* slices, cudaStream_t st,
+                     int kind, int bits, SplitLaunch* L)
+{
+    return split_prepare(g, desc, slices, st, kind, bits, L);
+}
+
+int split_reserve(SplitWS& ws, size_t bytes, cudaStream_t st)
+{
+    if (bytes <= ws.cap) return TDEIG_OK;
+    cudaStreamSynchronize(st);
+    split_free(ws);
+    const size_t want = bytes + bytes / 4;
+    if (cudaMalloc(&ws.base, want) != cudaSuccess) {
+        cudaGetLastError();
+        return TDEIG_ENOMEM;
+    }
+    ws.cap = want;
+    return TDEIG_OK;
+}
+
+double split_launch_gemm(const std::vector<GemmDesc>& g, SplitWS& ws, cudaStream_t st, int* rc,
+                         int* status, int kind, int bits)
+{
+    *rc = TDEIG_OK;
+    size_t db = 0, sb = 0;
+    split_sizes(g, split_prec(kind, bits), &db, &sb);
+    if ((*rc = split_reserve(ws, al256(db) + sb, st))) return 0.0;
+    SplitLaunch L;
+    if ((*rc = split_prepare(g, ws.base, ws.base + al256(db), st, kind, bits, &L))) return 0.0;
+    split_run(L, status, st, rc);
+    return L.ng ? L.flops : 0.0;
 }

@@ -226,14 +226,22 @@ __device__ __forceinline__ UmTile um_tile(const SplitGemmDesc* G, const int* t0,
     // column tiles fastest: the CTAs that run at the same time share the row
     // block of op(A), the larger operand here (M >= N), so it is read from
     // memory about once and from L2 by the others
-    const int tiles_n = (g.N + UM_BN - 1) / UM_BN;
+    const int tiles_n = g.tiles_n;
     const int tn = local % tiles_n, tm = local / tiles_n;
     u.row0 = tm * UM_BM;
     u.col0 = tn * UM_BN;
     int kb0 = 0, kb1 = g.Kp;
+    int kbot = g.kbot_beg, ktop = g.ktop_end;
+    if (g.dynK) {
+        // sizes from the device: a column tile past the actual N has no work
+        const int Na = *g.dynK;
+        kb1 = min(g.Kp, ((Na + UM_BK - 1) / UM_BK) * UM_BK);
+        if (u.col0 >= Na) kb1 = 0;
+        if (g.dynG) { kbot = g.dynG[0]; ktop = g.dynG[0] + g.dynG[1]; }
+    }
     if (g.rsplit > 0) {
-        if (u.row0 >= g.rsplit) kb0 = (g.kbot_beg / UM_BK) * UM_BK;
-        if (u.row0 + UM_BM <= g.rsplit) kb1 = min(g.Kp, ((g.ktop_end + UM_BK - 1) / UM_BK) * UM_BK);
+        if (u.row0 >= g.rsplit) kb0 = (kbot / UM_BK) * UM_BK;
+        if (u.row0 + UM_BM <= g.rsplit) kb1 = min(kb1, ((ktop + UM_BK - 1) / UM_BK) * UM_BK);
     }
     u.kb0 = kb0;
     u.nkb = kb1 > kb0 ? (kb1 - kb0) / UM_BK : 0;
@@ -409,7 +417,7 @@ __global__ void __launch_bounds__(UM_NT, 1)
             const SplitGemmDesc& g = G[u.pi];
             const int s = g.s, beta = g.beta, ckb = max(1, g.chunk / UM_BK);
             const int hl = min(s, UM_HI);
-            const int N = g.N;
+            const int N = g.dynK ? *g.dynK : g.N;
             // column metadata of the tile (lane c holds column c), loaded while the
             // sums are computed and read below by shuffles: no cross-warp sync
             const int mcol = u.col0 + lane;

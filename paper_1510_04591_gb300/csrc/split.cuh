@@ -40,6 +40,10 @@ struct SliceDesc {
     __nv_bfloat16* S;   // slice p, row r at S + (p * rows + r) * Kp (16-bit values)
     int* e;             // exponent bound per row: max |row| < 2^e
     int t_exp, t_sl;    // first tile of this operand in the exponent and slicing launches
+    // optional: rows (when dyn_rows) and K read from *dynK at run time; rows, K are
+    // then upper bounds (see GemmDesc::dynK)
+    const int* dynK;
+    int dyn_rows;
 };
 
 // One slice-pair product C = alpha 2^(ea+eb) sum_{p+q<=s-1} ... + betac C.
@@ -59,6 +63,9 @@ struct SplitGemmDesc {
     // TMA tensor maps (device CUtensorMap) of the slices: dims (Kp, rows, s),
     // box (32, 128 | 32, s), 64-byte swizzle
     const void *tmA, *tmB;
+    int tiles_n;                      // column tiles (of the upper bound N with dynK)
+    const int* dynK;                  // optional device sizes (see GemmDesc::dynK)
+    const int* dynG;
 };
 
 // Tensor-core (tcgen05) slice-pair products: tile 128 x 32 per CTA, one TMEM
@@ -92,5 +99,30 @@ struct SplitWS {
 // status: device word that receives TD_STATUS_TIMEOUT when a bounded wait expires.
 double split_launch_gemm(const std::vector<GemmDesc>& g, SplitWS& ws, cudaStream_t st, int* rc,
                          int* status, int kind, int bits);
+
+// A split-product launch prepared ahead of its kernels (descriptors, tensor maps
+// and tile offsets already in device memory): prepared before a CUDA-graph
+// capture, run inside it.
+struct SplitLaunch {
+    SliceDesc* dsl = nullptr;
+    int nop = 0;
+    long long nexp = 0, nsl = 0;
+    SplitGemmDesc* dsg = nullptr;
+    int* dt0 = nullptr;
+    int ng = 0, tiles = 0;
+    int* ebase = nullptr;
+    size_t erows = 0;
+    SplitPrec pr{};
+    double flops = 0, tflops = 0, sbytes = 0, ebytes = 0;
+    char note[160] = {0};
+};
+// Bytes of the slices of a launch (returned) and of its descriptors (*desc_bytes).
+size_t split_launch_bytes(const std::vector<GemmDesc>& g, int kind, int bits, size_t* desc_bytes);
+// Grows the split workspace to at least `bytes` (synchronising st first).
+int split_reserve(SplitWS& ws, size_t bytes, cudaStream_t st);
+// Descriptors at desc, slices at slices (both in device memory, 256-aligned).
+int split_prepare_at(const std::vector<GemmDesc>& g, char* desc, char* slices, cudaStream_t st,
+                     int kind, int bits, SplitLaunch* L);
+void split_run(const SplitLaunch& L, int* status, cudaStream_t st, int* rc);
 // Work counters of the launches go to td_ctx() (common.cuh).
 void split_free(SplitWS& ws);

@@ -35,8 +35,10 @@ static int tune_key(const LevelPlan& L)
     return a * 64 + b;
 }
 
-// A captured solve (dense FP64 mode with device buffers): replayed when the
-// sizes, buffers and workspace are the same as at capture time.
+// A captured solve (dense mode with device buffers): replayed when the sizes,
+// buffers and workspaces are the same as at capture time.  A handle keeps up to
+// TD_GRAPH_CACHE of them (one per chunk of a large batch).
+#define TD_GRAPH_CACHE 16
 struct GraphEntry {
     std::vector<int64_t> N;
     const void *d, *e, *lam, *Q;
@@ -46,6 +48,7 @@ struct GraphEntry {
     int* status = nullptr;
     double* scale = nullptr;
     int64_t batch = 0;
+    char* split_ws = nullptr;          // the split workspace the captured launches use
 };
 
 struct Plan {
@@ -73,7 +76,7 @@ struct tdeig_ctx {
     std::map<int, int> tuned;          // autotuner: level key -> tile shape of the update product
     std::vector<std::pair<int, std::vector<int>>> tuning;   // level key -> event indices of a trial
     std::vector<cudaEvent_t> tune_ev;  // events of the trials of the current solve
-    GraphEntry graph;                  // the last captured solve
+    std::vector<GraphEntry> graphs;    // captured solves (batch chunks), oldest first
     float* mlp = nullptr;              // rank model on the device: params, mean, std
     std::vector<float> records;        // TDEIG_FLAG_RECORD output of the last solve
     int mlp_fallbacks = 0;             // merges rebuilt with the estimate in the last solve
@@ -153,7 +156,8 @@ extern "C" int tdeig_destroy(tdeig_handle h)
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     for (cudaEvent_t e : h->tune_ev) cudaEventDestroy(e);
     for (cudaEvent_t e : h->ctx.prof.ev) cudaEventDestroy(e);
-    if (h->graph.exec) cudaGraphExecDestroy(h->graph.exec);
+    for (auto& g : h->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     if (h->mlp) cudaFree(h->mlp);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -500,33 +504,13 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     const bool d_dev = is_device_ptr(d), e_dev = is_device_ptr(e);
     const bool l_dev = is_device_ptr(lam_out), q_dev = Q_out && is_device_ptr(Q_out);
 
-    // CUDA-graph mode: dense FP64 with device buffers has no host round trip,
-    // so the whole launch sequence (every level of every matrix) is captured
-    // once and replayed while the sizes, buffers and workspace stay the same.
-    const bool graph = (mode & TDEIG_FLAG_GRAPH) && variant == TDEIG_MODE_DENSE &&
-                       prec == TDEIG_PREC_FP64 && d_dev && (e_dev || !e) && l_dev && q_dev;
-    GraphEntry& G = h->graph;
-    if (graph && G.exec && G.N == P.N && G.d == d && G.e == e && G.lam == lam_out && G.Q == Q_out &&
-        G.mode == mode && G.ws == h->ws) {
-        CU(cudaGraphLaunch(G.exec, st));
-        int hs = 0;
-        std::vector<double> sc(batch);
-        CU(cudaMemcpyAsync(&hs, G.status, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CU(cudaMemcpyAsync(sc.data(), G.scale, batch * sizeof(double), cudaMemcpyDeviceToHost, st));
-        CU(cudaStreamSynchronize(st));
-        double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
-        char buf[160];
-        snprintf(buf, sizeof(buf), "{\"graph\":\"replay\",\"seconds\":%.6f,\"status\":%d,\"launches\":1}",
-                 secs, hs);
-        h->stats = buf;
-        for (int64_t b = 0; b < batch; b++)
-            if (sc[b] < 0.0) return TDEIG_EINVAL;
-        return (hs & (TD_STATUS_NOTCONV | TD_STATUS_LEAF)) ? TDEIG_ENOTCONV : TDEIG_OK;
-    }
-    if (G.exec) {
-        cudaGraphExecDestroy(G.exec);
-        G.exec = nullptr;
-    }
+    // CUDA-graph mode: the dense update with device buffers has no host round
+    // trip (the split products are sized by upper bounds and read each merge's
+    // deflated sizes from the device), so the whole launch sequence (every level
+    // of every matrix) is captured once and replayed while the sizes, buffers and
+    // workspace stay the same.
+    const bool graph = (mode & TDEIG_FLAG_GRAPH) && variant == TDEIG_MODE_DENSE && d_dev &&
+                       (e_dev || !e) && l_dev && q_dev;
     // ends a capture that an early error return would otherwise leave open
     struct CaptureGuard {
         cudaStream_t st;
@@ -639,7 +623,69 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     if (!toff_host.empty())
         CU(cudaMemcpyAsync(toff_all, toff_host.data(), toff_host.size() * sizeof(int),
                            cudaMemcpyHostToDevice, st));
+    // Graph mode with split products: every level's launch is prepared before the
+    // capture (descriptors and tensor maps uploaded, sized by upper bounds: N = Kd
+    // = n, the merge's K and K1, Km read by the kernels), all sharing one slice
+    // region since the levels run in order.
+    const bool split = (prec != TDEIG_PREC_FP64);
+    const int split_kind = prec == TDEIG_PREC_BF16X2 ? SPLIT_BF16X2
+                           : prec == TDEIG_PREC_FP16X2 ? SPLIT_FP16X2 : SPLIT_OZAKI;
+    std::vector<SplitLaunch> glaunch(P.levels.size());
+    if (graph && split) {
+        std::vector<std::vector<GemmDesc>> lg(P.levels.size());
+        size_t dtot = 0, smax = 0;
+        std::vector<size_t> doff(P.levels.size(), 0);
+        for (size_t li = 0; li < P.levels.size(); li++) {
+            const LevelPlan& L = P.levels[li];
+            for (size_t i = 0; i < L.merges.size(); i++) {
+                const MergeDesc& m = L.merges[i];
+                GemmDesc g;
+                memset(&g, 0, sizeof(g));
+                g.A = m.W; g.lda = m.n; g.acol = lws.gemmW + m.g0;
+                g.B = m.qhat; g.ldb = m.n;
+                g.C = m.qout; g.ldc = m.n; g.ccol = lws.posNew + m.g0;
+                g.M = m.n; g.N = m.n; g.Kd = m.n; g.alpha = 1.0;
+                g.rsplit = m.n1;
+                g.dynK = lws.K + i;
+                g.dynG = lws.kgrp + 2 * i;
+                lg[li].push_back(g);
+            }
+            size_t db = 0;
+            const size_t sb = split_launch_bytes(lg[li], split_kind, TD_SPLIT_BITS, &db);
+            doff[li] = dtot;
+            dtot += (db + 255) & ~(size_t)255;
+            smax = std::max(smax, sb);
+        }
+        if ((rc = split_reserve(h->split, dtot + smax, st))) return rc;
+        for (size_t li = 0; li < P.levels.size(); li++)
+            if ((rc = split_prepare_at(lg[li], h->split.base + doff[li], h->split.base + dtot, st,
+                                       split_kind, TD_SPLIT_BITS, &glaunch[li])))
+                return rc;
+    }
     if (graph) {
+        // A solve captured before with the same sizes, buffers and workspaces is
+        // replayed.  The descriptors it reads were uploaded again above: captured
+        // solves of other sizes (batch chunks) share the workspace regions.
+        for (size_t gi = 0; gi < h->graphs.size(); gi++) {
+            GraphEntry& G = h->graphs[gi];
+            if (!(G.exec && G.N == P.N && G.d == d && G.e == e && G.lam == lam_out && G.Q == Q_out &&
+                  G.mode == mode && G.ws == h->ws && G.split_ws == h->split.base))
+                continue;
+            CU(cudaGraphLaunch(G.exec, st));
+            int hs = 0;
+            std::vector<double> sc(batch);
+            CU(cudaMemcpyAsync(&hs, G.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CU(cudaMemcpyAsync(sc.data(), G.scale, batch * sizeof(double), cudaMemcpyDeviceToHost, st));
+            CU(cudaStreamSynchronize(st));
+            double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+            char buf[160];
+            snprintf(buf, sizeof(buf), "{\"graph\":\"replay\",\"seconds\":%.6f,\"status\":%d,\"launches\":1}",
+                     secs, hs);
+            h->stats = buf;
+            for (int64_t b = 0; b < batch; b++)
+                if (sc[b] < 0.0) return TDEIG_EINVAL;
+            return (hs & (TD_STATUS_NOTCONV | TD_STATUS_LEAF)) ? TDEIG_ENOTCONV : TDEIG_OK;
+        }
         CU(cudaStreamSynchronize(st));
         CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         cap.active = true;
@@ -693,10 +739,9 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
         MARK("secular", lv);
         td_launch_secular(Md, nm, L.rows, lws, status, st);
         bool any_hss = false;
-        const bool split = (prec != TDEIG_PREC_FP64);
         std::vector<int> Kh, Gh;
         const bool hss_level = variant != TDEIG_MODE_DENSE && L.nmax > h->opt.hss_threshold;
-        if (hss_level || split) {
+        if (hss_level || (split && !graph)) {
             // sizes of the deflated problems, needed to size the launches below
             Kh.resize(nm);
             Gh.resize(2 * nm);
@@ -716,6 +761,9 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
                                   hss_js, [&](const char* nm) { return mark(nm, lv); },
                                   split ? &h->split : nullptr, &learn);
             if (rc) return rc;
+        } else if (split && graph) {
+            split_run(glaunch[li], status, st, &rc);
+            if (rc) return rc;
         } else if (split) {
             // block-structured update as split-precision tensor-core products
             std::vector<GemmDesc> gd;
@@ -726,7 +774,7 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
                 GemmDesc g;
                 memset(&g, 0, sizeof(g));
                 g.A = m.W; g.lda = m.n; g.acol = lws.gemmW + m.g0;
-                g.B = m.qhat; g.ldb = K;
+                g.B = m.qhat; g.ldb = m.n;   // product order, leading dimension n
                 g.C = m.qout; g.ldc = m.n; g.ccol = lws.posNew + m.g0;
                 g.M = m.n; g.N = K; g.Kd = K; g.alpha = 1.0;
                 g.rsplit = m.n1; g.ktop_end = Gh[2 * i] + Gh[2 * i + 1]; g.kbot_beg = Gh[2 * i];
@@ -775,6 +823,12 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
         const cudaError_t ie = cudaGraphInstantiate(&ex, gr, 0);
         cudaGraphDestroy(gr);
         if (ie != cudaSuccess) return TDEIG_ECUDA;
+        if (h->graphs.size() >= TD_GRAPH_CACHE) {   // the oldest capture makes room
+            if (h->graphs.front().exec) cudaGraphExecDestroy(h->graphs.front().exec);
+            h->graphs.erase(h->graphs.begin());
+        }
+        h->graphs.emplace_back();
+        GraphEntry& G = h->graphs.back();
         G.exec = ex;
         G.N = P.N;
         G.d = d; G.e = e; G.lam = lam_out; G.Q = Q_out;
@@ -783,6 +837,7 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
         G.status = status;
         G.scale = B.scale;
         G.batch = batch;
+        G.split_ws = h->split.base;
         CU(cudaGraphLaunch(ex, st));
     }
 

@@ -172,11 +172,15 @@ __device__ inline int td_find_merge(const MergeDesc* M, int nmerge, int g)
 }
 
 // d_k - lambda_j by Remark 1: (d_k - d_j) - gamma_j if k <= j, else
-// (d_k - d_{j+1}) + mu_j.
+// (d_k - d_{j+1}) + mu_j.  The operands are selected, not the results, so a
+// term costs one FP64 subtract and one add (x - g and x + (-g) round alike).
 __device__ __forceinline__ double td_dminus(const double* d, const double* gam, const double* mu,
                                             int k, int j)
 {
-    return (k <= j) ? (d[k] - d[j]) - gam[j] : (d[k] - d[j + 1]) + mu[j];
+    const bool below = (k <= j);
+    const double pole = below ? d[j] : d[j + 1];
+    const double off = below ? -gam[j] : mu[j];
+    return (d[k] - pole) + off;
 }
 
 __device__ __forceinline__ double td_warp_sum(double v)

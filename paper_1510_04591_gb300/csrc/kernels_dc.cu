@@ -1230,14 +1230,23 @@ __global__ void k_lowner(const MergeDesc* M, int nmerge, int rows, LevelWS ws)
     // its power of two kept in an integer: a factor of the scaled matrix is at
     // most 8 in magnitude, and 4 of them stay inside the FP64 range unless pole
     // gaps fall below 1e-75.
+    // lambda_j - d_i by Remark 1: (d_j+1 - d_i) - mu_j for j < i, (d_j - d_i) +
+    // gamma_j for j > i (reusing the denominator): two loops, so that no term
+    // evaluates both forms (a select of the two cost the FP64 pipe both)
     double pn = 1.0, pd = 1.0;
     int ex = 0, cnt = 0;
-    for (int j = lane; j < K; j += 32) {
-        if (j == i) continue;
+    for (int j = lane; j < i; j += 32) {
+        pn *= (d[j + 1] - di) - mu[j];
+        pd *= d[j] - di;
+        if (++cnt == 4) {
+            cnt = 0;
+            pn = td_renorm(pn, &ex, 1);
+            pd = td_renorm(pd, &ex, -1);
+        }
+    }
+    for (int j = i + 1 + lane; j < K; j += 32) {
         const double den = d[j] - di;
-        // lambda_j - d_i by Remark 1: (d_j - d_i) + gamma_j for j > i (the same
-        // value as -td_dminus, reusing the denominator), (d_j+1 - d_i) - mu_j below
-        pn *= (j > i) ? den + gam[j] : -td_dminus(d, gam, mu, i, j);
+        pn *= den + gam[j];
         pd *= den;
         if (++cnt == 4) {
             cnt = 0;
@@ -1289,10 +1298,17 @@ __global__ void __launch_bounds__(CAUCHY_NT) k_cauchy(const MergeDesc* M, int nm
     // write_qhat: 0 v only; 1 rows in secular order; 2 rows in the order of the
     // update product (gemmCol), so the product reads Qhat contiguously.
     const int* perm = (write_qhat == 2) ? ws.gemmCol + g0 : nullptr;
+    // d_k - lambda_j (Remark 1) with the column's poles and offsets held in
+    // registers: (d_k - d_j) - gamma_j for k <= j, (d_k - d_j+1) + mu_j above
+    const double dj = d[j], ngj = -gam[j];
+    const double dj1 = (j + 1 < K) ? d[j + 1] : 0.0, mj = mu[j];
+    auto term = [&](int k) {
+        const bool below = (k <= j);
+        return uh[k] * td_recip((d[k] - (below ? dj : dj1)) + (below ? ngj : mj));
+    };
     double acc = 0.0;
     for (int p = threadIdx.x; p < K; p += blockDim.x) {
-        const int k = perm ? perm[p] : p;
-        double t = uh[k] * td_recip(td_dminus(d, gam, mu, k, j));
+        const double t = term(perm ? perm[p] : p);
         if (SMEM) col[p] = t;
         acc += t * t;
     }
@@ -1311,8 +1327,7 @@ __global__ void __launch_bounds__(CAUCHY_NT) k_cauchy(const MergeDesc* M, int nm
     // launches can then be sized without knowing K), K in secular order
     double* out = md.qhat + (int64_t)j * (write_qhat == 2 ? md.n : K);
     for (int p = threadIdx.x; p < K; p += blockDim.x) {
-        const int k = perm ? perm[p] : p;
-        double t = SMEM ? col[p] : uh[k] * td_recip(td_dminus(d, gam, mu, k, j));
+        const double t = SMEM ? col[p] : term(perm ? perm[p] : p);
         out[p] = t * vj;
     }
 }

@@ -7,8 +7,7 @@
 //   k_leaf_apply    the rotations applied to Q (warp per leaf), eigenpairs sorted
 //   k_prep          eq. T3: u from the children's Q rows; sort; deflation
 //                   (tiny z and close-pole Givens tests); compaction
-//   k_build_w       sorted diag(Q1, Q2) columns
-//   k_rotate        deflation rotations applied to those columns
+//   k_build_w       sorted diag(Q1, Q2) columns with the deflation rotations applied
 //   k_secular       Theorem 1 roots, one warp per root, with gamma/mu of Remark 1
 //   k_lowner        eq. ev_z, one warp per entry
 //   k_cauchy        eq. Ev-Q column normalisation and the Cauchy-like matrix
@@ -543,12 +542,22 @@ __global__ void __launch_bounds__(PREP_NT) k_prep(const MergeDesc* M, LevelWS ws
         const double tau = s_tau;
         int j = -1, nrot = 0, mj = 0;
         double dj = 0.0, zj = 0.0;
+        // the next batch's entries are loaded while this one is decided (the
+        // sweep writes only entries at or below the current batch)
+        double nd0 = lane < n ? ws.dsort[g0 + lane] : 0.0;
+        double nz0 = lane < n ? ws.zsort[g0 + lane] : 0.0;
+        int ns0 = lane < n ? ws.src[g0 + lane] : 0;
         for (int base = 0; base < n; base += 32) {
             const int i = base + lane;
             const bool valid = i < n;
-            const double d0 = valid ? ws.dsort[g0 + i] : 0.0;
-            const double z0 = valid ? ws.zsort[g0 + i] : 0.0;
-            const int m0 = valid ? ((ws.src[g0 + i] < n1) ? 1 : 2) : 0;
+            const double d0 = valid ? nd0 : 0.0;
+            const double z0 = valid ? nz0 : 0.0;
+            const int m0 = valid ? ((ns0 < n1) ? 1 : 2) : 0;
+            if (i + 32 < n) {
+                nd0 = ws.dsort[g0 + i + 32];
+                nz0 = ws.zsort[g0 + i + 32];
+                ns0 = ws.src[g0 + i + 32];
+            }
             const bool type1 = valid && (rho * fabs(z0) <= tau);
             const bool cand = valid && !type1;
             const unsigned cmask = __ballot_sync(FULL, cand);
@@ -685,122 +694,115 @@ __global__ void __launch_bounds__(PREP_NT) k_prep(const MergeDesc* M, LevelWS ws
     }
 }
 
-// W[:, c] = column src[c] of diag(Q1, Q2), for the sorted order c.
-// Grid: (merge, 256-row tile, 32-column tile).
-__global__ void k_build_w(const MergeDesc* M, LevelWS ws)
+// W[:, c] = column src[c] of diag(Q1, Q2) for the sorted order c, with the
+// deflation rotations applied: one pass that reads each source column once and
+// writes each W column once.
+// Structure used: the sweep visits i in ascending order and rotates it against
+// the last survivor j < i, so the rotations come sorted by i, and a chain
+// (a maximal run whose j is the previous rotation's i) covers an interval of
+// columns that no other chain enters (the columns strictly inside a chain that
+// are not its i's are type-1 deflations, which no rotation touches).  A row
+// visits its columns in ascending order holding the latest value of the
+// chain's current j in a register: at a chain's first j the source value is
+// held; at each i the pair is rotated, the j column stored and the rotated i
+// held (stored when the chain ends); every other column is a plain copy.
+// Grid: (merge, 256-row tile, BW_G column groups); group boundaries are moved
+// forward out of chains, so each group applies whole chains.  The control flow
+// depends only on the column and the rotation list: it is uniform in a CTA.
+#define BW_NT 256
+#define BW_G 32
+#define BW_U 8   // source columns loaded ahead of their use
+
+// The smallest b' >= b that no chain straddles (no chain has its first j below
+// b' and a later column at or above it).
+__device__ int bw_boundary(const LevelWS& ws, int g0, int nrot, int n, int b)
 {
-    MergeDesc md = M[blockIdx.x];
-    const int n = md.n, n1 = md.n1, n2 = n - n1;
-    const int rt = blockIdx.y, ct = blockIdx.z;
-    if (ct * 32 >= n) return;
-    const int r = rt * 256 + threadIdx.x;
-    if (r >= n) return;
-    for (int cc = 0; cc < 32; cc++) {
-        int c = ct * 32 + cc;
-        if (c >= n) break;
-        // src is a permutation of [0, n) for ordered input; the clamp keeps a
-        // non-finite input (reported as TDEIG_EINVAL) from indexing outside.
-        int s = min(max(ws.src[md.g0 + c], 0), n - 1);
-        double v;
-        if (s < n1) v = (r < n1) ? md.qin1[(int64_t)s * n1 + r] : 0.0;
-        else v = (r >= n1) ? md.qin2[(int64_t)(s - n1) * n2 + (r - n1)] : 0.0;
-        md.W[(int64_t)c * n + r] = v;
+    if (b >= n) return n;
+    int lo = 0, hi = nrot;   // first rotation with i >= b
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (ws.rot_i[g0 + mid] < b) lo = mid + 1; else hi = mid;
     }
+    if (lo >= nrot) return b;
+    int st = lo;             // start of its chain
+    while (st > 0 && ws.rot_j[g0 + st] == ws.rot_i[g0 + st - 1]) st--;
+    if (ws.rot_j[g0 + st] >= b) return b;
+    int e = lo;              // end of the chain
+    while (e + 1 < nrot && ws.rot_j[g0 + e + 1] == ws.rot_i[g0 + e]) e++;
+    return min(n, ws.rot_i[g0 + e] + 1);
 }
 
-// Deflation rotations, in sweep order, one row per thread.
-// Grid: (merge, 64-row tile).  The sweep visits i in ascending order and
-// rotates it against the last survivor j, so the column i of a rotation has
-// not been touched before and its j is either the previous rotation's i or a
-// column not touched before.  The kernel keeps the latest rotated i column of
-// its row in a register (stored when the chain breaks and at the end), and
-// loads the untouched columns of the next 8 rotations while it applies the
-// current 8: a sequential load/store chain per rotation left it
-// latency-bound.  A column that turns out to have been touched (checked
-// against the running maximum of the columns seen) is read when its rotation
-// is applied instead.
-// The same structure makes the chains (maximal runs whose j is the previous
-// rotation's i) touch disjoint sets of columns, so they are independent: the
-// rotations are split into ROT_G groups of whole chains (a group starts at the
-// first chain start at or after its even share), each applied by its own CTAs.
-#define ROT_B 8
-#define ROT_G 32
-struct RotBlk {
-    int j[ROT_B], i[ROT_B];
-    double c[ROT_B], s[ROT_B], vj[ROT_B], vi[ROT_B];
-    bool fj[ROT_B], fi[ROT_B];
-};
-
-__device__ __forceinline__ void rot_fetch(RotBlk& b, const LevelWS& ws, int g0, int t0, int nrot,
-                                          int& mx, const double* W, int n, int r)
+__global__ void __launch_bounds__(BW_NT) k_build_w(const MergeDesc* M, LevelWS ws)
 {
-#pragma unroll
-    for (int u = 0; u < ROT_B; u++) {
-        const int t = t0 + u;
-        const bool ok = t < nrot;
-        b.j[u] = ok ? ws.rot_j[g0 + t] : -1;
-        b.i[u] = ok ? ws.rot_i[g0 + t] : -1;
-        b.c[u] = ok ? ws.rot_c[g0 + t] : 1.0;
-        b.s[u] = ok ? ws.rot_s[g0 + t] : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < ROT_B; u++) {
-        // untouched by every earlier rotation: no store to it can precede the load
-        b.fj[u] = b.j[u] > mx;
-        b.fi[u] = b.i[u] > mx && b.i[u] != b.j[u];
-        mx = max(mx, max(b.j[u], b.i[u]));
-    }
-#pragma unroll
-    for (int u = 0; u < ROT_B; u++) {
-        b.vj[u] = (b.j[u] >= 0 && b.fj[u]) ? W[(int64_t)b.j[u] * n + r] : 0.0;
-        b.vi[u] = (b.i[u] >= 0 && b.fi[u]) ? W[(int64_t)b.i[u] * n + r] : 0.0;
-    }
-}
-
-__device__ __forceinline__ void rot_apply(const RotBlk& b, double* W, int n, int r, int& cur, double& cv)
-{
-#pragma unroll
-    for (int u = 0; u < ROT_B; u++) {
-        const int j = b.j[u], i = b.i[u];
-        if (j < 0) continue;
-        if (cur >= 0 && cur != j && cur != i) { W[(int64_t)cur * n + r] = cv; cur = -1; }
-        const double qj = (j == cur) ? cv : b.fj[u] ? b.vj[u] : W[(int64_t)j * n + r];
-        const double qi = (i == cur) ? cv : b.fi[u] ? b.vi[u] : W[(int64_t)i * n + r];
-        const double c = b.c[u], sn = b.s[u];
-        W[(int64_t)j * n + r] = c * qj - sn * qi;
-        cur = i;
-        cv = sn * qj + c * qi;
-    }
-}
-
-__global__ void __launch_bounds__(64) k_rotate(const MergeDesc* M, LevelWS ws)
-{
-    MergeDesc md = M[blockIdx.x];
+    const MergeDesc md = M[blockIdx.x];
+    const int n = md.n, n1 = md.n1, n2 = n - n1, g0 = md.g0;
+    const int G = min(BW_G, (n + 63) / 64);
+    const int r = (int)blockIdx.y * BW_NT + (int)threadIdx.x;
+    if ((int)blockIdx.z >= G || (int)blockIdx.y * BW_NT >= n) return;
+    const bool live = r < n;
     const int nrot = ws.nrot[blockIdx.x];
-    const int n = md.n, g0 = md.g0;
-    const int r = blockIdx.y * blockDim.x + threadIdx.x;
-    if (nrot == 0 || r >= n) return;
-    // this group's whole chains: [tb, te)
-    auto chain_start = [&](int t) { return t == 0 || ws.rot_j[g0 + t] != ws.rot_i[g0 + t - 1]; };
-    int tb = (int)(((int64_t)blockIdx.z * nrot) / ROT_G);
-    int te = (int)(((int64_t)(blockIdx.z + 1) * nrot) / ROT_G);
-    while (tb < nrot && !chain_start(tb)) tb++;
-    while (te < nrot && !chain_start(te)) te++;
-    if (tb >= te) return;
-    double* const W = md.W;
-    int cur = -1;          // column whose latest value is held in cv (not yet stored)
-    double cv = 0.0;
-    int mx = -1;           // largest column touched by the rotations fetched so far
-    RotBlk A, B;
-    rot_fetch(A, ws, g0, tb, te, mx, W, n, r);
-    for (int t0 = tb; t0 < te; t0 += 2 * ROT_B) {
-        if (t0 + ROT_B < te) rot_fetch(B, ws, g0, t0 + ROT_B, te, mx, W, n, r);
-        rot_apply(A, W, n, r, cur, cv);
-        if (t0 + ROT_B >= te) break;
-        if (t0 + 2 * ROT_B < te) rot_fetch(A, ws, g0, t0 + 2 * ROT_B, te, mx, W, n, r);
-        rot_apply(B, W, n, r, cur, cv);
+    __shared__ int s_cb, s_ce, s_t;
+    if (threadIdx.x == 0) {
+        const int cb = bw_boundary(ws, g0, nrot, n, (int)(((int64_t)blockIdx.z * n) / G));
+        const int ce = bw_boundary(ws, g0, nrot, n, (int)(((int64_t)(blockIdx.z + 1) * n) / G));
+        int lo = 0, hi = nrot;   // first rotation with i >= cb
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (ws.rot_i[g0 + mid] < cb) lo = mid + 1; else hi = mid;
+        }
+        s_cb = cb; s_ce = ce; s_t = lo;
     }
-    if (cur >= 0) W[(int64_t)cur * n + r] = cv;
+    __syncthreads();
+    const int cb = s_cb, ce = s_ce;
+    int t = s_t;
+    int rj = n, ri = n;
+    double rc = 1.0, rs = 0.0;
+    if (t < nrot) { rj = ws.rot_j[g0 + t]; ri = ws.rot_i[g0 + t]; rc = ws.rot_c[g0 + t]; rs = ws.rot_s[g0 + t]; }
+    double* const W = md.W;
+    int cj = -1;      // column whose latest value is held in cv
+    double cv = 0.0;
+    for (int c0 = cb; c0 < ce; c0 += BW_U) {
+        double q[BW_U];
+#pragma unroll
+        for (int u = 0; u < BW_U; u++) {
+            const int c = c0 + u;
+            double v = 0.0;
+            if (live && c < ce) {
+                // src is a permutation of [0, n) for ordered input; the clamp keeps a
+                // non-finite input (reported as TDEIG_EINVAL) from indexing outside.
+                const int sc = min(max(ws.src[g0 + c], 0), n - 1);
+                if (sc < n1) { if (r < n1) v = md.qin1[(int64_t)sc * n1 + r]; }
+                else if (r >= n1) v = md.qin2[(int64_t)(sc - n1) * n2 + (r - n1)];
+            }
+            q[u] = v;
+        }
+#pragma unroll
+        for (int u = 0; u < BW_U; u++) {
+            const int c = c0 + u;
+            if (c >= ce) break;
+            if (c == ri) {
+                // rotation (j, i): the held j against this source column
+                const double qj = cv, qi = q[u];
+                // cj >= 0: the group holds its chains' first columns (a malformed
+                // rotation list still writes nothing outside W)
+                if (live && cj >= 0) W[(int64_t)cj * n + r] = rc * qj - rs * qi;
+                cv = rs * qj + rc * qi;
+                cj = c;
+                t++;
+                rj = n; ri = n;
+                if (t < nrot) { rj = ws.rot_j[g0 + t]; ri = ws.rot_i[g0 + t]; rc = ws.rot_c[g0 + t]; rs = ws.rot_s[g0 + t]; }
+                if (rj != c) {   // the chain ends here
+                    if (live) W[(int64_t)c * n + r] = cv;
+                    cj = -1;
+                }
+            } else if (c == rj) {
+                cv = q[u];       // first j of a chain
+                cj = c;
+            } else if (live) {
+                W[(int64_t)c * n + r] = q[u];
+            }
+        }
+    }
 }
 
 int td_binary_version(int* out)
@@ -824,10 +826,8 @@ void td_launch_merge_level(const MergeDesc* M, int nmerge, int nmax, int rows, i
 {
     (void)rows; (void)total_tiles; (void)status; (void)use_hss_mask;
     td_prof_begin(st); k_prep<<<nmerge, PREP_NT, 0, st>>>(M, ws); td_prof_end(st, "k_prep");
-    dim3 gw(nmerge, td_cdiv(nmax, 256), td_cdiv(nmax, 32));
-    td_prof_begin(st); k_build_w<<<gw, 256, 0, st>>>(M, ws); td_prof_end(st, "k_build_w");
-    dim3 gr(nmerge, td_cdiv(nmax, 64), ROT_G);
-    td_prof_begin(st); k_rotate<<<gr, 64, 0, st>>>(M, ws); td_prof_end(st, "k_rotate");
+    dim3 gw(nmerge, td_cdiv(nmax, BW_NT), BW_G);
+    td_prof_begin(st); k_build_w<<<gw, BW_NT, 0, st>>>(M, ws); td_prof_end(st, "k_build_w");
 }
 
 // ---------------------------------------------------------------------------

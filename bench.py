@@ -194,8 +194,12 @@ def kernel_work(name, stats_list, pk):
                 "FP64 FMA issue: 152 SMs x 2070 MHz x 2 FMA/clk/SM (measured FMA-chain probe "
                 "1.20 TFLOP/s; cuBLAS DGEMM 1.10)")
     if name == "k_gemm_grouped":
-        return (sum(grouped_flops(s) for s in stats_list) / 1e12, fp64_peak, "alu", "TFLOP/s",
-                "FP64 FMA issue peak, as for k_gemm_f64")
+        fl = sum(grouped_flops(s) - s.get("small_gemm_flops", 0.0) for s in stats_list)
+        return (fl / 1e12, fp64_peak, "alu", "TFLOP/s", "FP64 FMA issue peak, as for k_gemm_f64")
+    if name == "k_gemm_small":
+        return (sum(s.get("small_gemm_flops", 0.0) for s in stats_list) / 1e12, fp64_peak, "alu",
+                "TFLOP/s", "FP64 FMA issue peak, as for k_gemm_f64 (HSS construction products, "
+                "16 x 16 tiles)")
     if name == "k_split_umma":
         peak = pk.get("bf16_tflops", 1900.0)
         return (sum(s.get("split_tensor_flops", 0.0) for s in stats_list) / 1e12, peak, "tensor",

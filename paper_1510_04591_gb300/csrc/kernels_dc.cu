@@ -567,33 +567,56 @@ __global__ void __launch_bounds__(PREP_NT) k_prep(const MergeDesc* M, LevelWS ws
             double fd = d0, fz = z0, c = 0.0, sn = 0.0, djn = 0.0;
             int fm = m0;
             bool rot = false;
+            // A lane recomputes only in the first round and after its predecessor's
+            // state changed (the decision is a function of that state alone).  A
+            // pair is sent to the exact test (the square root and divides, which
+            // cost most of a round on the 1/64-rate FP64 pipe) only when a cheap
+            // bound cannot exclude the rotation: with S = z_i^2 + z_j^2 the exact
+            // |t c s| is |t z_i z_j| / S, every operation of the test is rounded
+            // once, so the computed |t c s| is at least (1 - 9 eps) of it; the
+            // bound |t z_i z_j| > tau S (1 + 1e-12), itself computed with a few
+            // roundings, therefore implies no rotation.  Decisions are those of
+            // the exact test alone.
+            bool lch = true;   // this lane's state changed in the previous round
             for (int it = 0; it < 33; it++) {
-                double pd = __shfl_sync(FULL, fd, pl < 0 ? 0 : pl);
-                double pz = __shfl_sync(FULL, fz, pl < 0 ? 0 : pl);
-                int pmk = __shfl_sync(FULL, fm, pl < 0 ? 0 : pl);
+                const int src = pl < 0 ? 0 : pl;
+                double pd = __shfl_sync(FULL, fd, src);
+                double pz = __shfl_sync(FULL, fz, src);
+                int pmk = __shfl_sync(FULL, fm, src);
+                const bool pch = __shfl_sync(FULL, (int)lch, src) != 0;
                 if (pl < 0) { pd = dj; pz = zj; pmk = mj; }
-                bool nr = false;
-                double nd = d0, nz = z0, nc = 0.0, ns = 0.0, nj = 0.0;
-                int nm = m0;
-                if (cand && has_pred) {
-                    const double t = d0 - pd;
-                    // survivors' weights: rho |z| > tau >= 8 eps rho max|z|, so the
-                    // squares neither underflow nor overflow
-                    const double r = sqrt(__dadd_rn(__dmul_rn(z0, z0), __dmul_rn(pz, pz)));
-                    const double cc = z0 / r, ss = pz / r;
-                    if (fabs(__dmul_rn(__dmul_rn(t, cc), ss)) <= tau) {
-                        nr = true;
-                        const double c2 = __dmul_rn(cc, cc), s2 = __dmul_rn(ss, ss);
-                        nj = __dadd_rn(__dmul_rn(c2, pd), __dmul_rn(s2, d0));
-                        nd = __dadd_rn(__dmul_rn(s2, pd), __dmul_rn(c2, d0));
-                        nz = r;
-                        nm = m0 | pmk;
-                        nc = cc;
-                        ns = ss;
+                bool nr = rot;
+                double nd = fd, nz = fz, nc = c, ns = sn, nj = djn;
+                int nm = fm;
+                if (it == 0 || (pl >= 0 && pch)) {
+                    nr = false;
+                    nd = d0; nz = z0; nc = 0.0; ns = 0.0; nj = 0.0;
+                    nm = m0;
+                    if (cand && has_pred) {
+                        const double t = d0 - pd;
+                        const bool maybe = !(fabs(t) * fabs(z0) * fabs(pz) >
+                                             tau * (z0 * z0 + pz * pz) * (1.0 + 1e-12));
+                        if (maybe) {
+                            // survivors' weights: rho |z| > tau >= 8 eps rho max|z|, so
+                            // the squares neither underflow nor overflow
+                            const double r = sqrt(__dadd_rn(__dmul_rn(z0, z0), __dmul_rn(pz, pz)));
+                            const double cc = z0 / r, ss = pz / r;
+                            if (fabs(__dmul_rn(__dmul_rn(t, cc), ss)) <= tau) {
+                                nr = true;
+                                const double c2 = __dmul_rn(cc, cc), s2 = __dmul_rn(ss, ss);
+                                nj = __dadd_rn(__dmul_rn(c2, pd), __dmul_rn(s2, d0));
+                                nd = __dadd_rn(__dmul_rn(s2, pd), __dmul_rn(c2, d0));
+                                nz = r;
+                                nm = m0 | pmk;
+                                nc = cc;
+                                ns = ss;
+                            }
+                        }
                     }
                 }
                 const bool changed = nr != rot || nd != fd || nz != fz || nm != fm;
                 rot = nr; fd = nd; fz = nz; fm = nm; c = nc; sn = ns; djn = nj;
+                lch = changed;
                 if (!__any_sync(FULL, changed)) break;
             }
             if (type1) { ws.zsort[g0 + i] = 0.0; ws.keep[g0 + i] = 0; }

@@ -103,25 +103,94 @@ __global__ void __launch_bounds__(HSS_NT) k_gemm_grouped(const GemmDesc* G, int 
     }
 }
 
+// Small problems (the HSS construction's products: sides of one or two ranks,
+// a few tens to a hundred and some): 16 x 16 output tiles, one output per
+// thread, k in chunks of 32 through shared memory.  The FP64 pipe (2 lanes per
+// clock per SM) bounds each CTA, so the 64 x 64 tiles above, padded to the
+// tile and few in number, left most SMs idle while each busy one worked for
+// ~0.1 ms; small tiles spread the same work over the whole GPU and pad less.
+#define GT_T 16
+#define GT_K 32
+__global__ void __launch_bounds__(GT_T * GT_T) k_gemm_small(const GemmDesc* G, int ng)
+{
+    __shared__ double As[GT_K][GT_T + 1];
+    __shared__ double Bs[GT_K][GT_T + 1];
+    const int bid = blockIdx.x;
+    int lo = 0, hi = ng - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (G[mid].tile0 <= bid) lo = mid; else hi = mid - 1;
+    }
+    const GemmDesc g = G[lo];
+    const int local = bid - g.tile0;
+    const int row0 = (local % g.tiles_m) * GT_T, col0 = (local / g.tiles_m) * GT_T;
+    if (row0 >= g.M || col0 >= g.N) return;
+    const int tx = threadIdx.x & (GT_T - 1), ty = threadIdx.x / GT_T;
+    double acc = 0.0;
+    for (int k0 = 0; k0 < g.Kd; k0 += GT_K) {
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            const int idx = threadIdx.x + GT_T * GT_T * q;   // 512 entries per operand
+            int r, kk;
+            if (!g.transA) { r = idx & (GT_T - 1); kk = idx / GT_T; } else { kk = idx & (GT_K - 1); r = idx / GT_K; }
+            const int i = row0 + r, k = k0 + kk;
+            double va = 0.0;
+            if (i < g.M && k < g.Kd) {
+                if (!g.transA) {
+                    const int col = g.acol ? g.acol[k] : k;
+                    va = g.A[i + (int64_t)col * g.lda];
+                } else {
+                    va = g.A[k + (int64_t)i * g.lda];
+                }
+            }
+            As[kk][r] = va;
+            int c, kb;
+            if (!g.transB) { kb = idx & (GT_K - 1); c = idx / GT_K; } else { c = idx & (GT_T - 1); kb = idx / GT_T; }
+            const int j = col0 + c, kg = k0 + kb;
+            double vb = 0.0;
+            if (j < g.N && kg < g.Kd)
+                vb = g.transB ? g.B[j + (int64_t)kg * g.ldb] : g.B[kg + (int64_t)j * g.ldb];
+            Bs[kb][c] = vb;
+        }
+        __syncthreads();
+        const int kn = min(GT_K, g.Kd - k0);
+#pragma unroll 8
+        for (int kk = 0; kk < kn; kk++) acc = fma(As[kk][tx], Bs[kk][ty], acc);
+        __syncthreads();
+    }
+    const int i = row0 + tx, j = col0 + ty;
+    if (i < g.M && j < g.N) {
+        double* out = g.C + (int64_t)(g.ccol ? g.ccol[j] : j) * g.ldc;
+        out[i] = g.beta != 0.0 ? g.alpha * acc + g.beta * out[i] : g.alpha * acc;
+    }
+}
+
 double hss_launch_gemm(const std::vector<GemmDesc>& gin, GemmDesc* dev, cudaStream_t st)
 {
+    // every problem small: 16 x 16 tiles; else the 64 x 64 tiles
+    bool small = true;
+    for (const GemmDesc& d : gin)
+        if (d.M > 0 && d.N > 0 && (d.M > 256 || d.N > 256)) small = false;
+    const int T = small ? GT_T : 64;
     std::vector<GemmDesc> g;
     g.reserve(gin.size());
     int tiles = 0;
     double flops = 0.0;
     for (GemmDesc d : gin) {
         if (d.M <= 0 || d.N <= 0) continue;
-        d.tiles_m = td_cdiv(d.M, 64);
+        d.tiles_m = td_cdiv(d.M, T);
         d.tile0 = tiles;
-        tiles += d.tiles_m * td_cdiv(d.N, 64);
+        tiles += d.tiles_m * td_cdiv(d.N, T);
         flops += 2.0 * d.M * d.N * d.Kd;
         g.push_back(d);
     }
     if (g.empty()) return 0.0;
     cudaMemcpyAsync(dev, g.data(), g.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice, st);
     td_prof_begin(st);
-    k_gemm_grouped<<<tiles, HSS_NT, 0, st>>>(dev, (int)g.size());
-    td_prof_end(st, "k_gemm_grouped");
+    if (small) k_gemm_small<<<tiles, GT_T * GT_T, 0, st>>>(dev, (int)g.size());
+    else k_gemm_grouped<<<tiles, HSS_NT, 0, st>>>(dev, (int)g.size());
+    td_prof_end(st, small ? "k_gemm_small" : "k_gemm_grouped");
+    if (small) td_ctx().small_gemm_flops += flops;
     return flops;
 }
 

@@ -473,6 +473,7 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     const long long launches0 = cx.launches;
     const double split_flops0 = cx.split_tensor_flops;
     const double slice_bytes0 = cx.split_slice_bytes, exp_bytes0 = cx.split_exp_bytes;
+    const double small_flops0 = cx.small_gemm_flops;
     TdProf& prof = cx.prof;
     // per-kernel events only for this solve (see TDEIG_FLAG_PROFILE)
     struct ProfOff {
@@ -886,7 +887,7 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     {
         // per-kernel device time of a profiled solve: "after" event minus "before"
         std::string kj;
-        char kb[200];
+        char kb[256];
         if (prof.on) {
             std::vector<std::pair<std::string, std::pair<double, int>>> agg;
             for (size_t i = 1; i < prof.n; i++) {
@@ -920,9 +921,11 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
             }
             if (!lj.empty()) kj += ",\"launch_shapes\":[" + lj + "]";
         }
-        snprintf(kb, sizeof(kb), ",\"split_tensor_flops\":%.6e,\"split_slice_bytes\":%.6e,\"split_exp_bytes\":%.6e",
+        snprintf(kb, sizeof(kb),
+                 ",\"split_tensor_flops\":%.6e,\"split_slice_bytes\":%.6e,\"split_exp_bytes\":%.6e,"
+                 "\"small_gemm_flops\":%.6e",
                  cx.split_tensor_flops - split_flops0, cx.split_slice_bytes - slice_bytes0,
-                 cx.split_exp_bytes - exp_bytes0);
+                 cx.split_exp_bytes - exp_bytes0, cx.small_gemm_flops - small_flops0);
         kj += kb;
         h->stats.pop_back();
         h->stats += kj + "}";

@@ -494,7 +494,7 @@ def run_batched(args, torch, dist, world, rank, local, dev, stream, solver, flus
     out = {"metric": "batched eigendecomposition time, 4096 uneven tridiagonals", "value": v,
            "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "vs_baseline": None, "dtype": DTYPES[args.prec], "data": "synthetic",
            "config": {"workload": workload_name(args), "members": len(sizes),
                       "rows": int(sum(sizes)), "q_entries": int(sum(n * n for n in sizes)),
                       "graph": bool(args.graph)},

@@ -135,8 +135,9 @@ void td_launch_merge_level(const MergeDesc* M, int nmerge, int nmax, int rows, i
 int td_binary_version(int* out);
 // k_prep alone (eq. T3, sort, deflation, compaction), for the deflation stage entry point.
 void td_launch_prep(const MergeDesc* M, int nmerge, const LevelWS& ws, cudaStream_t st);
-void td_launch_secular(const MergeDesc* M, int nmerge, int rows, const LevelWS& ws, int* status,
-                       cudaStream_t st);
+// nmax: the largest merge size of the launch (bounds every K; picks the form)
+void td_launch_secular(const MergeDesc* M, int nmerge, int rows, int nmax, const LevelWS& ws,
+                       int* status, cudaStream_t st);
 void td_launch_lowner_cauchy(const MergeDesc* M, int nmerge, int rows, int kmax, const LevelWS& ws,
                              int write_qhat, cudaStream_t st);
 // k_cauchy alone (v and, with write_qhat, the Cauchy-like matrix) from uhat.

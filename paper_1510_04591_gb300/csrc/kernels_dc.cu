@@ -526,69 +526,76 @@ __global__ void __launch_bounds__(PREP_NT) k_prep(const MergeDesc* M, LevelWS ws
     }
     __syncthreads();
 
-    // Deflation sweep by warp 0, 32 entries per batch.  The sweep's only carried
-    // state is the last survivor (index, d, z, support mask): entry i either
-    // deflates by type 1 (independent of the state), or is tested against the
-    // state and becomes the new survivor (after a rotation when the test holds).
-    // Each lane decides its entry against its predecessor's current final state
-    // and the batch repeats until no decision changes: since every decision
-    // depends only on the predecessor's, round k settles the first k candidates,
-    // so the fixpoint (reached in at most 32 rounds, typically 1-2) is exactly
-    // the sequential sweep, with the same arithmetic per decision.
-    if (threadIdx.x < 32) {
+    // Deflation sweep by the whole CTA, PREP_NT entries per batch.  The sweep's
+    // only carried state is the last survivor (index, d, z, support mask): entry
+    // i either deflates by type 1 (independent of the state), or is tested
+    // against the state and becomes the new survivor (after a rotation when the
+    // test holds).  Each thread decides its entry against its predecessor's
+    // current final state (exchanged through shared memory) and the batch
+    // repeats until no decision changes: since every decision depends only on
+    // the predecessor's, round k settles the first k candidates, so the fixpoint
+    // (reached in at most PREP_NT + 1 rounds, typically 2) is exactly the
+    // sequential sweep, with the same arithmetic per decision.  A warp alone
+    // (32 entries per batch) used one of the SM's four FP64 units and spent most
+    // of a batch in latency.
+    // A thread recomputes only in the first round and after its predecessor's
+    // state changed (the decision is a function of that state alone).  A pair is
+    // sent to the exact test (the square root and divides, which cost most of a
+    // round on the 1/64-rate FP64 pipe) only when a cheap bound cannot exclude
+    // the rotation: with S = z_i^2 + z_j^2 the exact |t c s| is |t z_i z_j| / S,
+    // every operation of the test is rounded once, so the computed |t c s| is at
+    // least (1 - 9 eps) of it; the bound |t z_i z_j| > tau S (1 + 1e-12), itself
+    // computed with a few roundings, therefore implies no rotation.  Decisions
+    // are those of the exact test alone.  States are compared as bit patterns
+    // (an FP64 compare issues on the FP64 pipe).
+    {
+        __shared__ double s_fd[2][PREP_NT], s_fz[2][PREP_NT];
+        __shared__ int s_fm[2][PREP_NT];
+        __shared__ int s_ch[2][PREP_NT];
+        __shared__ int s_lastc[PREP_NT / 32], s_rotw[PREP_NT / 32];
+        __shared__ int s_j, s_mj;
+        __shared__ double s_dj, s_zj;
         const unsigned FULL = 0xffffffffu;
-        const int lane = threadIdx.x;
+        const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
         const unsigned below = (1u << lane) - 1u;
         const double tau = s_tau;
-        int j = -1, nrot = 0, mj = 0;
-        double dj = 0.0, zj = 0.0;
-        // the next batch's entries are loaded while this one is decided (the
-        // sweep writes only entries at or below the current batch)
-        double nd0 = lane < n ? ws.dsort[g0 + lane] : 0.0;
-        double nz0 = lane < n ? ws.zsort[g0 + lane] : 0.0;
-        int ns0 = lane < n ? ws.src[g0 + lane] : 0;
-        for (int base = 0; base < n; base += 32) {
-            const int i = base + lane;
+        if (tid == 0) { s_j = -1; s_mj = 0; s_dj = 0.0; s_zj = 0.0; }
+        int nrot = 0;
+        __syncthreads();
+        for (int base = 0; base < n; base += PREP_NT) {
+            const int i = base + tid;
             const bool valid = i < n;
-            const double d0 = valid ? nd0 : 0.0;
-            const double z0 = valid ? nz0 : 0.0;
-            const int m0 = valid ? ((ns0 < n1) ? 1 : 2) : 0;
-            if (i + 32 < n) {
-                nd0 = ws.dsort[g0 + i + 32];
-                nz0 = ws.zsort[g0 + i + 32];
-                ns0 = ws.src[g0 + i + 32];
-            }
+            const double d0 = valid ? ws.dsort[g0 + i] : 0.0;
+            const double z0 = valid ? ws.zsort[g0 + i] : 0.0;
+            const int m0 = valid ? ((ws.src[g0 + i] < n1) ? 1 : 2) : 0;
             const bool type1 = valid && (rho * fabs(z0) <= tau);
             const bool cand = valid && !type1;
             const unsigned cmask = __ballot_sync(FULL, cand);
-            const unsigned pm = cmask & below;
-            const int pl = pm ? 31 - __clz(pm) : -1;   // predecessor lane; -1: carried survivor
-            const bool has_pred = pl >= 0 || j >= 0;
+            if (lane == 0) s_lastc[w] = cmask ? w * 32 + 31 - __clz(cmask) : -1;
+            const int j = s_j, mj = s_mj;      // carried survivor
+            const double dj = s_dj, zj = s_zj;
             double fd = d0, fz = z0, c = 0.0, sn = 0.0, djn = 0.0;
             int fm = m0;
             bool rot = false;
-            // A lane recomputes only in the first round and after its predecessor's
-            // state changed (the decision is a function of that state alone).  A
-            // pair is sent to the exact test (the square root and divides, which
-            // cost most of a round on the 1/64-rate FP64 pipe) only when a cheap
-            // bound cannot exclude the rotation: with S = z_i^2 + z_j^2 the exact
-            // |t c s| is |t z_i z_j| / S, every operation of the test is rounded
-            // once, so the computed |t c s| is at least (1 - 9 eps) of it; the
-            // bound |t z_i z_j| > tau S (1 + 1e-12), itself computed with a few
-            // roundings, therefore implies no rotation.  Decisions are those of
-            // the exact test alone.
-            bool lch = true;   // this lane's state changed in the previous round
-            for (int it = 0; it < 33; it++) {
-                const int src = pl < 0 ? 0 : pl;
-                double pd = __shfl_sync(FULL, fd, src);
-                double pz = __shfl_sync(FULL, fz, src);
-                int pmk = __shfl_sync(FULL, fm, src);
-                const bool pch = __shfl_sync(FULL, (int)lch, src) != 0;
-                if (pl < 0) { pd = dj; pz = zj; pmk = mj; }
+            s_fd[0][tid] = fd; s_fz[0][tid] = fz; s_fm[0][tid] = fm; s_ch[0][tid] = 1;
+            __syncthreads();
+            // predecessor: the last candidate before this entry in the batch (-1:
+            // the carried survivor)
+            const unsigned pm = cmask & below;
+            int pl = pm ? w * 32 + 31 - __clz(pm) : -1;
+            for (int v = w - 1; pl < 0 && v >= 0; v--) pl = s_lastc[v];
+            const bool has_pred = pl >= 0 || j >= 0;
+            int last = -1;   // the batch's last candidate
+            for (int v = PREP_NT / 32 - 1; last < 0 && v >= 0; v--) last = s_lastc[v];
+            for (int it = 0; it <= PREP_NT; it++) {
+                const int b = it & 1;
+                double pd = dj, pz = zj;
+                int pmk = mj, pch = 0;
+                if (pl >= 0) { pd = s_fd[b][pl]; pz = s_fz[b][pl]; pmk = s_fm[b][pl]; pch = s_ch[b][pl]; }
                 bool nr = rot;
                 double nd = fd, nz = fz, nc = c, ns = sn, nj = djn;
                 int nm = fm;
-                if (it == 0 || (pl >= 0 && pch)) {
+                if (it == 0 || pch) {
                     nr = false;
                     nd = d0; nz = z0; nc = 0.0; ns = 0.0; nj = 0.0;
                     nm = m0;
@@ -614,19 +621,30 @@ __global__ void __launch_bounds__(PREP_NT) k_prep(const MergeDesc* M, LevelWS ws
                         }
                     }
                 }
-                const bool changed = nr != rot || nd != fd || nz != fz || nm != fm;
+                const bool changed = nr != rot || nm != fm ||
+                                     __double_as_longlong(nd) != __double_as_longlong(fd) ||
+                                     __double_as_longlong(nz) != __double_as_longlong(fz);
                 rot = nr; fd = nd; fz = nz; fm = nm; c = nc; sn = ns; djn = nj;
-                lch = changed;
-                if (!__any_sync(FULL, changed)) break;
+                s_fd[b ^ 1][tid] = fd; s_fz[b ^ 1][tid] = fz; s_fm[b ^ 1][tid] = fm;
+                s_ch[b ^ 1][tid] = changed;
+                if (!__syncthreads_or(changed)) break;
             }
             if (type1) { ws.zsort[g0 + i] = 0.0; ws.keep[g0 + i] = 0; }
             if (cand) { ws.keep[g0 + i] = fm; ws.dsort[g0 + i] = fd; ws.zsort[g0 + i] = fz; }
-            __syncwarp();
             const unsigned rmask = __ballot_sync(FULL, rot);
+            if (lane == 0) s_rotw[w] = __popc(rmask);
+            // the predecessor's own entry is written above (by another warp,
+            // possibly): its deflation below must come after
+            __syncthreads();
+            int rbefore = 0, rtotal = 0;
+            for (int v = 0; v < PREP_NT / 32; v++) {
+                rbefore += (v < w) ? s_rotw[v] : 0;
+                rtotal += s_rotw[v];
+            }
             if (rot) {
                 // the predecessor deflates: rotated d, zero z; rotations keep sweep order
                 const int pj = pl >= 0 ? base + pl : j;
-                const int slot = nrot + __popc(rmask & below);
+                const int slot = nrot + rbefore + __popc(rmask & below);
                 ws.dsort[g0 + pj] = djn;
                 ws.zsort[g0 + pj] = 0.0;
                 ws.keep[g0 + pj] = 0;
@@ -635,17 +653,11 @@ __global__ void __launch_bounds__(PREP_NT) k_prep(const MergeDesc* M, LevelWS ws
                 ws.rot_c[g0 + slot] = c;
                 ws.rot_s[g0 + slot] = sn;
             }
-            nrot += __popc(rmask);
-            if (cmask) {
-                const int L = 31 - __clz(cmask);
-                j = base + L;
-                dj = __shfl_sync(FULL, fd, L);
-                zj = __shfl_sync(FULL, fz, L);
-                mj = __shfl_sync(FULL, fm, L);
-            }
-            __syncwarp();
+            nrot += rtotal;
+            if (tid == last) { s_j = i; s_dj = fd; s_zj = fz; s_mj = fm; }
+            __syncthreads();
         }
-        if (lane == 0) ws.nrot[blockIdx.x] = nrot;
+        if (tid == 0) ws.nrot[blockIdx.x] = nrot;
     }
     __syncthreads();
 
@@ -960,7 +972,10 @@ __device__ __forceinline__ void df_warp_sum(float& h, float& l)
 // The model step of the iteration (Bunch, Nielsen & Sorensen's two-pole
 // rational model of psi (poles <= i) and phi (poles > i) fitted in value and
 // slope at tau; for the last root one pole): returns tau + step when the model
-// root lies inside the bracket (lo, hi), else the bracket's midpoint.
+// root lies inside the bracket (lo, hi), else the bracket's midpoint.  Its
+// divide is a reciprocal by td_recip (a few ulp): the step only proposes the
+// next point, and a step accepted without another evaluation is below 1e-9 of
+// tau, so its last-place error is far below tau's.
 __device__ __forceinline__ double secular_step(double f, double dpsi, double dphi, double tau,
                                                double lo, double hi, double deli, double deli1,
                                                bool last, double* step_out, bool* model_out)
@@ -976,10 +991,10 @@ __device__ __forceinline__ double secular_step(double f, double dpsi, double dph
         double disc = beta * beta - 4.0 * E * c0;
         if (disc < 0.0) disc = 0.0;
         const double den = beta + (beta >= 0.0 ? sqrt(disc) : -sqrt(disc));
-        if (den == 0.0) ok = false; else step = 2.0 * c0 / den;
+        if (den == 0.0) ok = false; else step = 2.0 * c0 * td_recip(den);
     } else {
         const double E = f - dpsi * a1;
-        if (E == 0.0) ok = false; else step = a1 * f / E;
+        if (E == 0.0) ok = false; else step = a1 * f * td_recip(E);
     }
     const bool model = ok && tau + step > lo && tau + step < hi;
     *step_out = step;
@@ -989,8 +1004,9 @@ __device__ __forceinline__ double secular_step(double f, double dpsi, double dph
 
 // Merges with K >= this many poles run the double-float iterations before the
 // FP64 ones: below it the lane-0 scalar work of an iteration (FP64 issue costs a
-// whole warp slot whatever the active lanes) is not small next to an FP64 sum.
-#define TD_SECULAR_DF_MINK 1024
+// whole warp slot whatever the active lanes, ~40 slots for the model step) is
+// not small next to an FP64 sum (14 slots per 32 terms).
+#define TD_SECULAR_DF_MINK 256
 #define TD_SECULAR_DF_MAXIT 16
 
 // One root of the secular equation by one warp (Theorem 1; Remark 1 for gamma
@@ -1059,7 +1075,8 @@ __device__ void secular_root_warp(const double* __restrict__ d, const double* __
         // root in the bracket (the midpoint is the fallback).
         const double mid = 0.5 * (d[i + 1] - d[i]);   // midpoint offset from d_i
         const double wi = w[i], wi1 = w[i + 1];
-        const double a = fmid - wi / (-mid) - wi1 / (mid);   // 1 + c
+        const double rm = td_recip(mid);
+        const double a = fmid + wi * rm - wi1 * rm;   // 1 + c
         const double b = a * (deli + deli1) + wi + wi1;
         const double c0 = a * deli * deli1 + wi * deli1 + wi1 * deli;
         const double disc = b * b - 4.0 * a * c0;
@@ -1068,11 +1085,11 @@ __device__ void secular_root_warp(const double* __restrict__ d, const double* __
             double t0 = 0.5 * (lo + hi);
             bool got = false;
             if (qq != 0.0) {
-                const double r1 = c0 / qq;
+                const double r1 = c0 * td_recip(qq);
                 if (r1 > lo && r1 < hi) { t0 = r1; got = true; }
             }
             if (!got && a != 0.0) {
-                const double r2 = qq / a;
+                const double r2 = qq * td_recip(a);
                 if (r2 > lo && r2 < hi) t0 = r2;
             }
             tau = t0;
@@ -1190,6 +1207,294 @@ __device__ void secular_root_warp(const double* __restrict__ d, const double* __
     *iters = it;
 }
 
+// ---------------------------------------------------------------------------
+// Small merges (K <= 256): several roots per warp, one aligned group of G
+// lanes per root (G = 4, 8 or 16).  The iteration, stopping tests and arithmetic
+// per term are those of secular_root_warp; the sums run over the group and are
+// reduced within it.  What a warp of one root spent on its scalar work (the
+// model step and tests on lane 0, ~40 FP64 issue slots per iteration, each
+// costing a whole warp slot on this part whatever the active lanes) and on
+// five levels of FP64 shuffle sums is then shared by 32 / G roots: on the
+// lowest levels of a batch (K of 30 to 200) that work, not the K-term sums,
+// set the time.  Groups of one warp may belong to different merges and need
+// different iteration counts, so every loop that holds a shuffle runs until
+// no group of the warp needs it (finished groups idle through it).
+// ---------------------------------------------------------------------------
+template <int G>
+__device__ __forceinline__ float grp_sum_f(float v)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <int G>
+__device__ __forceinline__ double grp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <int G>
+__device__ __forceinline__ void grp_df_sum(float& h, float& l)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+        float t, e;
+        df_two_sum(h, oh, t, e);
+        h = t;
+        l = __fadd_rn(l, __fadd_rn(e, ol));
+    }
+}
+
+// One root per group of G lanes (gl: lane within the group).  act: the group
+// has a root (i < K); all lanes of the warp must call together.
+template <int G>
+__device__ void secular_root_group(const double* __restrict__ d, const double* __restrict__ w,
+                                   int K, int i, bool act, int gl, double* lam, double* gam,
+                                   double* mu, int* iters, int* df_iters,
+                                   const float* __restrict__ dh, const float* __restrict__ dl,
+                                   const float* __restrict__ wf, const float* __restrict__ wl)
+{
+    const unsigned FULL = 0xffffffffu;
+    *df_iters = 0;
+    *iters = 0;
+    const bool run = act && K > 1;   // K == 1: closed form, no sums
+    const bool last = run && i == K - 1;
+    int org = i;
+    double lo = 0.0, hi = 0.0, fmid = 0.0;
+    {
+        // origin from the FP32 midpoint value (not the last root)
+        const bool mid = run && !last;
+        double gap = 0.0;
+        float hf = 0.0f, ohi = 0.0f, olo = 0.0f;
+        if (mid) {
+            gap = d[i + 1] - d[i];
+            hf = __double2float_rn(0.5 * gap);
+            ohi = dh[i];
+            olo = dl[i];
+        }
+        float f = 0.0f;
+        const int ke = mid ? K : 0;
+        for (int j = gl; j < ke; j += G) {
+            const float del = (dh[j] - ohi) + (dl[j] - olo);   // d_j - d_i
+            f = fmaf(wf[j], td_rcp_f32(del - hf), f);
+        }
+        f = grp_sum_f<G>(f);
+        if (mid) {
+            fmid = 1.0 + (double)f;
+            if (fmid >= 0.0) { org = i; lo = 0.0; hi = gap; }
+            else { org = i + 1; lo = -gap; hi = 0.0; }
+        }
+    }
+    if (__any_sync(FULL, last)) {
+        double zz = 0.0;
+        const int ke = last ? K : 0;
+        for (int j = gl; j < ke; j += G) zz += w[j];
+        zz = grp_sum_d<G>(zz);
+        if (last) { org = i; lo = 0.0; hi = zz; }
+    }
+    const double dorg = run ? d[org] : 0.0;
+    const double deli = run ? d[i] - dorg : 0.0;
+    const double deli1 = (run && !last) ? d[i + 1] - dorg : 0.0;
+    double tau = 0.5 * (lo + hi);
+    if (run && !last && gl == 0) {
+        // start: the root in the bracket of the two-pole model with the other
+        // terms frozen at their midpoint value (as secular_root_warp)
+        const double mid = 0.5 * (d[i + 1] - d[i]);
+        const double wi = w[i], wi1 = w[i + 1];
+        const double rm = td_recip(mid);
+        const double a = fmid + wi * rm - wi1 * rm;   // 1 + c
+        const double b = a * (deli + deli1) + wi + wi1;
+        const double c0 = a * deli * deli1 + wi * deli1 + wi1 * deli;
+        const double disc = b * b - 4.0 * a * c0;
+        if (disc >= 0.0) {
+            const double qq = 0.5 * (b + (b >= 0.0 ? sqrt(disc) : -sqrt(disc)));
+            double t0 = 0.5 * (lo + hi);
+            bool got = false;
+            if (qq != 0.0) {
+                const double r1 = c0 * td_recip(qq);
+                if (r1 > lo && r1 < hi) { t0 = r1; got = true; }
+            }
+            if (!got && a != 0.0) {
+                const double r2 = qq * td_recip(a);
+                if (r2 > lo && r2 < hi) t0 = r2;
+            }
+            tau = t0;
+        }
+    }
+    tau = __shfl_sync(FULL, tau, 0, G);
+
+    // ---- double-float iterations (as secular_root_warp) ------------------
+    const double lo0 = lo, hi0 = hi;
+    bool dfrun = run && K >= TD_SECULAR_DF_MINK;
+    if (__any_sync(FULL, dfrun)) {
+        float oh = 0.0f, ol = 0.0f;
+        int jn = -1;
+        double djn = 0.0;
+        if (dfrun) {
+            oh = dh[org];
+            ol = dl[org];
+            jn = last ? -1 : (org == i ? i + 1 : i);
+            djn = last ? 0.0 : d[jn] - dorg;
+        }
+        int itdf = 0;
+        for (int t = 0; t < TD_SECULAR_DF_MAXIT; t++) {
+            if (!__any_sync(FULL, dfrun)) break;
+            float th = 0.0f, tl = 0.0f, xh = 0.0f, xl = 0.0f;
+            if (dfrun) {
+                th = __double2float_rn(tau);
+                tl = __double2float_rn(tau - (double)th);
+                const double x = djn - tau;
+                xh = __double2float_rn(x);
+                xl = __double2float_rn(x - (double)xh);
+            }
+            float ph = 0.0f, pl = 0.0f, pd = 0.0f, fh = 0.0f, fl = 0.0f, fd = 0.0f;
+            const int ie = dfrun ? i : -1, ke = dfrun ? K : 0;
+            for (int j = gl; j <= ie; j += G)
+                df_term(dh[j], dl[j], oh, ol, th, tl, wf[j], wl[j], j == jn, xh, xl, ph, pl, pd);
+            for (int j = i + 1 + gl; j < ke; j += G)
+                df_term(dh[j], dl[j], oh, ol, th, tl, wf[j], wl[j], j == jn, xh, xl, fh, fl, fd);
+            grp_df_sum<G>(ph, pl);
+            grp_df_sum<G>(fh, fl);
+            pd = grp_sum_f<G>(pd);
+            fd = grp_sum_f<G>(fd);
+            int stop = 0;
+            double nt = tau;
+            if (dfrun && gl == 0) {
+                const double psi = (double)ph + (double)pl, phi = (double)fh + (double)fl;
+                const double dpsi = pd, dphi = fd;
+                const double f = 1.0 + psi + phi;
+                const double noise = 9.094947017729282e-13 *   // 2^-40
+                                     (1.0 + fabs(psi) + fabs(phi) + fabs(tau) * (dpsi + dphi));
+                if (fabs(f) <= noise) {
+                    stop = 1;
+                } else {
+                    if (f > 0.0) hi = tau; else lo = tau;
+                    double step;
+                    bool model;
+                    nt = secular_step(f, dpsi, dphi, tau, lo, hi, deli, deli1, last, &step, &model);
+                    if (hi - lo <= 4.0 * TD_EPS * fmax(fabs(lo), fabs(hi)) ||
+                        (model && fabs(step) <= 1e-12 * fabs(tau)))
+                        stop = 1;
+                }
+            }
+            stop = __shfl_sync(FULL, stop, 0, G);
+            nt = __shfl_sync(FULL, nt, 0, G);
+            if (dfrun) {
+                tau = nt;
+                itdf++;
+                if (stop) dfrun = false;
+            }
+        }
+        *df_iters = itdf;
+    }
+    lo = lo0;
+    hi = hi0;
+
+    // ---- FP64 iterations (as secular_root_warp) ---------------------------
+    bool frun = run;
+    int it = 0;
+    for (int t = 1; t <= TD_SECULAR_MAXIT; t++) {
+        if (!__any_sync(FULL, frun)) break;
+        double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
+        const int ie = frun ? i : -1, ke = frun ? K : 0;
+        for (int j = gl; j <= ie; j += G) {
+            double q = td_recip((d[j] - dorg) - tau);
+            double tt = w[j] * q;
+            s1 += tt; s2 += tt * q;
+        }
+        for (int j = i + 1 + gl; j < ke; j += G) {
+            double q = td_recip((d[j] - dorg) - tau);
+            double tt = w[j] * q;
+            s3 += tt; s4 += tt * q;
+        }
+        const double psi = grp_sum_d<G>(s1), dpsi = grp_sum_d<G>(s2);
+        const double phi = grp_sum_d<G>(s3), dphi = grp_sum_d<G>(s4);
+        int stop = 0;
+        double nt = tau;
+        if (frun && gl == 0) {
+            const double f = 1.0 + psi + phi;
+            const double err = 8.0 * TD_EPS * (1.0 + fabs(psi) + fabs(phi) + fabs(tau) * (dpsi + dphi));
+            if (fabs(f) <= err) {
+                stop = 1;
+            } else {
+                if (f > 0.0) hi = tau; else lo = tau;
+                if (hi - lo <= 4.0 * TD_EPS * fmax(fabs(lo), fabs(hi))) {
+                    stop = 1;
+                } else {
+                    double step;
+                    bool model;
+                    nt = secular_step(f, dpsi, dphi, tau, lo, hi, deli, deli1, last, &step, &model);
+                    if (nt == tau) stop = 1;
+                    else if (model && fabs(step) <= 1e-9 * fabs(tau)) stop = 2;
+                }
+            }
+        }
+        stop = __shfl_sync(FULL, stop, 0, G);
+        nt = __shfl_sync(FULL, nt, 0, G);
+        if (frun) {
+            it = t;
+            if (stop == 1) frun = false;
+            else {
+                tau = nt;
+                if (stop == 2) frun = false;
+            }
+        }
+    }
+    if (frun) it = TD_SECULAR_MAXIT + 1;   // not converged
+    if (run) {
+        *lam = dorg + tau;
+        if (last) { *gam = tau; *mu = 0.0; }
+        else if (org == i) { *gam = tau; *mu = (d[i + 1] - d[i]) - tau; }
+        else { *mu = -tau; *gam = (d[i + 1] - d[i]) + tau; }
+        *iters = it;
+    } else if (act) {
+        *lam = d[0] + w[0]; *gam = w[0]; *mu = 0.0; *iters = 0;
+    }
+}
+
+// Merges of at most this many poles take the grouped form (G = 4 up to 64, 8
+// up to 128, 16 up to 256).
+#define TD_SECULAR_GRP_MAXK 256
+
+template <int G>
+__global__ void k_secular_grp(const MergeDesc* M, int nmerge, int rows, LevelWS ws, int* status)
+{
+    const int tg = blockIdx.x * blockDim.x + threadIdx.x;
+    if (((tg & ~31) / G) >= rows) return;   // the warp's first root: whole warps leave
+    const int gl = threadIdx.x & (G - 1);
+    const int r = tg / G;
+    int g0 = 0, i = 0, K = 0;
+    bool act = false;
+    if (r < rows) {
+        const int m = td_find_merge(M, nmerge, r);
+        if (m >= 0) {
+            g0 = M[m].g0;
+            i = r - g0;
+            K = ws.K[m];
+            act = i < K;
+        }
+    }
+    if (!act) { g0 = 0; i = 0; K = 0; }
+    double lam = 0.0, gam = 0.0, mu = 0.0;
+    int it, itdf;
+    secular_root_group<G>(ws.dK + g0, ws.wK + g0, K, i, act, gl, &lam, &gam, &mu, &it, &itdf,
+                          ws.dhK + g0, ws.dlK + g0, ws.wfK + g0, ws.wlK + g0);
+    if (act && gl == 0) {
+        ws.lamK[g0 + i] = lam;
+        ws.gamK[g0 + i] = gam;
+        ws.muK[g0 + i] = mu;
+        if (it > TD_SECULAR_MAXIT) atomicOr(status, TD_STATUS_NOTCONV);
+        atomicAdd((unsigned long long*)(status + TD_STATUS_SECULAR_TERMS),
+                  (unsigned long long)(min(it, TD_SECULAR_MAXIT) + (i == K - 1 ? 1 : 0)) *
+                      (unsigned long long)K);
+        atomicAdd((unsigned long long*)(status + TD_STATUS_SECULAR_DFTERMS),
+                  (unsigned long long)itdf * (unsigned long long)K);
+    }
+}
+
 __global__ void k_secular(const MergeDesc* M, int nmerge, int rows, LevelWS ws, int* status)
 {
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1221,11 +1526,20 @@ __global__ void k_secular(const MergeDesc* M, int nmerge, int rows, LevelWS ws, 
     }
 }
 
-void td_launch_secular(const MergeDesc* M, int nmerge, int rows, const LevelWS& ws, int* status,
-                       cudaStream_t st)
+void td_launch_secular(const MergeDesc* M, int nmerge, int rows, int nmax, const LevelWS& ws,
+                       int* status, cudaStream_t st)
 {
     if (rows <= 0) return;
-    td_prof_begin(st); k_secular<<<td_cdiv(rows, 8), 256, 0, st>>>(M, nmerge, rows, ws, status); td_prof_end(st, "k_secular");
+    td_prof_begin(st);
+    if (nmax <= 64)
+        k_secular_grp<4><<<td_cdiv(rows, 64), 256, 0, st>>>(M, nmerge, rows, ws, status);
+    else if (nmax <= 128)
+        k_secular_grp<8><<<td_cdiv(rows, 32), 256, 0, st>>>(M, nmerge, rows, ws, status);
+    else if (nmax <= TD_SECULAR_GRP_MAXK)
+        k_secular_grp<16><<<td_cdiv(rows, 16), 256, 0, st>>>(M, nmerge, rows, ws, status);
+    else
+        k_secular<<<td_cdiv(rows, 8), 256, 0, st>>>(M, nmerge, rows, ws, status);
+    td_prof_end(st, "k_secular");
 }
 
 // ---------------------------------------------------------------------------
@@ -1713,6 +2027,30 @@ __global__ void k_secular_noalloc(const double* d, const double* w, const float*
     }
 }
 
+// The grouped form for K <= TD_SECULAR_GRP_MAXK, chosen as tdeig_secular
+// chooses it, so that the two stay bit-identical.
+template <int G>
+__global__ void k_secular_noalloc_grp(const double* d, const double* w, const float* wf,
+                                      const float* wl, const float* dh, const float* dl, int K,
+                                      int* status, double* lam, double* gam, double* mu)
+{
+    const int tg = blockIdx.x * blockDim.x + threadIdx.x;
+    if (((tg & ~31) / G) >= K) return;   // whole warps leave
+    const int gl = threadIdx.x & (G - 1);
+    const int i = tg / G;
+    const bool act = i < K;
+    double l = 0.0, g = 0.0, m = 0.0;
+    int it, itdf;
+    secular_root_group<G>(d, w, act ? K : 0, act ? i : 0, act, gl, &l, &g, &m, &it, &itdf, dh, dl,
+                          wf, wl);
+    if (act && gl == 0) {
+        lam[i] = l;
+        gam[i] = g;
+        mu[i] = m;
+        if (it > TD_SECULAR_MAXIT) atomicOr(status, TD_STATUS_NOTCONV);
+    }
+}
+
 // Device memory of the current device (host, managed or another device's
 // memory is rejected).
 static bool noalloc_on_device(const void* p, int dev)
@@ -1762,8 +2100,18 @@ extern "C" int tdeig_secular_noalloc(int64_t K, const double* d, const double* z
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int k = (int)K;
     k_noalloc_weights<<<td_cdiv(k, 256), 256, 0, st>>>(d, z, rho, k, w, wf, wl, dh, dl, status);
-    k_secular_noalloc<<<td_cdiv(k, 8), 256, 0, st>>>(d, w, wf, wl, dh, dl, k, status, lambda, gamma,
-                                                      mu);
+    if (k <= 64)
+        k_secular_noalloc_grp<4><<<td_cdiv(k, 64), 256, 0, st>>>(d, w, wf, wl, dh, dl, k, status,
+                                                                lambda, gamma, mu);
+    else if (k <= 128)
+        k_secular_noalloc_grp<8><<<td_cdiv(k, 32), 256, 0, st>>>(d, w, wf, wl, dh, dl, k, status,
+                                                                lambda, gamma, mu);
+    else if (k <= TD_SECULAR_GRP_MAXK)
+        k_secular_noalloc_grp<16><<<td_cdiv(k, 16), 256, 0, st>>>(d, w, wf, wl, dh, dl, k, status,
+                                                                 lambda, gamma, mu);
+    else
+        k_secular_noalloc<<<td_cdiv(k, 8), 256, 0, st>>>(d, w, wf, wl, dh, dl, k, status, lambda,
+                                                          gamma, mu);
     if (cudaGetLastError() != cudaSuccess) return TDEIG_ECUDA;
     int hs = 0;
     if (cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||

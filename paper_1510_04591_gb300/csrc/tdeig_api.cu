@@ -738,7 +738,7 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
         CU(cudaMemcpyAsync(gstat + 2 * L.desc_off, lws.kgrp, 2 * nm * sizeof(int),
                            cudaMemcpyDeviceToDevice, st));
         MARK("secular", lv);
-        td_launch_secular(Md, nm, L.rows, lws, status, st);
+        td_launch_secular(Md, nm, L.rows, L.nmax, lws, status, st);
         bool any_hss = false;
         std::vector<int> Kh, Gh;
         const bool hss_level = variant != TDEIG_MODE_DENSE && L.nmax > h->opt.hss_threshold;
@@ -1061,7 +1061,7 @@ extern "C" int tdeig_secular(tdeig_handle h, int64_t K, const double* d, const d
     cudaStream_t st = h->stream;
     if ((rc = copy_in(lws.dK, d, K, st)) || (rc = copy_in(lws.zK, z, K, st))) return rc;
     td_launch_stage_init(lws, (int)K, rho, st);
-    td_launch_secular(md, 1, (int)K, lws, status, st);
+    td_launch_secular(md, 1, (int)K, (int)K, lws, status, st);
     CU(cudaGetLastError());
     if ((rc = copy_out(lambda, lws.lamK, K, st)) || (rc = copy_out(gamma, lws.gamK, K, st)) ||
         (rc = copy_out(mu, lws.muK, K, st)))

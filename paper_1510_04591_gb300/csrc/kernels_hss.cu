@@ -263,6 +263,11 @@ static void launch_gather(const std::vector<GatherDesc>& G, GatherDesc* dev, cud
     td_prof_end(st, "k_gather_rows");
 }
 
+// Row stride of the ID's matrix in shared memory: the smallest ld >= m with
+// ld = 8 (mod 16), so that the update's four row phases of eight neighbouring
+// columns fall in distinct double-word banks (two wavefronts per warp).
+__host__ __device__ __forceinline__ int id_ld(int m) { return m + ((24 - (m & 15)) & 15); }
+
 // ---------------------------------------------------------------------------
 // Interpolative decomposition (Sec. 3): Householder QR with column pivoting of
 // Phi^T (s x m; its columns are the rows of Phi), stopped at the first k with
@@ -278,18 +283,20 @@ __global__ void __launch_bounds__(HSS_NT) k_id(const IdDesc* D, int nd, double t
     const IdDesc g = D[blockIdx.x];
     const int m = g.m, s = g.s;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    double* A = sm;                       // s x m
-    double* nrm = A + (size_t)s * m;      // m: squared norm of the rows below the current step
+    const int q4 = tid & 3;
+    const int ld = id_ld(m);              // row stride of A (see id_ld)
+    double* A = sm;                       // s x m, rows ld apart
+    double* nrm = A + (size_t)s * ld;     // m: squared norm of the rows below the current step
     double* ref = nrm + m;                // m: that norm when last computed exactly
     int* perm = (int*)(ref + m);          // m
     for (int t = tid; t < s * m; t += HSS_NT) {
         const int j = t % m, i = t / m;
-        A[i * m + j] = g.Phi[j + (int64_t)i * g.ldphi];
+        A[i * ld + j] = g.Phi[j + (int64_t)i * g.ldphi];
     }
     __syncthreads();
     for (int j = tid; j < m; j += HSS_NT) {
         double a = 0.0;
-        for (int i = 0; i < s; i++) a += A[i * m + j] * A[i * m + j];
+        for (int i = 0; i < s; i++) a += A[i * ld + j] * A[i * ld + j];
         nrm[j] = a;
         ref[j] = a;
         perm[j] = j;
@@ -337,7 +344,7 @@ __global__ void __launch_bounds__(HSS_NT) k_id(const IdDesc* D, int nd, double t
         }
         if (p != k) {
             for (int i = tid; i < s; i += HSS_NT) {
-                double t = A[i * m + k]; A[i * m + k] = A[i * m + p]; A[i * m + p] = t;
+                double t = A[i * ld + k]; A[i * ld + k] = A[i * ld + p]; A[i * ld + p] = t;
             }
             if (tid == 0) {
                 double t = nrm[k]; nrm[k] = nrm[p]; nrm[p] = t;
@@ -348,11 +355,11 @@ __global__ void __launch_bounds__(HSS_NT) k_id(const IdDesc* D, int nd, double t
         __syncthreads();
         if (wid == 0) {
             double a = 0.0;
-            for (int i = k + lane; i < s; i += 32) a += A[i * m + k] * A[i * m + k];
+            for (int i = k + lane; i < s; i += 32) a += A[i * ld + k] * A[i * ld + k];
             a = td_warp_sum(a);
             if (lane == 0) {
                 const double xn = sqrt(a);
-                const double x0 = A[k * m + k];
+                const double x0 = A[k * ld + k];
                 const double alpha = (x0 >= 0.0) ? -xn : xn;
                 s_stop = xn <= tol * r00;
                 s_par[0] = 1.0 / (alpha * (alpha - x0));   // beta
@@ -363,37 +370,86 @@ __global__ void __launch_bounds__(HSS_NT) k_id(const IdDesc* D, int nd, double t
         __syncthreads();
         if (s_stop) { rank = k; break; }
         const double beta = s_par[0], v0 = s_par[1];
-        for (int j = k + 1 + tid; j < m; j += HSS_NT) {
-            double dot = v0 * A[k * m + j];
-            for (int i = k + 1; i < s; i++) dot += A[i * m + k] * A[i * m + j];
-            const double f = beta * dot;
-            const double akj = A[k * m + j] - f * v0;
-            A[k * m + j] = akj;
-            for (int i = k + 1; i < s; i++) A[i * m + j] -= f * A[i * m + k];
-            double nn = nrm[j] - akj * akj;
-            if (!(nn > 1.4901161193847656e-8 * ref[j])) {   // sqrt(2^-52)
-                nn = 0.0;
-                for (int i = k + 1; i < s; i++) nn += A[i * m + j] * A[i * m + j];
-                ref[j] = nn;
+        // Four lanes per column (lane q of a group takes rows k+1+q, k+5+q, ...;
+        // the dot product's partial sums are combined by shuffles): one lane per
+        // column left the SM's FP64 units partly idle and each column's sum one
+        // long dependent chain.  Whole warps iterate together (shuffles).
+        for (int base = k + 1; base < m; base += HSS_NT / 4) {
+            const int j = base + (tid >> 2);
+            const bool act = j < m;
+            double dot = 0.0;
+            if (act) {
+                if (q4 == 0) dot = v0 * A[k * ld + j];
+                for (int i = k + 1 + q4; i < s; i += 4) dot = fma(A[i * ld + k], A[i * ld + j], dot);
             }
-            nrm[j] = nn;
+            dot += __shfl_xor_sync(0xffffffffu, dot, 1);
+            dot += __shfl_xor_sync(0xffffffffu, dot, 2);
+            double akj = 0.0;
+            if (act) {
+                const double f = beta * dot;
+                if (q4 == 0) {
+                    akj = A[k * ld + j] - f * v0;
+                    A[k * ld + j] = akj;
+                }
+                for (int i = k + 1 + q4; i < s; i += 4) A[i * ld + j] -= f * A[i * ld + k];
+            }
+            int rec = 0;
+            double nn = 0.0;
+            if (act && q4 == 0) {
+                nn = nrm[j] - akj * akj;
+                rec = !(nn > 1.4901161193847656e-8 * ref[j]);   // sqrt(2^-52)
+            }
+            rec = __shfl_sync(0xffffffffu, rec, lane & ~3);
+            if (__any_sync(0xffffffffu, rec)) {
+                // exact norm of the rows below k (each lane its own rows, updated above)
+                double a = 0.0;
+                if (act && rec)
+                    for (int i = k + 1 + q4; i < s; i += 4) a = fma(A[i * ld + j], A[i * ld + j], a);
+                a += __shfl_xor_sync(0xffffffffu, a, 1);
+                a += __shfl_xor_sync(0xffffffffu, a, 2);
+                if (rec) {
+                    nn = a;
+                    if (act && q4 == 0) ref[j] = a;
+                }
+            }
+            if (act && q4 == 0) nrm[j] = nn;
         }
         __syncthreads();
-        if (tid == 0) A[k * m + k] = s_par[2];   // column k is read by no one until the end
+        if (tid == 0) A[k * ld + k] = s_par[2];   // column k is read by no one until the end
     }
     __syncthreads();
-    // T = R11^{-1} R12 in place (columns rank..m-1), back substitution
-    for (int j = rank + tid; j < m; j += HSS_NT) {
-        for (int i = rank - 1; i >= 0; i--) {
-            double t = A[i * m + j];
-            for (int l = i + 1; l < rank; l++) t -= A[i * m + l] * A[l * m + j];
-            A[i * m + j] = t / A[i * m + i];
+    // T = R11^{-1} R12 in place (columns rank..m-1), back substitution by groups
+    // of four lanes per column (each lane a quarter of every row's sum, combined
+    // by shuffles), with the diagonal's reciprocals taken once: one lane per
+    // column left most of the SM's FP64 units idle and spent ~40 % of the work
+    // on divides
+    double* rdiag = nrm;   // the column norms are no longer needed
+    for (int i = tid; i < rank; i += HSS_NT) rdiag[i] = 1.0 / A[i * ld + i];
+    __syncthreads();
+    {
+        const int q = lane & 3;
+        const unsigned gmask = 0xFu << (lane & ~3);
+        const int ncol = m - rank;
+        // whole warps iterate together (the group shuffles need all four lanes)
+        for (int base = 0; base < ncol; base += HSS_NT / 4) {
+            const int jj = base + (tid >> 2);
+            const bool act = jj < ncol;
+            const int j = rank + (act ? jj : 0);
+            for (int i = rank - 1; i >= 0; i--) {
+                double t = 0.0;
+                if (act)
+                    for (int l = i + 1 + q; l < rank; l += 4) t = fma(A[i * ld + l], A[l * ld + j], t);
+                t += __shfl_xor_sync(gmask, t, 1);
+                t += __shfl_xor_sync(gmask, t, 2);
+                if (act && q == 0) A[i * ld + j] = (A[i * ld + j] - t) * rdiag[i];
+                __syncwarp();
+            }
         }
     }
     __syncthreads();
     for (int t = tid; t < m * rank; t += HSS_NT) {
         const int row = t % m, c = t / m;   // row = position in pivot order
-        const double val = (row < rank) ? (row == c ? 1.0 : 0.0) : A[c * m + row];
+        const double val = (row < rank) ? (row == c ? 1.0 : 0.0) : A[c * ld + row];
         g.U[perm[row] + (int64_t)c * g.ldu] = val;
     }
     for (int c = tid; c < rank; c += HSS_NT) {
@@ -404,7 +460,7 @@ __global__ void __launch_bounds__(HSS_NT) k_id(const IdDesc* D, int nd, double t
     if (tid == 0) *g.out_rank = rank;
 }
 
-static size_t id_smem(int s, int m) { return (size_t)s * m * 8 + (size_t)m * 20 + (size_t)s * 8 + 64; }
+static size_t id_smem(int s, int m) { return (size_t)s * id_ld(m) * 8 + (size_t)m * 20 + (size_t)s * 8 + 64; }
 
 int hss_launch_id(const IdDesc* dev, int nd, int smax, int mmax, double tol, cudaStream_t st)
 {

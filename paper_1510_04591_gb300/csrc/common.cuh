@@ -80,6 +80,9 @@ struct LevelWS {
     float *dhK, *dlK;  // FP32 pair of dK (dK ~ dhK + dlK, 48 bits): FP32 midpoint test and
                        // the double-float secular iterations
     float *wfK, *wlK;  // wK as an FP32 pair (wK ~ wfK + wlK)
+    float* dxK;        // third part of dK: dK = dhK + dlK + dxK exactly (the double-float
+                       // Cauchy kernel forms pole differences from it)
+    float *ufK, *ulK;  // uhat as an FP32 pair (written by k_lowner)
 };
 
 // Per-kernel timing of a solve made with TDEIG_FLAG_PROFILE: td_prof_begin
@@ -138,8 +141,9 @@ void td_launch_prep(const MergeDesc* M, int nmerge, const LevelWS& ws, cudaStrea
 // nmax: the largest merge size of the launch (bounds every K; picks the form)
 void td_launch_secular(const MergeDesc* M, int nmerge, int rows, int nmax, const LevelWS& ws,
                        int* status, cudaStream_t st);
+// df: the Cauchy-like matrix in double-float (split-precision solves)
 void td_launch_lowner_cauchy(const MergeDesc* M, int nmerge, int rows, int kmax, const LevelWS& ws,
-                             int write_qhat, cudaStream_t st);
+                             int write_qhat, cudaStream_t st, bool df = false);
 // k_cauchy alone (v and, with write_qhat, the Cauchy-like matrix) from uhat.
 void td_launch_cauchy(const MergeDesc* M, int nmerge, int rows, int kmax, const LevelWS& ws,
                       int write_qhat, cudaStream_t st);

@@ -680,7 +680,10 @@ __global__ void __launch_bounds__(PREP_NT) k_prep(const MergeDesc* M, LevelWS ws
                 ws.wK[g0 + k] = wi;
                 const float dh = __double2float_rn(di);
                 ws.dhK[g0 + k] = dh;
-                ws.dlK[g0 + k] = __double2float_rn(di - (double)dh);
+                const double r1 = di - (double)dh;   // exact
+                const float dm = __double2float_rn(r1);
+                ws.dlK[g0 + k] = dm;
+                ws.dxK[g0 + k] = __double2float_rn(r1 - (double)dm);   // exact (a few bits)
                 const float wh = __double2float_rn(wi);
                 ws.wfK[g0 + k] = wh;
                 ws.wlK[g0 + k] = __double2float_rn(wi - (double)wh);
@@ -1526,19 +1529,27 @@ __global__ void k_secular(const MergeDesc* M, int nmerge, int rows, LevelWS ws, 
     }
 }
 
+// Lanes per root: the smallest group the merge size allows (4 up to 64 poles, 8
+// up to 128, 16 up to 256, else a warp), widened while the launch would have
+// fewer than 16 warps per SM (fewer roots per warp then hide more latency).
+static int secular_group(int nmax, int rows)
+{
+    int g = nmax <= 64 ? 4 : nmax <= 128 ? 8 : nmax <= TD_SECULAR_GRP_MAXK ? 16 : 32;
+    while (g < 32 && (long long)rows * g / 32 < 16LL * td_sm_count()) g *= 2;
+    return g;
+}
+
 void td_launch_secular(const MergeDesc* M, int nmerge, int rows, int nmax, const LevelWS& ws,
                        int* status, cudaStream_t st)
 {
     if (rows <= 0) return;
     td_prof_begin(st);
-    if (nmax <= 64)
-        k_secular_grp<4><<<td_cdiv(rows, 64), 256, 0, st>>>(M, nmerge, rows, ws, status);
-    else if (nmax <= 128)
-        k_secular_grp<8><<<td_cdiv(rows, 32), 256, 0, st>>>(M, nmerge, rows, ws, status);
-    else if (nmax <= TD_SECULAR_GRP_MAXK)
-        k_secular_grp<16><<<td_cdiv(rows, 16), 256, 0, st>>>(M, nmerge, rows, ws, status);
-    else
-        k_secular<<<td_cdiv(rows, 8), 256, 0, st>>>(M, nmerge, rows, ws, status);
+    switch (secular_group(nmax, rows)) {
+    case 4: k_secular_grp<4><<<td_cdiv(rows, 64), 256, 0, st>>>(M, nmerge, rows, ws, status); break;
+    case 8: k_secular_grp<8><<<td_cdiv(rows, 32), 256, 0, st>>>(M, nmerge, rows, ws, status); break;
+    case 16: k_secular_grp<16><<<td_cdiv(rows, 16), 256, 0, st>>>(M, nmerge, rows, ws, status); break;
+    default: k_secular<<<td_cdiv(rows, 8), 256, 0, st>>>(M, nmerge, rows, ws, status); break;
+    }
     td_prof_end(st, "k_secular");
 }
 
@@ -1603,7 +1614,11 @@ __global__ void k_lowner(const MergeDesc* M, int nmerge, int rows, LevelWS ws)
     }
     if (lane == 0) {
         double u = sqrt(scalbn(gam[i] / ws.rho[m] * p, ex));
-        ws.uhat[g0 + i] = copysign(u, ws.zK[g0 + i]);
+        const double us = copysign(u, ws.zK[g0 + i]);
+        ws.uhat[g0 + i] = us;
+        const float uf = __double2float_rn(us);
+        ws.ufK[g0 + i] = uf;
+        ws.ulK[g0 + i] = __double2float_rn(us - (double)uf);
     }
 }
 
@@ -1649,11 +1664,15 @@ __global__ void __launch_bounds__(CAUCHY_NT) k_cauchy(const MergeDesc* M, int nm
         if (SMEM) col[p] = t;
         acc += t * t;
     }
-    acc = blk_sum(acc, red);
-    // one thread takes the FP64 square root and divide (all 256 repeating it
-    // cost the 1/64-rate FP64 pipe a sizeable share of a small column)
+    // warp sums, then the warps' partial sums and the FP64 square root and
+    // divide by one thread (every thread repeating them cost the 1/64-rate FP64
+    // pipe a sizeable share of a small column)
+    acc = td_warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
     __shared__ double s_vj;
     if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) acc += red[w];
         s_vj = 1.0 / sqrt(acc);
         ws.vv[g0 + j] = s_vj;
     }
@@ -1669,16 +1688,183 @@ __global__ void __launch_bounds__(CAUCHY_NT) k_cauchy(const MergeDesc* M, int nm
     }
 }
 
+// ---------------------------------------------------------------------------
+// The Cauchy-like matrix in double-float, for solves whose products are split
+// precision (42-bit slices): the column norms v and the entries of Qhat are
+// formed from FP32 pairs on the FP32 pipe, 64x the FP64 rate on this part
+// (the FP64 form above keeps that pipe ~85 % busy).  Pole differences are
+// exact inputs to it: each pole is held as an exact FP32 triple (dhK + dlK +
+// dxK = dK), so d_k - d_j comes out of TwoSums of the parts with a relative
+// error of about 2^-47 however close the poles; the Remark 1 offset
+// (-gamma_j or mu_j) has the same sign, so d_k - lambda_j keeps that relative
+// accuracy, and the reciprocal (one Newton step from the FP32 estimate), the
+// product with uhat and the squares keep entries and norms within ~2^-44 --
+// below the 2^-42 of the split products that use them.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void df_fast_two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// d_k - p for exact triples (kh + km + kx, ph + pm + px) as a double-float.
+__device__ __forceinline__ void df_pole_diff(float kh, float km, float kx, float ph, float pm,
+                                             float px, float& rh, float& rl)
+{
+    float s1, e1, s2, e2, t, u;
+    df_two_sum(kh, -ph, s1, e1);
+    df_two_sum(km, -pm, s2, e2);
+    const float s3 = __fsub_rn(kx, px);
+    df_two_sum(s1, s2, t, u);
+    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), s3), u);
+    df_two_sum(t, lo, rh, rl);
+}
+
+// uhat_k / (d_k - lambda_j) as a double-float (th, tl).
+__device__ __forceinline__ void df_cauchy_entry(float kh, float km, float kx, float ph, float pm,
+                                                float px, float oh, float ol, float uh, float ul,
+                                                float& th, float& tl)
+{
+    float Ph, Pl, a, b, Dh, Dl;
+    df_pole_diff(kh, km, kx, ph, pm, px, Ph, Pl);
+    df_two_sum(Ph, oh, a, b);                       // same signs: no cancellation
+    b = __fadd_rn(b, __fadd_rn(Pl, ol));
+    df_fast_two_sum(a, b, Dh, Dl);
+    const float q0 = td_rcp_f32(Dh);
+    float r = fmaf(-Dh, q0, 1.0f);
+    r = fmaf(-Dl, q0, r);
+    const float ql = __fmul_rn(q0, r);
+    th = __fmul_rn(uh, q0);
+    tl = __fadd_rn(fmaf(uh, q0, -th), fmaf(uh, ql, __fmul_rn(ul, q0)));
+}
+
+// An FP32 value as FP64 by assembling the bit pattern (sign, rebiased exponent,
+// mantissa) with integer operations: exact for normal values, like a
+// conversion, but off the 1/64-rate FP64 pipe that conversions issue on.
+// Subnormal FP32 values (below 1.2e-38) are taken as zero.
+__device__ __forceinline__ double td_f2d_bits(float x)
+{
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned long long ee = (e == 0xffu) ? 0x7ffull : (unsigned long long)(e + 896u);
+    const unsigned long long b = ((unsigned long long)(u >> 31) << 63) | (ee << 52) |
+                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+    return e == 0u ? 0.0 : __longlong_as_double(b);
+}
+
+template <bool SMEM>
+__global__ void __launch_bounds__(CAUCHY_NT) k_cauchy_df(const MergeDesc* M, int nmerge, int rows,
+                                                         LevelWS ws, int write_qhat)
+{
+    extern __shared__ float2 colf[];
+    const int gcol = blockIdx.x;
+    if (gcol >= rows) return;
+    const int m = td_find_merge(M, nmerge, gcol);
+    if (m < 0) return;
+    const MergeDesc& md = M[m];
+    const int g0 = md.g0;
+    const int j = gcol - g0;
+    const int K = ws.K[m];
+    if (j >= K) return;
+    const float* dh = ws.dhK + g0;
+    const float* dm = ws.dlK + g0;
+    const float* dx = ws.dxK + g0;
+    const float* uf = ws.ufK + g0;
+    const float* ul = ws.ulK + g0;
+    const int* perm = (write_qhat == 2) ? ws.gemmCol + g0 : nullptr;
+    // the column's poles (j and j+1) and Remark 1 offsets as FP32 parts
+    const float pjh = dh[j], pjm = dm[j], pjx = dx[j];
+    const bool hasn = j + 1 < K;
+    const float pnh = hasn ? dh[j + 1] : 0.0f, pnm = hasn ? dm[j + 1] : 0.0f,
+                pnx = hasn ? dx[j + 1] : 0.0f;
+    // the offsets' FP32 pairs by one thread (FP64 conversions issue on the
+    // 1/64-rate pipe; repeated by every thread they outweighed a small column)
+    __shared__ float s_off[4];
+    if (threadIdx.x == 0) {
+        const double ng = -ws.gamK[g0 + j], mj = ws.muK[g0 + j];
+        const float a = __double2float_rn(ng), b = __double2float_rn(mj);
+        s_off[0] = a;
+        s_off[1] = __double2float_rn(ng - (double)a);
+        s_off[2] = b;
+        s_off[3] = __double2float_rn(mj - (double)b);
+    }
+    __syncthreads();
+    const float ngh = s_off[0], ngl = s_off[1], mjh = s_off[2], mjl = s_off[3];
+    auto term = [&](int k, float& th, float& tl) {
+        const bool below = (k <= j);
+        df_cauchy_entry(dh[k], dm[k], dx[k], below ? pjh : pnh, below ? pjm : pnm,
+                        below ? pjx : pnx, below ? ngh : mjh, below ? ngl : mjl, uf[k], ul[k],
+                        th, tl);
+    };
+    float Ah = 0.0f, Al = 0.0f;
+    for (int p = threadIdx.x; p < K; p += blockDim.x) {
+        float th, tl;
+        term(perm ? perm[p] : p, th, tl);
+        if (SMEM) colf[p] = make_float2(th, tl);
+        // (th + tl)^2 to the double-float sum, renormalised every term (a low
+        // part left to grow would carry a rounding error per term)
+        const float sh = __fmul_rn(th, th);
+        const float sl = fmaf(2.0f * th, tl, fmaf(th, th, -sh));
+        float s, e;
+        df_two_sum(Ah, sh, s, e);
+        df_fast_two_sum(s, __fadd_rn(Al, __fadd_rn(e, sl)), Ah, Al);
+    }
+    // block sum in double-float (FP32 shuffles and TwoSums); one thread turns it
+    // into FP64 (an FP64 sum over all threads cost more than a small column)
+    df_warp_sum(Ah, Al);
+    __shared__ float2 s_part[CAUCHY_NT / 32];
+    __shared__ float s_vf[2];
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = make_float2(Ah, Al);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float h = s_part[0].x, l = s_part[0].y;
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+            float t, e;
+            df_two_sum(h, s_part[w].x, t, e);
+            df_fast_two_sum(t, __fadd_rn(l, __fadd_rn(e, s_part[w].y)), h, l);
+        }
+        const double vj = 1.0 / sqrt(td_f2d_bits(h) + td_f2d_bits(l));
+        ws.vv[g0 + j] = vj;
+        s_vf[0] = __double2float_rn(vj);
+        s_vf[1] = __double2float_rn(vj - (double)s_vf[0]);
+    }
+    __syncthreads();
+    if (!write_qhat) return;
+    const float vh = s_vf[0], vl = s_vf[1];
+    double* out = md.qhat + (int64_t)j * (write_qhat == 2 ? md.n : K);
+    for (int p = threadIdx.x; p < K; p += blockDim.x) {
+        float th, tl;
+        if (SMEM) { const float2 t2 = colf[p]; th = t2.x; tl = t2.y; }
+        else term(perm ? perm[p] : p, th, tl);
+        const float ph = __fmul_rn(th, vh);
+        const float pl = __fadd_rn(fmaf(th, vh, -ph), fmaf(th, vl, __fmul_rn(tl, vh)));
+        out[p] = td_f2d_bits(ph) + td_f2d_bits(pl);
+    }
+}
+
 #define CAUCHY_SMEM_MAX 200000
 static void launch_cauchy(const MergeDesc* M, int nmerge, int rows, int kmax, const LevelWS& ws,
-                          int write_qhat, cudaStream_t st)
+                          int write_qhat, cudaStream_t st, bool df = false)
 {
     size_t sm = (size_t)kmax * sizeof(double);
+    // one CTA per column, as many threads as the longest column needs (at most
+    // CAUCHY_NT): idle warps of small columns only added reduction work
+    const int nt = std::min(CAUCHY_NT, std::max(32, td_cdiv(kmax, 32) * 32));
+    if (df) {
+        // double-float form (the FP32 parts of the poles and of uhat are in ws)
+        if (sm <= CAUCHY_SMEM_MAX) {
+            td_smem_attr((const void*)k_cauchy_df<true>, CAUCHY_SMEM_MAX);
+            td_prof_begin(st); k_cauchy_df<true><<<rows, nt, sm, st>>>(M, nmerge, rows, ws, write_qhat); td_prof_end(st, "k_cauchy");
+        } else {
+            td_prof_begin(st); k_cauchy_df<false><<<rows, nt, 0, st>>>(M, nmerge, rows, ws, write_qhat); td_prof_end(st, "k_cauchy");
+        }
+        return;
+    }
     if (sm <= CAUCHY_SMEM_MAX) {
         td_smem_attr((const void*)k_cauchy<true>, CAUCHY_SMEM_MAX);
-        td_prof_begin(st); k_cauchy<true><<<rows, CAUCHY_NT, sm, st>>>(M, nmerge, rows, ws, write_qhat); td_prof_end(st, "k_cauchy");
+        td_prof_begin(st); k_cauchy<true><<<rows, nt, sm, st>>>(M, nmerge, rows, ws, write_qhat); td_prof_end(st, "k_cauchy");
     } else {
-        td_prof_begin(st); k_cauchy<false><<<rows, CAUCHY_NT, 0, st>>>(M, nmerge, rows, ws, write_qhat); td_prof_end(st, "k_cauchy");
+        td_prof_begin(st); k_cauchy<false><<<rows, nt, 0, st>>>(M, nmerge, rows, ws, write_qhat); td_prof_end(st, "k_cauchy");
     }
 }
 
@@ -1690,11 +1876,11 @@ void td_launch_cauchy(const MergeDesc* M, int nmerge, int rows, int kmax, const 
 }
 
 void td_launch_lowner_cauchy(const MergeDesc* M, int nmerge, int rows, int kmax, const LevelWS& ws,
-                             int write_qhat, cudaStream_t st)
+                             int write_qhat, cudaStream_t st, bool df)
 {
     if (rows <= 0) return;
     td_prof_begin(st); k_lowner<<<td_cdiv(rows, 8), 256, 0, st>>>(M, nmerge, rows, ws); td_prof_end(st, "k_lowner");
-    launch_cauchy(M, nmerge, rows, kmax, ws, write_qhat, st);
+    launch_cauchy(M, nmerge, rows, kmax, ws, write_qhat, st, df);
 }
 
 // ---------------------------------------------------------------------------
@@ -1948,7 +2134,10 @@ __global__ void k_stage_init(LevelWS ws, int K, double rho)
         ws.wK[i] = w;
         const float dh = __double2float_rn(di);
         ws.dhK[i] = dh;
-        ws.dlK[i] = __double2float_rn(di - (double)dh);
+        const double r1 = di - (double)dh;
+        const float dm = __double2float_rn(r1);
+        ws.dlK[i] = dm;
+        ws.dxK[i] = __double2float_rn(r1 - (double)dm);
         const float wh = __double2float_rn(w);
         ws.wfK[i] = wh;
         ws.wlK[i] = __double2float_rn(w - (double)wh);
@@ -2100,18 +2289,24 @@ extern "C" int tdeig_secular_noalloc(int64_t K, const double* d, const double* z
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int k = (int)K;
     k_noalloc_weights<<<td_cdiv(k, 256), 256, 0, st>>>(d, z, rho, k, w, wf, wl, dh, dl, status);
-    if (k <= 64)
+    switch (secular_group(k, k)) {   // as tdeig_secular (a single merge of size K)
+    case 4:
         k_secular_noalloc_grp<4><<<td_cdiv(k, 64), 256, 0, st>>>(d, w, wf, wl, dh, dl, k, status,
                                                                 lambda, gamma, mu);
-    else if (k <= 128)
+        break;
+    case 8:
         k_secular_noalloc_grp<8><<<td_cdiv(k, 32), 256, 0, st>>>(d, w, wf, wl, dh, dl, k, status,
                                                                 lambda, gamma, mu);
-    else if (k <= TD_SECULAR_GRP_MAXK)
+        break;
+    case 16:
         k_secular_noalloc_grp<16><<<td_cdiv(k, 16), 256, 0, st>>>(d, w, wf, wl, dh, dl, k, status,
                                                                  lambda, gamma, mu);
-    else
+        break;
+    default:
         k_secular_noalloc<<<td_cdiv(k, 8), 256, 0, st>>>(d, w, wf, wl, dh, dl, k, status, lambda,
                                                           gamma, mu);
+        break;
+    }
     if (cudaGetLastError() != cudaSuccess) return TDEIG_ECUDA;
     int hs = 0;
     if (cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||

@@ -380,6 +380,9 @@ static void carve_level_ws(Arena& a, LevelWS& w, int64_t R, int64_t Mmax)
     w.dlK = a.take<float>(R);
     w.wfK = a.take<float>(R);
     w.wlK = a.take<float>(R);
+    w.dxK = a.take<float>(R);
+    w.ufK = a.take<float>(R);
+    w.ulK = a.take<float>(R);
 }
 
 // Statistics of the last solve: per level the merge sizes n, n1, deflated sizes
@@ -753,7 +756,7 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
                 for (int i = 0; i < nm; i++) any_hss |= Kh[i] > h->opt.hss_threshold;
         }
         MARK("lowner_cauchy", lv);
-        td_launch_lowner_cauchy(Md, nm, L.rows, L.kmax, lws, any_hss ? 1 : 2, st);
+        td_launch_lowner_cauchy(Md, nm, L.rows, L.kmax, lws, any_hss ? 1 : 2, st, split);
         MARK("order", lv);
         td_launch_order(Md, nm, L.nmax, lws, st);
         MARK(any_hss ? "hss_update" : "update", lv);

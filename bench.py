@@ -176,6 +176,11 @@ def grouped_flops(st):
     return fl
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel of the
+# default workload (Toeplitz N=16384, ADC2, split), from an ncu capture of its timed solve
+# (1-pass metrics over all 73 launches); to be removed when the kernel changes
+DRAM_BYTES_PER_LAUNCH = {"k_split_umma": 4.1407e8}
+
 # FP64 issue slots per FP64 secular term (2 subtractions, reciprocal by approximation and two
 # Newton steps, multiply, add, FMA): 10 instructions, measured by an ncu capture of the
 # kernel at about 14 slots of the FP64 pipe
@@ -428,6 +433,13 @@ def main():
                            "stage_ms": st_f[-1]["stage_ms"], "clocks": ck_f,
                            "roofline": roofline(st_f, peaks())}
     out["roofline"] = roofline(stats, peaks())
+    rl = out["roofline"]
+    if (rl and args.n == 16384 and args.matrix == "toeplitz" and args.mode == "adc2"
+            and args.prec == "split" and rl["kernel"] in DRAM_BYTES_PER_LAUNCH):
+        rl["traffic"] = DRAM_BYTES_PER_LAUNCH[rl["kernel"]]
+        rl["traffic_note"] = ("DRAM bytes read + written per launch, mean over the launches of "
+                              "one timed solve of this workload in an ncu capture "
+                              "(profiles/k_split_umma_toeplitz4096_full.md)")
 
     if not args.no_e2e:
         out["e2e"] = e2e(args, a, b, solver, mode)

@@ -165,6 +165,15 @@ int tdeig_lowner_cauchy(tdeig_handle h, int64_t K, const double* d, const double
                         const double* mu, const double* z, double rho,
                         double* uhat, double* v, double* Qhat);
 
+/* The same, with v and Qhat formed as split-precision solves form them
+ * (eq. Ev-Q in double-float on the FP32 units: each pole as an exact triple of
+ * FP32 parts, d_k - lambda_j within ~2^-47 relative however close the poles,
+ * entries and norms within ~2^-44); uhat as tdeig_lowner_cauchy (FP64).
+ * Arguments, layout and errors as tdeig_lowner_cauchy. */
+int tdeig_lowner_cauchy_split(tdeig_handle h, int64_t K, const double* d, const double* gamma,
+                              const double* mu, const double* z, double rho,
+                              double* uhat, double* v, double* Qhat);
+
 /* Split-precision product (the products of TDEIG_PREC_SPLIT / _BF16X2 /
  * _FP16X2 in isolation, not in the paper): C = op(A) op(B) with op(A) M x K,
  * op(B) K x N; A, B, C column-major FP64 with leading dimensions lda, ldb, ldc

@@ -342,8 +342,8 @@ static void build_plan(Plan& P, const Bufs& B, int leaf)
 
 static size_t level_ws_bytes(int64_t R, int64_t Mmax)
 {
-    return (size_t)R * (12 * sizeof(double) + 11 * sizeof(int) + 4 * sizeof(float)) +
-           Mmax * (5 * sizeof(int) + 8) + 37 * 256;
+    return (size_t)R * (12 * sizeof(double) + 11 * sizeof(int) + 7 * sizeof(float)) +
+           Mmax * (5 * sizeof(int) + 8) + 40 * 256;
 }
 
 static void carve_level_ws(Arena& a, LevelWS& w, int64_t R, int64_t Mmax)
@@ -1075,9 +1075,9 @@ extern "C" int tdeig_secular(tdeig_handle h, int64_t K, const double* d, const d
     return (hs & TD_STATUS_NOTCONV) ? TDEIG_ENOTCONV : TDEIG_OK;
 }
 
-extern "C" int tdeig_lowner_cauchy(tdeig_handle h, int64_t K, const double* d, const double* gamma,
-                                   const double* mu, const double* z, double rho, double* uhat,
-                                   double* v, double* Qhat)
+static int lowner_cauchy_stage(tdeig_handle h, int64_t K, const double* d, const double* gamma,
+                               const double* mu, const double* z, double rho, double* uhat,
+                               double* v, double* Qhat, bool df)
 {
     TdCtxScope ctx_scope_(h ? &h->ctx : nullptr);
     if (!h || K < 1 || K > (1 << 20) || !d || !gamma || !mu || !z || !uhat || !v) return TDEIG_EINVAL;
@@ -1102,12 +1102,26 @@ extern "C" int tdeig_lowner_cauchy(tdeig_handle h, int64_t K, const double* d, c
         (rc = copy_in(lws.muK, mu, K, st)) || (rc = copy_in(lws.zK, z, K, st)))
         return rc;
     td_launch_stage_init(lws, (int)K, rho, st);
-    td_launch_lowner_cauchy(md, 1, (int)K, (int)K, lws, Qhat ? 1 : 0, st);
+    td_launch_lowner_cauchy(md, 1, (int)K, (int)K, lws, Qhat ? 1 : 0, st, df);
     CU(cudaGetLastError());
     if ((rc = copy_out(uhat, lws.uhat, K, st)) || (rc = copy_out(v, lws.vv, K, st))) return rc;
     if (Qhat && !qdev) CU(cudaMemcpyAsync(Qhat, qbuf, K * K * sizeof(double), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     return TDEIG_OK;
+}
+
+extern "C" int tdeig_lowner_cauchy(tdeig_handle h, int64_t K, const double* d, const double* gamma,
+                                   const double* mu, const double* z, double rho, double* uhat,
+                                   double* v, double* Qhat)
+{
+    return lowner_cauchy_stage(h, K, d, gamma, mu, z, rho, uhat, v, Qhat, false);
+}
+
+extern "C" int tdeig_lowner_cauchy_split(tdeig_handle h, int64_t K, const double* d,
+                                         const double* gamma, const double* mu, const double* z,
+                                         double rho, double* uhat, double* v, double* Qhat)
+{
+    return lowner_cauchy_stage(h, K, d, gamma, mu, z, rho, uhat, v, Qhat, true);
 }
 
 // ---------------------------------------------------------------------------

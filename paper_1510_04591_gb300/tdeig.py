@@ -76,6 +76,8 @@ def lib():
         L.tdeig_lowner_cauchy.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp, ctypes.c_double, _vp, _vp,
                                           _vp]
         L.tdeig_lowner_cauchy.restype = ctypes.c_int
+        L.tdeig_lowner_cauchy_split.argtypes = L.tdeig_lowner_cauchy.argtypes
+        L.tdeig_lowner_cauchy_split.restype = ctypes.c_int
         L.tdeig_secular_noalloc.argtypes = [_i64, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp]
         L.tdeig_secular_noalloc.restype = ctypes.c_int
         L.tdeig_mlp_forward.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _vp]
@@ -266,16 +268,18 @@ class Solver:
             raise TdeigError(st, "tdeig_secular")
         return lam, gam, mu
 
-    def lowner_cauchy(self, d, gamma, mu, z, rho, qhat=True):
+    def lowner_cauchy(self, d, gamma, mu, z, rho, qhat=True, split=False):
+        """split=True: v and Qhat as split-precision solves form them (double-float)."""
         d, gamma, mu, z = (_as_f64(x) for x in (d, gamma, mu, z))
         K = d.shape[0]
         uh = _empty_like_kind(d, (K,))
         v = _empty_like_kind(d, (K,))
         Qh = _empty_like_kind(d, (K, K), fortran=True) if qhat else None
-        st = lib().tdeig_lowner_cauchy(self.h, K, _ptr(d), _ptr(gamma), _ptr(mu), _ptr(z),
-                                       float(rho), _ptr(uh), _ptr(v), _ptr(Qh))
+        name = "tdeig_lowner_cauchy_split" if split else "tdeig_lowner_cauchy"
+        st = getattr(lib(), name)(self.h, K, _ptr(d), _ptr(gamma), _ptr(mu), _ptr(z),
+                                  float(rho), _ptr(uh), _ptr(v), _ptr(Qh))
         if st != OK:
-            raise TdeigError(st, "tdeig_lowner_cauchy")
+            raise TdeigError(st, name)
         return uh, v, Qh
 
     # ----------------------------------------------------------------------

@@ -92,6 +92,23 @@ def test_lowner_cauchy_stage(solver, K, seed):
     assert metrics.orthogonality(Qh) <= 1e-14
 
 
+@pytest.mark.parametrize("K,seed,cluster", [(1, 0, False), (7, 1, False), (500, 2, True),
+                                            (3000, 3, True)])
+def test_lowner_cauchy_split_stage(solver, K, seed, cluster):
+    """v and Qhat as split-precision solves form them (double-float from exact
+    FP32 triples of the poles) against the FP64 oracle: within ~2^-44, far below
+    the 2^-42 of the split products that use them, also for poles 1e-13 apart."""
+    d, z, rho = rank_one(K, seed, 1.3, cluster)
+    lam, gam, mu, _ = dc.secular(d, z, rho)
+    uh, v, Qh = solver.lowner_cauchy(d, gam, mu, z, rho, split=True)
+    uh_r = dc.lowner(d, gam, mu, rho, z)
+    Qh_r, v_r = dc.cauchy(d, gam, mu, uh_r)
+    assert np.max(np.abs(uh - uh_r)) <= 1e-14
+    assert np.max(np.abs(v - v_r) / v_r) <= 1e-13
+    assert np.max(np.abs(Qh - Qh_r)) <= 1e-13
+    assert metrics.orthogonality(Qh) <= 1e-13
+
+
 # -------------------------------------------------------------------------
 # whole solver, dense mode
 # -------------------------------------------------------------------------

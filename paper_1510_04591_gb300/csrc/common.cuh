@@ -189,6 +189,21 @@ __device__ __forceinline__ double td_dminus(const double* d, const double* gam, 
     return (d[k] - pole) + off;
 }
 
+// 1 / x by Newton-Raphson iteration for the reciprocal (r <- r + r (1 - x r),
+// each step squaring the relative error) from the hardware's approximate FP64
+// reciprocal: two steps take its ~2^-22 seed below 2^-53.  Within a few ulp,
+// not correctly rounded; FP64 divides issue as long instruction sequences on
+// the 1/64-rate FP64 pipe, this is five FP64 instructions.
+__device__ __forceinline__ double td_recip(double x)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+
 __device__ __forceinline__ double td_warp_sum(double v)
 {
 #pragma unroll

@@ -879,20 +879,6 @@ void td_launch_merge_level(const MergeDesc* M, int nmerge, int nmax, int rows, i
 // converged value without evaluating there (the oracle evaluates once more).
 // The K-term sums are lane-strided and reduced with warp shuffles.
 // ---------------------------------------------------------------------------
-// 1 / x by Newton-Raphson iteration for the reciprocal (r <- r + r (1 - x r),
-// each step squaring the relative error) from the hardware's approximate FP64
-// reciprocal: two steps take its ~2^-22 seed below 2^-53.  Within a few ulp,
-// not correctly rounded; FP64 divides issue as long instruction sequences on
-// the 1/64-rate FP64 pipe, this is five FP64 instructions.
-__device__ __forceinline__ double td_recip(double x)
-{
-    double r;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-    double e = fma(-x, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-x, r, 1.0);
-    return fma(r, e, r);
-}
 
 // x = m 2^e with m in [1, 2) (sign kept): returns m and adds sgn * e to *ex.
 // Zero (and subnormal) x is returned unchanged.

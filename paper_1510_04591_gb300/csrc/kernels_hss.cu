@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(HSS_NT) k_id(const IdDesc* D, int nd, double t
                 const double x0 = A[k * ld + k];
                 const double alpha = (x0 >= 0.0) ? -xn : xn;
                 s_stop = xn <= tol * r00;
-                s_par[0] = 1.0 / (alpha * (alpha - x0));   // beta
+                s_par[0] = td_recip(alpha * (alpha - x0));   // beta (Newton reciprocal, a few ulp)
                 s_par[1] = x0 - alpha;                     // first entry of the Householder vector
                 s_par[2] = alpha;
             }
@@ -706,11 +706,15 @@ __global__ void __launch_bounds__(SR_NT) k_srrsc(const SrrscDesc* D, double tol,
         const int p = s_p, q = s_q;
         const double spq = s_spq, gp = g.g[p], hq = g.h[q];
         const int rp = sr_row(g, p), cq = sr_col(g, q);
+        // Schur-complement update of the generators.  Divides are Newton
+        // reciprocals (td_recip, a few ulp) and the pivot's reciprocal is taken
+        // once: IEEE divides, two per row or column and step, issued as long
+        // sequences on the 1/64-rate FP64 pipe and bound the kernel.
+        const double rspq = td_recip(spq), hq_spq = hq * rspq;
         for (int a = tid; a < m; a += SR_NT) {
             if (!g.actr[a]) continue;
             if (a == p) { g.mult[(size_t)a * g.kcap + t] = 1.0; continue; }
-            const double saq = g.g[a] * hq / sr_diff(g, sr_row(g, a), cq);
-            const double l = saq / spq;
+            const double l = g.g[a] * hq_spq * td_recip(sr_diff(g, sr_row(g, a), cq));   // s_aq / s_pq
             g.mult[(size_t)a * g.kcap + t] = l;
             const double ga = g.g[a] - l * gp;
             g.g[a] = ga;
@@ -718,8 +722,8 @@ __global__ void __launch_bounds__(SR_NT) k_srrsc(const SrrscDesc* D, double tol,
         }
         for (int b = tid; b < nc; b += SR_NT) {
             if (!g.actc[b] || b == q) continue;
-            const double spb = gp * g.h[b] / sr_diff(g, rp, sr_col(g, b));
-            const double hb = g.h[b] - spb * hq / spq;
+            const double spb = gp * g.h[b] * td_recip(sr_diff(g, rp, sr_col(g, b)));
+            const double hb = g.h[b] - spb * hq_spq;
             g.h[b] = hb;
             g.hf[b] = (float)hb;
         }

@@ -100,7 +100,7 @@ struct SrrscDesc {
     int base;
     int s0, s1, K, side, kcap;
     const double *d, *gam, *mu, *uh, *v;   // Cauchy generators of the merge
-    float* invd;           // m x ncols magnitudes |1/(d - lambda)| (row-major)
+    float* invd;           // ncols x 8: each column's pole data for the pivot search
     double *g, *h;         // generators, m and ncols
     float *gf, *hf;        // FP32 copies for the pivot search
     unsigned char *actr, *actc;

@@ -625,6 +625,34 @@ __device__ __forceinline__ double sr_diff(const SrrscDesc& g, int r, int c)
     return g.side == 0 ? td_dminus(g.d, g.gam, g.mu, r, c) : td_dminus(g.d, g.gam, g.mu, c, r);
 }
 
+// Pole data of an index x for the pivot search, in FP32: [dh, dl] of d_x (an
+// FP32 pair), [dh, dl] of d_x and of d_x+1 and the Remark 1 offsets -gamma_x,
+// mu_x (for |d_k - lambda_x|).
+__device__ __forceinline__ void sr_pole_f32(const SrrscDesc& g, int x, float* o)
+{
+    const double dx = g.d[x];
+    const float h = __double2float_rn(dx);
+    o[0] = h;
+    o[1] = __double2float_rn(dx - (double)h);
+    o[2] = o[0];
+    o[3] = o[1];
+    const bool nx = x + 1 < g.K;
+    const double d1 = nx ? g.d[x + 1] : 0.0;
+    const float h1 = __double2float_rn(d1);
+    o[4] = h1;
+    o[5] = __double2float_rn(d1 - (double)h1);
+    o[6] = __double2float_rn(-g.gam[x]);
+    o[7] = __double2float_rn(g.mu[x]);
+}
+
+// d_K - lambda_J in FP32 (Remark 1), K's pair (kh, kl), J's pole data J.
+__device__ __forceinline__ float sr_diff_f32(float kh, float kl, int kidx, const float* J, int jidx)
+{
+    const bool below = kidx <= jidx;
+    const float ph = below ? J[2] : J[4], pl = below ? J[3] : J[5];
+    return ((kh - ph) + (kl - pl)) + (below ? J[6] : J[7]);
+}
+
 __global__ void __launch_bounds__(SR_NT) k_srrsc(const SrrscDesc* D, double tol, int* status)
 {
     __shared__ float redv[SR_NT / 32];
@@ -633,9 +661,15 @@ __global__ void __launch_bounds__(SR_NT) k_srrsc(const SrrscDesc* D, double tol,
     __shared__ double s_spq;
     __shared__ int s_pr[SR_MAXK];
     __shared__ int s_rowpos[SR_MAXM];
+    // rows' pole data, global indices, FP32 generators and active flags
+    __shared__ float s_row[SR_MAXM][8];
+    __shared__ int s_ridx[SR_MAXM];
+    __shared__ float s_gf[SR_MAXM];
+    __shared__ unsigned char s_act[SR_MAXM];
     const SrrscDesc g = D[blockIdx.x];
     const int m = g.m, nc = g.K - (g.s1 - g.s0);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    float* const ctab = g.invd;   // per column: its pole data (8 floats)
     for (int a = tid; a < m; a += SR_NT) {
         const int ra = sr_row(g, a);
         const double gv = g.side == 0 ? g.uh[ra] : g.v[ra];
@@ -643,6 +677,10 @@ __global__ void __launch_bounds__(SR_NT) k_srrsc(const SrrscDesc* D, double tol,
         g.gf[a] = (float)gv;
         g.actr[a] = 1;
         s_rowpos[a] = -1;
+        s_ridx[a] = ra;
+        s_gf[a] = (float)gv;
+        s_act[a] = 1;
+        sr_pole_f32(g, ra, s_row[a]);
     }
     for (int b = tid; b < nc; b += SR_NT) {
         const int cb = sr_col(g, b);
@@ -650,26 +688,37 @@ __global__ void __launch_bounds__(SR_NT) k_srrsc(const SrrscDesc* D, double tol,
         g.h[b] = hv;
         g.hf[b] = (float)hv;
         g.actc[b] = 1;
-    }
-    for (int a = wid; a < m; a += SR_NT / 32) {
-        const int ra = sr_row(g, a);
-        for (int b = lane; b < nc; b += 32)
-            g.invd[(size_t)a * nc + b] = 1.0f / fabsf((float)sr_diff(g, ra, sr_col(g, b)));
+        float o[8];
+        sr_pole_f32(g, cb, o);
+        float4* c4 = reinterpret_cast<float4*>(ctab + (size_t)8 * b);
+        c4[0] = make_float4(o[0], o[1], o[2], o[3]);
+        c4[1] = make_float4(o[4], o[5], o[6], o[7]);
     }
     __syncthreads();
     const int kmax = min(g.kcap, min(m, nc));
     double first = 0.0;
     int rank = 0;
     for (int t = 0; t < kmax; t++) {
+        // Pivot: the largest |g_a h_b / (d - lambda)| over the active block, in
+        // FP32 with the differences formed on the fly (Remark 1, FP32 pairs of
+        // the poles): each thread owns columns and sweeps the rows held in
+        // shared memory.  (A stored m x ncols table of 1/|d - lambda| re-read
+        // every step kept the kernel waiting on memory.)  The pivot's entry is
+        // then formed in FP64.  Ties go to the lowest row-major index.
         float best = -1.0f;
         int bi = 0x7fffffff;
-        for (int a = wid; a < m; a += SR_NT / 32) {
-            if (!g.actr[a]) continue;
-            const float ga = fabsf(g.gf[a]);
-            const float* row = g.invd + (size_t)a * nc;
-            for (int b = lane; b < nc; b += 32) {
-                if (!g.actc[b]) continue;
-                const float val = ga * fabsf(g.hf[b]) * row[b];
+        for (int b = tid; b < nc; b += SR_NT) {
+            if (!g.actc[b]) continue;
+            const float hb = fabsf(g.hf[b]);
+            const int cb = sr_col(g, b);
+            const float4* c4 = reinterpret_cast<const float4*>(ctab + (size_t)8 * b);
+            const float4 u0 = c4[0], u1 = c4[1];
+            const float C[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+            for (int a = 0; a < m; a++) {
+                if (!s_act[a]) continue;
+                const float dv = g.side == 0 ? sr_diff_f32(s_row[a][0], s_row[a][1], s_ridx[a], C, cb)
+                                             : sr_diff_f32(C[0], C[1], cb, s_row[a], s_ridx[a]);
+                const float val = fabsf(s_gf[a]) * hb / fabsf(dv);
                 const int idx = a * nc + b;
                 if (val > best || (val == best && idx < bi)) { best = val; bi = idx; }
             }
@@ -719,6 +768,7 @@ __global__ void __launch_bounds__(SR_NT) k_srrsc(const SrrscDesc* D, double tol,
             const double ga = g.g[a] - l * gp;
             g.g[a] = ga;
             g.gf[a] = (float)ga;
+            s_gf[a] = (float)ga;
         }
         for (int b = tid; b < nc; b += SR_NT) {
             if (!g.actc[b] || b == q) continue;
@@ -728,7 +778,7 @@ __global__ void __launch_bounds__(SR_NT) k_srrsc(const SrrscDesc* D, double tol,
             g.hf[b] = (float)hb;
         }
         __syncthreads();
-        if (tid == 0) { g.actr[p] = 0; g.actc[q] = 0; }
+        if (tid == 0) { g.actr[p] = 0; g.actc[q] = 0; s_act[p] = 0; }
         __syncthreads();
         rank = t + 1;
     }
@@ -911,7 +961,7 @@ static int srrsc_levels(const tdeig_options& opt, std::vector<HMerge>& H, int Lm
                         b.map2 = side ? c2->J : c2->I;
                         b.m = b.n1 + (side ? c2->kV : c2->kU);
                     }
-                    b.invd = S.take<float>((size_t)b.m * nc);
+                    b.invd = S.take<float>((size_t)8 * nc);   // the columns' pole data
                     b.g = S.take<double>(b.m);
                     b.h = S.take<double>(nc);
                     b.gf = S.take<float>(b.m);

@@ -210,12 +210,16 @@ def kernel_work(name, stats_list, pk):
         return (sum(s.get("split_tensor_flops", 0.0) for s in stats_list) / 1e12, peak, "tensor",
                 "TFLOP/s", "tensor work issued (2 M N K per slice pair) against the measured bf16 "
                 "peak (cuBLAS burst) %.0f TFLOP/s" % peak)
-    if name in ("k_slice", "k_slice_exp"):
-        key = "split_slice_bytes" if name == "k_slice" else "split_exp_bytes"
+    if name in ("k_slice", "k_slice_exp", "k_slice_fused"):
+        key = {"k_slice": "split_slice_bytes", "k_slice_exp": "split_exp_bytes",
+               "k_slice_fused": "split_fused_bytes"}[name]
         peak = pk.get("hbm_gbs", 6800.0)
-        what = ("reads each operand element once (8 B) and writes its s 16-bit slices "
-                "(2 s B per element, k padded to 32)" if name == "k_slice" else
-                "reads each operand element once (8 B) for the row exponents")
+        what = {"k_slice": "reads each operand element once (8 B) and writes its s 16-bit slices "
+                           "(2 s B per element, k padded to 32)",
+                "k_slice_exp": "reads each operand element once (8 B) for the row exponents",
+                "k_slice_fused": "one pass for operands with short rows (k <= 256): reads each "
+                                 "element once (8 B), writes its s 16-bit slices (2 s B per "
+                                 "element, k padded to 32) and the row exponents"}[name]
         return (sum(s.get(key, 0.0) for s in stats_list) / 1e9, peak, "hbm", "GB/s",
                 "algorithmic bytes: %s; masked sampling entries counted as read; against the "
                 "measured HBM copy bandwidth %.0f GB/s" % (what, peak))

@@ -106,6 +106,7 @@ struct TdCtx {
     double split_tensor_flops = 0.0;   // tensor work issued: 2 M N K per slice pair
     double split_slice_bytes = 0.0;    // algorithmic bytes of k_slice (read 8 B, write 2 s B per element)
     double split_exp_bytes = 0.0;      // algorithmic bytes of k_slice_exp (read 8 B per element)
+    double split_fused_bytes = 0.0;    // algorithmic bytes of k_slice_fused (read 8 B, write 2 s B per element)
     double small_gemm_flops = 0.0;     // FP64 flops of the small-tile grouped products (k_gemm_small)
     TdProf prof;
 };

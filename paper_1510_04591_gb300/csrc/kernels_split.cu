@@ -1,7 +1,8 @@
 // Split-precision FP64 products on the tensor cores (see split.cuh for the
 // scheme).  k_slice_exp finds the per-row exponent bounds of op(A) / per-column
 // ones of op(B); k_slice writes the digits as BF16 or FP16 slices (K
-// contiguous, padded to a multiple of 32); the products run in k_split_umma
+// contiguous, padded to a multiple of 32); operands with short rows take both
+// steps in one pass (k_slice7f); the products run in k_split_umma
 // (kernels_umma.cu).
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -35,13 +36,19 @@ __device__ __forceinline__ double slice_load(const SliceDesc& d, int r, int k)
 #define SE_K 1024
 
 // Operand of flattened tile t: the last operand whose first tile is <= t
-// (every launch covers exactly the tiles of its operands, whatever their sizes).
-__device__ __forceinline__ int sl_operand(const SliceDesc* D, int nop, int t, bool exp_pass)
+// (every launch covers exactly the tiles of its operands, whatever their sizes;
+// an operand with no tile in a launch shares its first tile with the next one
+// and is never chosen).  Launch: 0 exponents, 1 slices, 2 one-pass slices.
+__device__ __forceinline__ int sl_first(const SliceDesc& d, int launch)
+{
+    return launch == 0 ? d.t_exp : (launch == 1 ? d.t_sl : d.t_fu);
+}
+__device__ __forceinline__ int sl_operand(const SliceDesc* D, int nop, int t, int launch)
 {
     int lo = 0, hi = nop - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if ((exp_pass ? D[mid].t_exp : D[mid].t_sl) <= t) lo = mid; else hi = mid - 1;
+        if (sl_first(D[mid], launch) <= t) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
@@ -61,7 +68,7 @@ __host__ __device__ __forceinline__ int se_kchunk(long long sr) { return sr == 1
 __global__ void k_slice_exp(const SliceDesc* D, int nop)
 {
     const int t = blockIdx.x;
-    const SliceDesc d = D[sl_operand(D, nop, t, true)];
+    const SliceDesc d = D[sl_operand(D, nop, t, 0)];
     const int RT = se_rows(d.sr);
     const int ry = (d.rows + RT - 1) / RT;
     const int local = t - d.t_exp;
@@ -178,7 +185,7 @@ __device__ __forceinline__ void slice_tile_load(const SliceDesc& d, double (*T)[
 __global__ void __launch_bounds__(SL_NT) k_slice(const SliceDesc* D, int nop)
 {
     const int t = blockIdx.x;   // flattened (operand, 64-row tile, 64-wide k tile)
-    const SliceDesc d = D[sl_operand(D, nop, t, false)];
+    const SliceDesc d = D[sl_operand(D, nop, t, 1)];
     const int ky = (d.Kp + SL_T - 1) / SL_T;
     const int k0 = ((t - d.t_sl) % ky) * SL_T, r0 = ((t - d.t_sl) / ky) * SL_R;
     // actual sizes (device-sized operands: the upper bounds only place the tiles);
@@ -254,11 +261,67 @@ __global__ void __launch_bounds__(SL_NT) k_slice(const SliceDesc* D, int nop)
 // 2^(-7p) and -192 2^(-7p); t_0 <= 128 has at most 8 significant bits and is
 // converted exactly through FP32.  The entries' signs are then set by an XOR of
 // the sign bits.  Every value is exact.
+// The S slices of 8 consecutive entries src[0..7] (in shared memory, 16-byte
+// aligned) of a row with exponent bound e: slice p's 8 values go to dst + p * pstep
+// with one 16-byte store.
+template <int S>
+__device__ __forceinline__ void slice7_emit(const double2* src, int e, __nv_bfloat16* dst, size_t pstep)
+{
+    constexpr int BS = 7 * S;
+    // 64 in every base-128 digit below the top one
+    unsigned long long B = 0;
+#pragma unroll
+    for (int j = 0; j < S - 1; j++) B |= 64ull << (7 * j);
+    unsigned long long m[8];
+    unsigned sgn[4];   // sign bits of the pairs at bits 15 and 31
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const double2 x2 = src[j];
+        m[2 * j] = (unsigned long long)slice_mag(x2.x, e, BS) + B;
+        m[2 * j + 1] = (unsigned long long)slice_mag(x2.y, e, BS) + B;
+        sgn[j] = (((unsigned)__double2hiint(x2.x) >> 31) << 15) | ((unsigned)__double2hiint(x2.y) & 0x80000000u);
+    }
+    {
+        // top digit t_0 = (m + B) >> 7 (S - 1) in [0, 128], exact through FP32
+        unsigned w[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const unsigned t0 = (unsigned)(m[2 * j] >> (7 * (S - 1)));
+            const unsigned t1 = (unsigned)(m[2 * j + 1] >> (7 * (S - 1)));
+            const unsigned h0 = __float_as_uint(__uint_as_float(0x4B000000u | t0) - 8388608.0f) >> 16;
+            const unsigned h1 = __float_as_uint(__uint_as_float(0x4B000000u | t1) - 8388608.0f) >> 16;
+            w[j] = (h0 | (h1 << 16)) ^ sgn[j];
+        }
+        *(uint4*)dst = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+#pragma unroll
+    for (int p = 1; p < S; p++) {
+        const int sh = 7 * (S - 1 - p);
+        const unsigned sc = (unsigned)(127 - 7 * p) << 7;                     // BF16 2^(-7p)
+        const unsigned nc = ((unsigned)(134 - 7 * p) << 7) | 0x8040u;         // BF16 -192 2^(-7p)
+        const __nv_bfloat162 sc2 = __halves2bfloat162(__ushort_as_bfloat16((unsigned short)sc),
+                                                      __ushort_as_bfloat16((unsigned short)sc));
+        const __nv_bfloat162 nc2 = __halves2bfloat162(__ushort_as_bfloat16((unsigned short)nc),
+                                                      __ushort_as_bfloat16((unsigned short)nc));
+        unsigned w[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const unsigned d0 = (unsigned)(m[2 * j] >> sh) & 127u;
+            const unsigned d1 = (unsigned)(m[2 * j + 1] >> sh) & 127u;
+            const unsigned pk = d0 | (d1 << 16) | 0x43004300u;
+            __nv_bfloat162 x = *reinterpret_cast<const __nv_bfloat162*>(&pk);
+            x = __hfma2(x, sc2, nc2);
+            w[j] = *reinterpret_cast<const unsigned*>(&x) ^ sgn[j];
+        }
+        *(uint4*)(dst + (size_t)p * pstep) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
 template <int S>
 __global__ void __launch_bounds__(SL_NT, 2) k_slice7(const SliceDesc* D, int nop)
 {
     const int t = blockIdx.x;   // flattened (operand, 64-row tile, 64-wide k tile)
-    const SliceDesc d = D[sl_operand(D, nop, t, false)];
+    const SliceDesc d = D[sl_operand(D, nop, t, 1)];
     const int ky = (d.Kp + SL_T - 1) / SL_T;
     const int k0 = ((t - d.t_sl) % ky) * SL_T, r0 = ((t - d.t_sl) / ky) * SL_R;
     // actual sizes (device-sized operands: the upper bounds only place the tiles);
@@ -272,62 +335,112 @@ __global__ void __launch_bounds__(SL_NT, 2) k_slice7(const SliceDesc* D, int nop
     const int tid = threadIdx.x;
     slice_tile_load(d, T, r0, k0, nrows, Kact);
     __syncthreads();
-    constexpr int BS = 7 * S;
-    // 64 in every base-128 digit below the top one
-    unsigned long long B = 0;
-#pragma unroll
-    for (int j = 0; j < S - 1; j++) B |= 64ull << (7 * j);
 #pragma unroll
     for (int i = 0; i < (SL_R * SL_T / 8) / SL_NT; i++) {
         const int u = tid + SL_NT * i;
         const int r = u / (SL_T / 8), kg = u % (SL_T / 8);
         const int row = r0 + r, kk = k0 + kg * 8;
         if (row >= nrows || kk >= Kpa) continue;
-        const int e = d.e[row];
-        unsigned long long m[8];
-        unsigned sgn[4];   // sign bits of the pairs at bits 15 and 31
-        const double2* src = (const double2*)&T[r][kg * SL_G];
+        slice7_emit<S>((const double2*)&T[r][kg * SL_G], d.e[row], d.S + (size_t)row * d.Kp + kk,
+                       (size_t)d.rows * d.Kp);
+    }
+}
+
+// One-pass form for operands with short padded rows (Kp <= SF_KMAX: the
+// products of Algorithm 3, whose k ranges are a leaf's columns or a node's
+// ranks).  A CTA holds SF_ELEMS entries, sf_rows(Kp) whole rows, in shared
+// memory (Kp / 8 groups of 8 doubles per row, each padded to 10 as in k_slice7),
+// takes each row's exponent bound from the integer maxima of the exponent
+// fields, stores it for the product and writes the digits: each operand entry is
+// read from memory once, and the exponent launch is not needed.
+#define SF_ELEMS 8192
+#define SF_KMAX 256
+__host__ __device__ __forceinline__ int sf_rows(int Kp) { return SF_ELEMS / Kp; }
+__host__ __device__ __forceinline__ int sf_rowstride(int Kp) { return (Kp / 8) * SL_G + 2; }
+// dynamic shared memory of the largest tile (Kp = 32: 256 rows of 42 doubles)
+#define SF_SMEM ((size_t)(SF_ELEMS / 8 * SL_G + 2 * (SF_ELEMS / 32)) * sizeof(double))
+
+template <int S>
+__global__ void __launch_bounds__(SL_NT, 2) k_slice7f(const SliceDesc* D, int nop)
+{
+    const int t = blockIdx.x;   // flattened (operand, row tile)
+    const SliceDesc d = D[sl_operand(D, nop, t, 2)];
+    const int RT = sf_rows(d.Kp), G = d.Kp >> 3, rs = sf_rowstride(d.Kp);
+    const int r0 = (t - d.t_fu) * RT;
+    // actual sizes, as in k_slice7
+    const int nrows = (d.dynK && d.dyn_rows) ? *d.dynK : d.rows;
+    const int Kact = d.dynK ? *d.dynK : d.K;
+    const int Kpa = d.dynK ? min(d.Kp, max(32, ((Kact + 31) / 32) * 32)) : d.Kp;
+    if (r0 >= nrows) return;
+    extern __shared__ __align__(16) double sl_smem[];
+    __shared__ int s_part[SF_ELEMS / 8 + SF_ELEMS / 256];   // per group, index u + u / 32
+    __shared__ int s_e[SF_ELEMS / 32];                      // per row
+    const int tid = threadIdx.x;
+    const int nel = RT * d.Kp;
+    // the tile, lanes along whichever dimension of X is contiguous: flattened
+    // index i = a + W b with a along that dimension (rows when sr == 1), stepped
+    // by SL_NT without divisions; all loads issued before any shared store
+    const int W = (d.sr == 1) ? RT : d.Kp;
+    const int bq = SL_NT / W, aq = SL_NT % W;
+    {
+        double v[SF_ELEMS / SL_NT];
+        int a = tid % W, b = tid / W;
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const double2 x2 = src[j];
-            m[2 * j] = (unsigned long long)slice_mag(x2.x, e, BS) + B;
-            m[2 * j + 1] = (unsigned long long)slice_mag(x2.y, e, BS) + B;
-            sgn[j] = (((unsigned)__double2hiint(x2.x) >> 31) << 15) | ((unsigned)__double2hiint(x2.y) & 0x80000000u);
+        for (int i = 0; i < SF_ELEMS / SL_NT; i++) {
+            const int r = (d.sr == 1) ? a : b, k = (d.sr == 1) ? b : a;
+            v[i] = (tid + SL_NT * i < nel && r0 + r < nrows && k < Kact) ? slice_load(d, r0 + r, k) : 0.0;
+            a += aq; b += bq;
+            if (a >= W) { a -= W; b++; }
         }
-        {
-            // top digit t_0 = (m + B) >> 7 (S - 1) in [0, 128], exact through FP32
-            unsigned w[4];
+        a = tid % W; b = tid / W;
+#pragma unroll
+        for (int i = 0; i < SF_ELEMS / SL_NT; i++) {
+            const int r = (d.sr == 1) ? a : b, k = (d.sr == 1) ? b : a;
+            if (tid + SL_NT * i < nel) sl_smem[r * rs + (k >> 3) * SL_G + (k & 7)] = v[i];
+            a += aq; b += bq;
+            if (a >= W) { a -= W; b++; }
+        }
+    }
+    __syncthreads();
+    // largest exponent field of each group of 8, then of each row
+    const int ng = RT * G;
+#pragma unroll
+    for (int i = 0; i < SF_ELEMS / 8 / SL_NT; i++) {
+        const int u = tid + SL_NT * i;
+        if (u < ng) {
+            const int r = u / G, kg = u - r * G;
+            const double2* src = (const double2*)&sl_smem[r * rs + kg * SL_G];
+            int mx = 0;
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                const unsigned t0 = (unsigned)(m[2 * j] >> (7 * (S - 1)));
-                const unsigned t1 = (unsigned)(m[2 * j + 1] >> (7 * (S - 1)));
-                const unsigned h0 = __float_as_uint(__uint_as_float(0x4B000000u | t0) - 8388608.0f) >> 16;
-                const unsigned h1 = __float_as_uint(__uint_as_float(0x4B000000u | t1) - 8388608.0f) >> 16;
-                w[j] = (h0 | (h1 << 16)) ^ sgn[j];
+                const double2 x2 = src[j];
+                mx = max(mx, max(exp_field(x2.x), exp_field(x2.y)));
             }
-            *(uint4*)(d.S + (size_t)row * d.Kp + kk) = make_uint4(w[0], w[1], w[2], w[3]);
+            s_part[u + (u >> 5)] = mx;
         }
-#pragma unroll
-        for (int p = 1; p < S; p++) {
-            const int sh = 7 * (S - 1 - p);
-            const unsigned sc = (unsigned)(127 - 7 * p) << 7;                     // BF16 2^(-7p)
-            const unsigned nc = ((unsigned)(134 - 7 * p) << 7) | 0x8040u;         // BF16 -192 2^(-7p)
-            const __nv_bfloat162 sc2 = __halves2bfloat162(__ushort_as_bfloat16((unsigned short)sc),
-                                                          __ushort_as_bfloat16((unsigned short)sc));
-            const __nv_bfloat162 nc2 = __halves2bfloat162(__ushort_as_bfloat16((unsigned short)nc),
-                                                          __ushort_as_bfloat16((unsigned short)nc));
-            unsigned w[4];
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const unsigned d0 = (unsigned)(m[2 * j] >> sh) & 127u;
-                const unsigned d1 = (unsigned)(m[2 * j + 1] >> sh) & 127u;
-                const unsigned pk = d0 | (d1 << 16) | 0x43004300u;
-                __nv_bfloat162 x = *reinterpret_cast<const __nv_bfloat162*>(&pk);
-                x = __hfma2(x, sc2, nc2);
-                w[j] = *reinterpret_cast<const unsigned*>(&x) ^ sgn[j];
-            }
-            *(uint4*)(d.S + ((size_t)p * d.rows + row) * d.Kp + kk) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    __syncthreads();
+    if (tid < RT) {
+        int mx = 0;
+        for (int kg = 0; kg < G; kg++) {
+            const int u = tid * G + kg;
+            mx = max(mx, s_part[u + (u >> 5)]);
         }
+        // no normal entry: the bound stays far below any exponent (all digits zero)
+        const int e = mx > 0 ? mx - 1022 : (int)0xC0C0C0C0;
+        s_e[tid] = e;
+        if (r0 + tid < nrows) d.e[r0 + tid] = e;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < SF_ELEMS / 8 / SL_NT; i++) {
+        const int u = tid + SL_NT * i;
+        if (u >= ng) continue;
+        const int r = u / G, kg = u - r * G;
+        const int row = r0 + r, kk = kg * 8;
+        if (row >= nrows || kk >= Kpa) continue;
+        slice7_emit<S>((const double2*)&sl_smem[r * rs + kg * SL_G], s_e[r], d.S + (size_t)row * d.Kp + kk,
+                       (size_t)d.rows * d.Kp);
     }
 }
 
@@ -428,18 +541,13 @@ static int split_prepare(const std::vector<GemmDesc>& gin, char* desc, char* sli
         if (d.M > 0 && d.N > 0) g.push_back(d);
     if (g.empty()) return TDEIG_OK;
     std::vector<int> kps(g.size());
-    double flops = 0.0, tflops = 0.0, sbytes = 0.0, ebytes = 0.0;
+    double flops = 0.0, tflops = 0.0, sbytes = 0.0, ebytes = 0.0, fbytes = 0.0;
     const int s = pr.s;
     for (size_t i = 0; i < g.size(); i++) {
         const int Kt = g[i].Kd + g[i].Kd2;
         kps[i] = std::max(32, ((Kt + 31) / 32) * 32);
         flops += 2.0 * g[i].M * g[i].N * Kt;
         tflops += 2.0 * g[i].M * g[i].N * Kt * (s * (s + 1) / 2);
-        // algorithmic traffic: every operand element read once by each slicing kernel,
-        // 2 s bytes of slices written per padded element
-        const double elems = (double)(g[i].M + g[i].N) * Kt;
-        sbytes += 8.0 * elems + 2.0 * s * (double)(g[i].M + g[i].N) * kps[i];
-        ebytes += 8.0 * elems;
     }
     char* p = desc;
     auto take = [&](size_t n) { char* r = p; p += al256(n); return r; };
@@ -515,15 +623,29 @@ static int split_prepare(const std::vector<GemmDesc>& gin, char* desc, char* sli
         tiles += sd.tiles_m * sd.tiles_n;
         sg.push_back(sd);
     }
-    // flattened tile lists of the two slicing launches
-    long long nexp = 0, nsl = 0;
+    // flattened tile lists of the slicing launches: operands with short rows (7-bit
+    // digits, not masked) go to the one-pass kernel, the others to the exponent and
+    // slicing kernels.  Algorithmic traffic: every operand element read once by each
+    // kernel that reads it, 2 s bytes of slices written per padded element.
+    const bool fuse = pr.beta == 7 && !pr.f16;
+    long long nexp = 0, nsl = 0, nfu = 0;
     for (auto& o : sl) {
         o.t_exp = (int)nexp;
         o.t_sl = (int)nsl;
-        nexp += (long long)td_cdiv(o.rows, se_rows(o.sr)) * td_cdiv(o.K, se_kchunk(o.sr));
-        nsl += (long long)td_cdiv(o.Kp, SL_T) * td_cdiv(o.rows, SL_R);
+        o.t_fu = (int)nfu;
+        const double elems = (double)o.rows * o.K;
+        const double bytes = 8.0 * elems + 2.0 * s * (double)o.rows * o.Kp;
+        if (fuse && o.Kp <= SF_KMAX && !o.mask) {
+            nfu += td_cdiv(o.rows, sf_rows(o.Kp));
+            fbytes += bytes;
+        } else {
+            nexp += (long long)td_cdiv(o.rows, se_rows(o.sr)) * td_cdiv(o.K, se_kchunk(o.sr));
+            nsl += (long long)td_cdiv(o.Kp, SL_T) * td_cdiv(o.rows, SL_R);
+            sbytes += bytes;
+            ebytes += 8.0 * elems;
+        }
     }
-    if (nexp >= (1ll << 31) || nsl >= (1ll << 31)) return TDEIG_EINVAL;
+    if (nexp >= (1ll << 31) || nsl >= (1ll << 31) || nfu >= (1ll << 31)) return TDEIG_EINVAL;
     std::vector<int> t0(sg.size());
     for (size_t i = 0; i < sg.size(); i++) t0[i] = sg[i].tile0;
     if (cudaMemcpyAsync(dtm, tm.data(), tm.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st) !=
@@ -536,10 +658,10 @@ static int split_prepare(const std::vector<GemmDesc>& gin, char* desc, char* sli
             cudaSuccess)
         return TDEIG_ECUDA;
     // the host vectors are pageable: the copies are staged before returning
-    L->dsl = dsl; L->nop = (int)sl.size(); L->nexp = nexp; L->nsl = nsl;
+    L->dsl = dsl; L->nop = (int)sl.size(); L->nexp = nexp; L->nsl = nsl; L->nfu = nfu;
     L->dsg = dsg; L->dt0 = dt0; L->ng = (int)sg.size(); L->tiles = tiles;
     L->ebase = ebase; L->erows = erows;
-    L->flops = flops; L->tflops = tflops; L->sbytes = sbytes; L->ebytes = ebytes;
+    L->flops = flops; L->tflops = tflops; L->sbytes = sbytes; L->ebytes = ebytes; L->fbytes = fbytes;
     double kbl = 0.0;
     for (size_t i = 0; i < g.size(); i++)
         kbl += (double)sg[i].tiles_m * sg[i].tiles_n * (kps[i] / UM_BK);
@@ -547,50 +669,64 @@ static int split_prepare(const std::vector<GemmDesc>& gin, char* desc, char* sli
     return TDEIG_OK;
 }
 
-// The kernels of a prepared launch: exponents, slices, the tensor-core product.
+template <int S>
+static void launch_slice7(bool fused, unsigned grid, size_t smem, const SliceDesc* dsl, int nop, cudaStream_t st)
+{
+    const void* fn = fused ? (const void*)k_slice7f<S> : (const void*)k_slice7<S>;
+    td_smem_attr(fn, smem);
+    if (fused) k_slice7f<S><<<grid, SL_NT, smem, st>>>(dsl, nop);
+    else k_slice7<S><<<grid, SL_NT, smem, st>>>(dsl, nop);
+}
+
+static void launch_slice7_s(int s, bool fused, unsigned grid, size_t smem, const SliceDesc* dsl, int nop,
+                            cudaStream_t st)
+{
+    switch (s) {
+    case 1: launch_slice7<1>(fused, grid, smem, dsl, nop, st); break;
+    case 2: launch_slice7<2>(fused, grid, smem, dsl, nop, st); break;
+    case 3: launch_slice7<3>(fused, grid, smem, dsl, nop, st); break;
+    case 4: launch_slice7<4>(fused, grid, smem, dsl, nop, st); break;
+    case 5: launch_slice7<5>(fused, grid, smem, dsl, nop, st); break;
+    case 6: launch_slice7<6>(fused, grid, smem, dsl, nop, st); break;
+    case 7: launch_slice7<7>(fused, grid, smem, dsl, nop, st); break;
+    default: launch_slice7<8>(fused, grid, smem, dsl, nop, st); break;
+    }
+}
+
+// The kernels of a prepared launch: exponents and slices (two passes for long
+// rows, one for short ones), then the tensor-core product.
 void split_run(const SplitLaunch& L, int* status, cudaStream_t st, int* rc)
 {
     *rc = TDEIG_OK;
     if (L.ng == 0) return;
     const SplitPrec& pr = L.pr;
-    if (cudaMemsetAsync(L.ebase, 0xC0, L.erows * 4, st) != cudaSuccess) {
-        *rc = TDEIG_ECUDA;
-        return;
-    }
-    td_prof_begin(st);
-    k_slice_exp<<<(unsigned)L.nexp, 256, 0, st>>>(L.dsl, L.nop);
-    td_prof_end(st, "k_slice_exp");
-    const unsigned gs = (unsigned)L.nsl;
-    const size_t tile_smem = (size_t)SL_R * SL_ROW * sizeof(double);   // 82 KiB: opt-in size
-    td_prof_begin(st);
-    if (pr.beta == 7 && !pr.f16) {
-        const void* fn;
-        switch (pr.s) {
-        case 1: fn = (const void*)k_slice7<1>; break;
-        case 2: fn = (const void*)k_slice7<2>; break;
-        case 3: fn = (const void*)k_slice7<3>; break;
-        case 4: fn = (const void*)k_slice7<4>; break;
-        case 5: fn = (const void*)k_slice7<5>; break;
-        case 6: fn = (const void*)k_slice7<6>; break;
-        case 7: fn = (const void*)k_slice7<7>; break;
-        default: fn = (const void*)k_slice7<8>; break;
+    if (L.nexp > 0) {
+        // bounds start far below any exponent; the one-pass kernel writes its rows' own
+        if (cudaMemsetAsync(L.ebase, 0xC0, L.erows * 4, st) != cudaSuccess) {
+            *rc = TDEIG_ECUDA;
+            return;
         }
-        td_smem_attr(fn, tile_smem);
-        switch (pr.s) {
-        case 1: k_slice7<1><<<gs, SL_NT, tile_smem, st>>>(L.dsl, L.nop); break;
-        case 2: k_slice7<2><<<gs, SL_NT, tile_smem, st>>>(L.dsl, L.nop); break;
-        case 3: k_slice7<3><<<gs, SL_NT, tile_smem, st>>>(L.dsl, L.nop); break;
-        case 4: k_slice7<4><<<gs, SL_NT, tile_smem, st>>>(L.dsl, L.nop); break;
-        case 5: k_slice7<5><<<gs, SL_NT, tile_smem, st>>>(L.dsl, L.nop); break;
-        case 6: k_slice7<6><<<gs, SL_NT, tile_smem, st>>>(L.dsl, L.nop); break;
-        case 7: k_slice7<7><<<gs, SL_NT, tile_smem, st>>>(L.dsl, L.nop); break;
-        default: k_slice7<8><<<gs, SL_NT, tile_smem, st>>>(L.dsl, L.nop); break;
-        }
-    } else {
-        td_smem_attr((const void*)k_slice, tile_smem);
-        k_slice<<<gs, SL_NT, tile_smem, st>>>(L.dsl, L.nop);
+        td_prof_begin(st);
+        k_slice_exp<<<(unsigned)L.nexp, 256, 0, st>>>(L.dsl, L.nop);
+        td_prof_end(st, "k_slice_exp");
     }
-    td_prof_end(st, "k_slice");
+    if (L.nsl > 0) {
+        const unsigned gs = (unsigned)L.nsl;
+        const size_t tile_smem = (size_t)SL_R * SL_ROW * sizeof(double);   // 82 KiB: opt-in size
+        td_prof_begin(st);
+        if (pr.beta == 7 && !pr.f16) {
+            launch_slice7_s(pr.s, false, gs, tile_smem, L.dsl, L.nop, st);
+        } else {
+            td_smem_attr((const void*)k_slice, tile_smem);
+            k_slice<<<gs, SL_NT, tile_smem, st>>>(L.dsl, L.nop);
+        }
+        td_prof_end(st, "k_slice");
+    }
+    if (L.nfu > 0) {
+        td_prof_begin(st);
+        launch_slice7_s(pr.s, true, (unsigned)L.nfu, SF_SMEM, L.dsl, L.nop, st);
+        td_prof_end(st, "k_slice_fused");
+    }
     umma_launch(L.dsg, L.dt0, L.ng, L.tiles, pr.s, pr.nacc, status, st);
     TdCtx& cx = td_ctx();
     // [tiles, k-blocks over all tiles, slices, problems, tensor flops]
@@ -598,6 +734,7 @@ void split_run(const SplitLaunch& L, int* status, cudaStream_t st, int* rc)
     cx.split_tensor_flops += L.tflops;
     cx.split_slice_bytes += L.sbytes;
     cx.split_exp_bytes += L.ebytes;
+    cx.split_fused_bytes += L.fbytes;
     if (cudaGetLastError() != cudaSuccess) *rc = TDEIG_ECUDA;
 }
 

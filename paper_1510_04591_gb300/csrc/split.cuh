@@ -40,6 +40,7 @@ struct SliceDesc {
     __nv_bfloat16* S;   // slice p, row r at S + (p * rows + r) * Kp (16-bit values)
     int* e;             // exponent bound per row: max |row| < 2^e
     int t_exp, t_sl;    // first tile of this operand in the exponent and slicing launches
+    int t_fu;           // first tile in the one-pass launch (operands with short rows)
     // optional: rows (when dyn_rows) and K read from *dynK at run time; rows, K are
     // then upper bounds (see GemmDesc::dynK)
     const int* dynK;
@@ -106,14 +107,14 @@ double split_launch_gemm(const std::vector<GemmDesc>& g, SplitWS& ws, cudaStream
 struct SplitLaunch {
     SliceDesc* dsl = nullptr;
     int nop = 0;
-    long long nexp = 0, nsl = 0;
+    long long nexp = 0, nsl = 0, nfu = 0;
     SplitGemmDesc* dsg = nullptr;
     int* dt0 = nullptr;
     int ng = 0, tiles = 0;
     int* ebase = nullptr;
     size_t erows = 0;
     SplitPrec pr{};
-    double flops = 0, tflops = 0, sbytes = 0, ebytes = 0;
+    double flops = 0, tflops = 0, sbytes = 0, ebytes = 0, fbytes = 0;
     char note[160] = {0};
 };
 // Bytes of the slices of a launch (returned) and of its descriptors (*desc_bytes).

@@ -476,6 +476,7 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
     const long long launches0 = cx.launches;
     const double split_flops0 = cx.split_tensor_flops;
     const double slice_bytes0 = cx.split_slice_bytes, exp_bytes0 = cx.split_exp_bytes;
+    const double fused_bytes0 = cx.split_fused_bytes;
     const double small_flops0 = cx.small_gemm_flops;
     TdProf& prof = cx.prof;
     // per-kernel events only for this solve (see TDEIG_FLAG_PROFILE)
@@ -926,9 +927,10 @@ static int solve_impl(tdeig_ctx* h, int64_t batch, const int64_t* N_each, const 
         }
         snprintf(kb, sizeof(kb),
                  ",\"split_tensor_flops\":%.6e,\"split_slice_bytes\":%.6e,\"split_exp_bytes\":%.6e,"
-                 "\"small_gemm_flops\":%.6e",
+                 "\"split_fused_bytes\":%.6e,\"small_gemm_flops\":%.6e",
                  cx.split_tensor_flops - split_flops0, cx.split_slice_bytes - slice_bytes0,
-                 cx.split_exp_bytes - exp_bytes0, cx.small_gemm_flops - small_flops0);
+                 cx.split_exp_bytes - exp_bytes0, cx.split_fused_bytes - fused_bytes0,
+                 cx.small_gemm_flops - small_flops0);
         kj += kb;
         h->stats.pop_back();
         h->stats += kj + "}";

@@ -129,3 +129,26 @@ def test_zero_rows_and_columns():
     e = rel_err(C[np.ix_(rows, cols)], A[rows], B[:, cols])
     print("zero rows/cols", e)
     assert e <= 2.0 ** -36
+
+
+@pytest.mark.parametrize("M,N,K,tA,tB", [(1000, 70, 256, False, False), (777, 45, 200, True, True),
+                                         (300, 300, 96, False, True)])
+def test_one_pass_and_two_pass_slicing_agree(M, N, K, tA, tB):
+    """Operands with k <= 256 are sliced in one pass (exponents and digits by
+    one CTA that holds whole rows); longer ones by the exponent and slicing
+    kernels.  Padding k with zero columns past 256 moves the same product to the
+    two-pass path without changing any exponent bound or digit, and the level
+    sums stay within one drain (k <= 384), so the two results are bit-identical."""
+    rng = np.random.default_rng(M + K)
+    A = rng.standard_normal((M, K)) * np.exp(rng.uniform(-20, 20, (M, 1)))
+    B = rng.standard_normal((K, N)) * np.exp(rng.uniform(-20, 20, (1, N)))
+    Kz = 320
+    Az = np.zeros((M, Kz)); Az[:, :K] = A
+    Bz = np.zeros((Kz, N)); Bz[:K, :] = B
+    opA = lambda X: np.ascontiguousarray(X.T) if tA else X
+    opB = lambda X: np.ascontiguousarray(X.T) if tB else X
+    with solver() as s:
+        C1 = s.split_gemm(opA(A), opB(B), "split", 40, tA, tB)
+        C2 = s.split_gemm(opA(Az), opB(Bz), "split", 40, tA, tB)
+    assert np.array_equal(C1, C2)
+    assert rel_err(C1, A, B) <= 2.0 ** -36

@@ -87,7 +87,28 @@ __global__ void k_slice_exp(const SliceDesc* D, int nop)
         const int r = r0 + 32 * (ty & 3) + tx;
         const int kp = ty >> 2;
         int mx = 0;
-        if (r < nrows)
+        if (d.twin_e) {
+            // also the column maxima (the twin's row bounds): every lane runs the
+            // loop (rows past the end read as zero) for the warp maxima over its rows
+            __shared__ int s_cm[256];
+            for (int i = threadIdx.x; i < 256; i += 256) s_cm[i] = 0;
+            __syncthreads();
+            for (int k = kb + kp; k < ke; k += 32) {
+                double v[16];
+#pragma unroll
+                for (int j = 0; j < 16; j++) v[j] = (r < nrows && k + 2 * j < ke) ? slice_load(d, r, k + 2 * j) : 0.0;
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    const int f = exp_field(v[j]);
+                    mx = max(mx, f);
+                    const int cm = __reduce_max_sync(0xffffffffu, f);
+                    if (tx == 0 && cm > 0) atomicMax(&s_cm[k + 2 * j - kb], cm);
+                }
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < ke - kb; i += 256)
+                if (s_cm[i] > 0) atomicMax(d.twin_e + kb + i, s_cm[i] - 1022);
+        } else if (r < nrows) {
             for (int k = kb + kp; k < ke; k += 32) {
                 double v[16];
 #pragma unroll
@@ -95,6 +116,7 @@ __global__ void k_slice_exp(const SliceDesc* D, int nop)
 #pragma unroll
                 for (int j = 0; j < 16; j++) mx = max(mx, exp_field(v[j]));
             }
+        }
         red[ty][tx] = mx;
         __syncthreads();
         if (ty < 4 && r < nrows) {
@@ -691,21 +713,38 @@ static int split_prepare(const std::vector<GemmDesc>& gin, char* desc, char* sli
     // slicing kernels.  Algorithmic traffic: every operand element read once by each
     // kernel that reads it, 2 s bytes of slices written per padded element.
     const bool fuse = pr.beta == 7 && !pr.f16;
+    auto one_pass = [&](const SliceDesc& o) { return fuse && o.Kp <= SF_KMAX && !o.mask; };
+    // transposed twins (Y = A Omega then Z = A^T Omega over the same masked A, as
+    // ADC2's sampling issues them): Z's exponents come from Y's exponent pass
+    std::vector<char> covered(sl.size(), 0);
+    for (size_t i = 0; i + 1 < g.size(); i++) {
+        const GemmDesc &y = g[i], &z = g[i + 1];
+        SliceDesc &ay = sl[2 * i], &az = sl[2 * i + 2];
+        if (!y.transA && z.transA && y.A == z.A && y.lda == z.lda && y.amask && y.amask == z.amask &&
+            y.Kd2 == 0 && z.Kd2 == 0 && y.M == y.Kd && z.M == z.Kd && y.M == z.M && !y.dynK && !z.dynK &&
+            !y.acol && !one_pass(ay) && !one_pass(az) && !covered[2 * i]) {
+            ay.twin_e = az.e;
+            covered[2 * i + 2] = 1;
+        }
+    }
     long long nexp = 0, nsl = 0, nfu = 0;
-    for (auto& o : sl) {
+    for (size_t oi = 0; oi < sl.size(); oi++) {
+        SliceDesc& o = sl[oi];
         o.t_exp = (int)nexp;
         o.t_sl = (int)nsl;
         o.t_fu = (int)nfu;
         const double elems = (double)o.rows * o.K;
         const double bytes = 8.0 * elems + 2.0 * s * (double)o.rows * o.Kp;
-        if (fuse && o.Kp <= SF_KMAX && !o.mask) {
+        if (one_pass(o)) {
             nfu += td_cdiv(o.rows, sf_rows(o.Kp));
             fbytes += bytes;
         } else {
-            nexp += (long long)td_cdiv(o.rows, se_rows(o.sr)) * td_cdiv(o.K, se_kchunk(o.sr));
+            if (!covered[oi]) {
+                nexp += (long long)td_cdiv(o.rows, se_rows(o.sr)) * td_cdiv(o.K, se_kchunk(o.sr));
+                ebytes += 8.0 * elems;
+            }
             nsl += (long long)td_cdiv(o.Kp, SL_T) * td_cdiv(o.rows, SL_R);
             sbytes += bytes;
-            ebytes += 8.0 * elems;
         }
     }
     if (nexp >= (1ll << 31) || nsl >= (1ll << 31) || nfu >= (1ll << 31)) return TDEIG_EINVAL;

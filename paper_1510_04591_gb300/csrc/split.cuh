@@ -45,6 +45,11 @@ struct SliceDesc {
     // then upper bounds (see GemmDesc::dynK)
     const int* dynK;
     int dyn_rows;
+    // optional: the exponent bounds of the transposed twin operand (same X and
+    // mask, rows and k swapped: ADC2's Z = Qhat^T Omega beside Y = Qhat Omega),
+    // raised from this operand's exponent pass, which has every entry in hand;
+    // the twin then has no exponent tiles of its own
+    int* twin_e;
 };
 
 // One slice-pair product C = alpha 2^(ea+eb) sum_{p+q<=s-1} ... + betac C.
